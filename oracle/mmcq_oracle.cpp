@@ -1,0 +1,835 @@
+// FP64 CPU oracle for the LLG + cavity-QED hot path of Mumax3-cQED
+// (arXiv 2410.00966).
+//
+// TEST INFRASTRUCTURE ONLY.  Only tests, the package smoke check and the
+// benchmark's CPU-baseline leg may load this library.  It shares no code,
+// header, table or constant generator with the CUDA library; every formula is
+// written out here from the paper (and from the published demag-tensor and
+// Runge-Kutta literature the paper relies on) in plain loops.
+//
+// What it computes, by paper section / equation:
+//   * LLG right-hand side, Eq. (llg) of Sec. 2.1.
+//   * Effective field terms listed in Sec. 2.1: Zeeman, demagnetisation,
+//     exchange, uniaxial anisotropy (thermal and DMI are out of scope: all
+//     runs are at T = 0 and none uses DMI).
+//   * Cavity field B_cav = B_rms * Gamma(t), Eq. (bcav) / Eq. (gammafinal),
+//     Sec. 2.2, in two forms:
+//       E-mode: the photon amplitude alpha is integrated as an ODE state next
+//               to m, using the classical equations of motion of Sec. 2.2
+//               (Eq. eqmotionspinclasical, Eq. eqmotionaclasical) with the loss
+//               substitution omega_c -> omega_c - i kappa.  Integrating alpha
+//               out (Appendix A) gives exactly Eq. (gammafinal).
+//       P-mode: the paper-literal recursive accumulators S_n, C_n of Sec. 3.1
+//               (Eq. Sdiscrete, Eq. Cdiscrete) and Gamma from
+//               Eq. (gammadiscretefinal).
+//   * Demag tensor: Newell, Williams & Dunlop (1993) cell-averaged tensor,
+//     point-dipole form beyond a switch radius (the paper does not describe
+//     Mumax3's demag kernel; this is the reading used by both sides).
+//   * Integrators: classic RK4 and Dormand-Prince 5(4) (the paper uses
+//     Mumax3's unmodified ODE solver, Sec. 3.1).
+//
+// Parity of this oracle against the real Mumax3-cQED program is unpinned
+// (no program output is available); each function is pinned instead by the
+// closed forms, invariants and brute-force checks in tests/test_oracle_*.py.
+//
+// Build: g++ -O2 -fopenmp -shared -fPIC -o liboracle.so mmcq_oracle.cpp
+
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+typedef std::complex<double> cplx;
+
+static const double OR_PI = 3.14159265358979323846264338327950288;
+
+// ---------------------------------------------------------------------------
+// Demag tensor (Newell et al. 1993).  The paper lists B_demag among the field
+// terms (Sec. 2.1) without giving the method.
+// ---------------------------------------------------------------------------
+
+// Newell's f(x,y,z); even in every argument.  Written for a generic real type
+// so that an extended-precision copy can pin the double one.
+template <typename T>
+static T newell_f_t(T x, T y, T z) {
+    x = std::fabs(x); y = std::fabs(y); z = std::fabs(z);
+    T x2 = x * x, y2 = y * y, z2 = z * z;
+    T R = std::sqrt(x2 + y2 + z2);
+    T r = 0;
+    if (x2 + z2 > 0) r += T(0.5) * y * (z2 - x2) * std::asinh(y / std::sqrt(x2 + z2));
+    if (x2 + y2 > 0) r += T(0.5) * z * (y2 - x2) * std::asinh(z / std::sqrt(x2 + y2));
+    if (x > 0 && R > 0) r -= x * y * z * std::atan(y * z / (x * R));
+    r += (T(2) * x2 - y2 - z2) * R / T(6);
+    return r;
+}
+
+// Newell's g(x,y,z); odd in x and y, even in z.
+template <typename T>
+static T newell_g_t(T x, T y, T z) {
+    T sgn = 1;
+    if (x < 0) { sgn = -sgn; x = -x; }
+    if (y < 0) { sgn = -sgn; y = -y; }
+    z = std::fabs(z);
+    T x2 = x * x, y2 = y * y, z2 = z * z;
+    T R = std::sqrt(x2 + y2 + z2);
+    T r = 0;
+    if (x2 + y2 > 0) r += x * y * z * std::asinh(z / std::sqrt(x2 + y2));
+    if (y2 + z2 > 0) r += y / T(6) * (T(3) * z2 - y2) * std::asinh(x / std::sqrt(y2 + z2));
+    if (x2 + z2 > 0) r += x / T(6) * (T(3) * z2 - x2) * std::asinh(y / std::sqrt(x2 + z2));
+    if (z > 0 && R > 0) r -= z2 * z / T(6) * std::atan(x * y / (z * R));
+    if (y > 0 && R > 0) r -= z * y2 / T(2) * std::atan(x * z / (y * R));
+    if (x > 0 && R > 0) r -= z * x2 / T(2) * std::atan(y * z / (x * R));
+    r -= x * y * R / T(3);
+    return sgn * r;
+}
+
+// Weight of offset e in {-1,0,1} in the 27-point second-difference stencil.
+static inline int nw(int e) { return e == 0 ? 2 : -1; }
+
+// Exact Newell tensor between two cells of size dx*dy*dz whose centres differ
+// by (X,Y,Z).  out = {Nxx, Nyy, Nzz, Nxy, Nxz, Nyz}.  N is positive-definite
+// in the self term (a cube gives 1/3 on the diagonal) and H = -N M.
+template <typename T>
+static void newell_t(T X, T Y, T Z, T dx, T dy, T dz, T out[6]) {
+    T sxx = 0, syy = 0, szz = 0, sxy = 0, sxz = 0, syz = 0;
+    for (int i = -1; i <= 1; i++)
+        for (int j = -1; j <= 1; j++)
+            for (int k = -1; k <= 1; k++) {
+                T w = T(nw(i) * nw(j) * nw(k));
+                T x = X + i * dx, y = Y + j * dy, z = Z + k * dz;
+                sxx += w * newell_f_t<T>(x, y, z);
+                syy += w * newell_f_t<T>(y, x, z);
+                szz += w * newell_f_t<T>(z, y, x);
+                sxy += w * newell_g_t<T>(x, y, z);
+                sxz += w * newell_g_t<T>(x, z, y);
+                syz += w * newell_g_t<T>(y, z, x);
+            }
+    T c = T(1) / (T(4) * T(OR_PI) * dx * dy * dz);
+    out[0] = sxx * c; out[1] = syy * c; out[2] = szz * c;
+    out[3] = sxy * c; out[4] = sxz * c; out[5] = syz * c;
+}
+
+// Point-dipole tensor of a source cell of volume V at offset r:
+// N_ab = V/(4 pi r^3) (delta_ab - 3 r_a r_b / r^2).
+static void dipole_tensor(double X, double Y, double Z, double V, double out[6]) {
+    double r2 = X * X + Y * Y + Z * Z;
+    double r = std::sqrt(r2);
+    double c = V / (4.0 * OR_PI * r2 * r);
+    out[0] = c * (1.0 - 3.0 * X * X / r2);
+    out[1] = c * (1.0 - 3.0 * Y * Y / r2);
+    out[2] = c * (1.0 - 3.0 * Z * Z / r2);
+    out[3] = -c * 3.0 * X * Y / r2;
+    out[4] = -c * 3.0 * X * Z / r2;
+    out[5] = -c * 3.0 * Y * Z / r2;
+}
+
+// Switch radius, in units of the largest cell edge: Newell's closed form is
+// used up to and including this distance, the point dipole beyond it.
+static const double OR_R_SWITCH = 16.0;
+
+// The demag tensor as the method defines it here.
+static void demag_tensor(double X, double Y, double Z, double dx, double dy, double dz,
+                         double out[6]) {
+    double h = std::fmax(dx, std::fmax(dy, dz));
+    double r2 = X * X + Y * Y + Z * Z;
+    if (r2 <= (OR_R_SWITCH * h) * (OR_R_SWITCH * h))
+        newell_t<double>(X, Y, Z, dx, dy, dz, out);
+    else
+        dipole_tensor(X, Y, Z, dx * dy * dz, out);
+}
+
+// Aharoni (1998) demagnetising factor D_z of a rectangular prism with full
+// edges (2a, 2b, 2c) along (x, y, z); an independent closed form that the
+// cell-averaged Newell tensor must reproduce.
+static double aharoni_dz(double a, double b, double c) {
+    double abc = std::sqrt(a * a + b * b + c * c);
+    double ab = std::sqrt(a * a + b * b), bc = std::sqrt(b * b + c * c),
+           ac = std::sqrt(a * a + c * c);
+    double s = 0;
+    s += (b * b - c * c) / (2 * b * c) * std::log((abc - a) / (abc + a));
+    s += (a * a - c * c) / (2 * a * c) * std::log((abc - b) / (abc + b));
+    s += b / (2 * c) * std::log((ab + a) / (ab - a));
+    s += a / (2 * c) * std::log((ab + b) / (ab - b));
+    s += c / (2 * a) * std::log((bc - b) / (bc + b));
+    s += c / (2 * b) * std::log((ac - a) / (ac + a));
+    s += 2 * std::atan(a * b / (c * abc));
+    s += (a * a * a + b * b * b - 2 * c * c * c) / (3 * a * b * c);
+    s += (a * a + b * b - 2 * c * c) / (3 * a * b * c) * abc;
+    s += c / (a * b) * (ac + bc);
+    s -= (std::pow(ab, 3) + std::pow(bc, 3) + std::pow(ac, 3)) / (3 * a * b * c);
+    return s / OR_PI;
+}
+
+// ---------------------------------------------------------------------------
+// Plain radix-2 complex FFT (FP64), used for the oracle's own zero-padded
+// convolution.  sign = -1 forward, +1 inverse (unnormalised).
+// ---------------------------------------------------------------------------
+// tw[k] = exp(sign * 2 pi i k / n) for k < n/2.
+static void fft1d(cplx* a, int n, const cplx* tw) {
+    for (int i = 1, j = 0; i < n; i++) {
+        int bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) std::swap(a[i], a[j]);
+    }
+    for (int len = 2; len <= n; len <<= 1) {
+        int step = n / len;
+        for (int k = 0; k < len / 2; k++) {
+            cplx w = tw[k * step];
+            for (int i = 0; i < n; i += len) {
+                cplx u = a[i + k], v = a[i + k + len / 2] * w;
+                a[i + k] = u + v;
+                a[i + k + len / 2] = u - v;
+            }
+        }
+    }
+}
+
+static std::vector<cplx> twiddles(int n, int sign) {
+    std::vector<cplx> tw(n / 2 + 1);
+    for (int k = 0; k <= n / 2; k++) {
+        double ang = sign * 2.0 * OR_PI * k / n;
+        tw[k] = cplx(std::cos(ang), std::sin(ang));
+    }
+    return tw;
+}
+
+// 3-D FFT of an array laid out [z][y][x] with sizes (px, py, pz).
+static void fft3d(cplx* a, int px, int py, int pz, int sign) {
+    std::vector<cplx> twx = twiddles(px, sign), twy = twiddles(py, sign), twz = twiddles(pz, sign);
+#pragma omp parallel if ((long)px * py * pz >= 32768)
+    {
+        std::vector<cplx> line(std::max(px, std::max(py, pz)));
+#pragma omp for collapse(2)
+        for (int z = 0; z < pz; z++)
+            for (int y = 0; y < py; y++) fft1d(a + ((size_t)z * py + y) * px, px, twx.data());
+#pragma omp for collapse(2)
+        for (int z = 0; z < pz; z++)
+            for (int x = 0; x < px; x++) {
+                for (int y = 0; y < py; y++) line[y] = a[((size_t)z * py + y) * px + x];
+                fft1d(line.data(), py, twy.data());
+                for (int y = 0; y < py; y++) a[((size_t)z * py + y) * px + x] = line[y];
+            }
+#pragma omp for collapse(2)
+        for (int y = 0; y < py; y++)
+            for (int x = 0; x < px; x++) {
+                for (int z = 0; z < pz; z++) line[z] = a[((size_t)z * py + y) * px + x];
+                fft1d(line.data(), pz, twz.data());
+                for (int z = 0; z < pz; z++) a[((size_t)z * py + y) * px + x] = line[z];
+            }
+    }
+}
+
+static int pow2_at_least(int n) {
+    int p = 1;
+    while (p < n) p <<= 1;
+    return p;
+}
+
+// ---------------------------------------------------------------------------
+// Simulation state.
+// ---------------------------------------------------------------------------
+enum { OR_DEMAG_NONE = 0, OR_DEMAG_DIRECT = 1, OR_DEMAG_FFT = 2 };
+enum { OR_RK4 = 0, OR_DP45 = 1 };
+enum { OR_CAV_E = 0, OR_CAV_P = 1 };
+
+struct oracle {
+    int nx, ny, nz;
+    long n;
+    double dx, dy, dz, vc;
+    double Aex, alpha, Ku, u[3];
+    double gamma, mu0, hbar;
+    std::vector<double> ms;    // [n]
+    std::vector<double> m;     // [n*3]
+    double bext[3];
+    // cavity (Sec. 2.2 / 3.1)
+    int cav_on;
+    double wc, kappa, x0, p0;
+    std::vector<double> brms;  // [n*3] in tesla
+    int cav_mode;
+    cplx a;        // E-mode photon amplitude alpha
+    double S, C;   // P-mode accumulators (include the cell volume V_c)
+    double t, tcav;
+    // integrator
+    int kind; double tol, dt_next;
+    long n_acc, n_rej;
+    std::vector<double> dt_hist;
+    // demag
+    int demag;
+    int px, py, pz;
+    std::vector<double> Nreal;   // direct: [(2nz-1)(2ny-1)(2nx-1)][6]
+    std::vector<cplx> Nhat;      // fft: [6][pz*py*px]
+};
+
+static inline long cidx(const oracle* o, int x, int y, int z) {
+    return ((long)z * o->ny + y) * o->nx + x;
+}
+
+// Demag field B_demag,i = -mu0 sum_j N(r_i - r_j) Ms_j m_j  (Sec. 2.1 term
+// list), by the plain O(N^2) sum.
+static void demag_direct(const oracle* o, const double* m, double* B) {
+    int nx = o->nx, ny = o->ny, nz = o->nz;
+    int ox = 2 * nx - 1, oy = 2 * ny - 1;
+#pragma omp parallel for collapse(3) schedule(static) if (o->n >= 256)
+    for (int zi = 0; zi < nz; zi++)
+        for (int yi = 0; yi < ny; yi++)
+            for (int xi = 0; xi < nx; xi++) {
+                double h[3] = {0, 0, 0};
+                for (int zj = 0; zj < nz; zj++)
+                    for (int yj = 0; yj < ny; yj++)
+                        for (int xj = 0; xj < nx; xj++) {
+                            long j = cidx(o, xj, yj, zj);
+                            double M[3] = {o->ms[j] * m[3 * j], o->ms[j] * m[3 * j + 1],
+                                           o->ms[j] * m[3 * j + 2]};
+                            long t = (((long)(zi - zj + nz - 1) * oy + (yi - yj + ny - 1)) * ox +
+                                      (xi - xj + nx - 1)) * 6;
+                            const double* N = &o->Nreal[t];
+                            h[0] += N[0] * M[0] + N[3] * M[1] + N[4] * M[2];
+                            h[1] += N[3] * M[0] + N[1] * M[1] + N[5] * M[2];
+                            h[2] += N[4] * M[0] + N[5] * M[1] + N[2] * M[2];
+                        }
+                long i = cidx(o, xi, yi, zi);
+                B[3 * i] = -o->mu0 * h[0];
+                B[3 * i + 1] = -o->mu0 * h[1];
+                B[3 * i + 2] = -o->mu0 * h[2];
+            }
+}
+
+// Same convolution through the oracle's own zero-padded FFT.
+static void demag_fft(const oracle* o, const double* m, double* B) {
+    int px = o->px, py = o->py, pz = o->pz;
+    size_t P = (size_t)px * py * pz;
+    std::vector<cplx> Mh(3 * P, cplx(0, 0));
+    for (int z = 0; z < o->nz; z++)
+        for (int y = 0; y < o->ny; y++)
+            for (int x = 0; x < o->nx; x++) {
+                long i = cidx(o, x, y, z);
+                size_t p = ((size_t)z * py + y) * px + x;
+                for (int c = 0; c < 3; c++) Mh[c * P + p] = o->ms[i] * m[3 * i + c];
+            }
+    for (int c = 0; c < 3; c++) fft3d(&Mh[c * P], px, py, pz, -1);
+    const cplx *Nxx = &o->Nhat[0], *Nyy = &o->Nhat[P], *Nzz = &o->Nhat[2 * P],
+               *Nxy = &o->Nhat[3 * P], *Nxz = &o->Nhat[4 * P], *Nyz = &o->Nhat[5 * P];
+    std::vector<cplx> Hh(3 * P);
+#pragma omp parallel for if (P >= 32768)
+    for (long p = 0; p < (long)P; p++) {
+        cplx mx = Mh[p], my = Mh[P + p], mz = Mh[2 * P + p];
+        Hh[p] = Nxx[p] * mx + Nxy[p] * my + Nxz[p] * mz;
+        Hh[P + p] = Nxy[p] * mx + Nyy[p] * my + Nyz[p] * mz;
+        Hh[2 * P + p] = Nxz[p] * mx + Nyz[p] * my + Nzz[p] * mz;
+    }
+    for (int c = 0; c < 3; c++) fft3d(&Hh[c * P], px, py, pz, +1);
+    for (int z = 0; z < o->nz; z++)
+        for (int y = 0; y < o->ny; y++)
+            for (int x = 0; x < o->nx; x++) {
+                long i = cidx(o, x, y, z);
+                size_t p = ((size_t)z * py + y) * px + x;
+                for (int c = 0; c < 3; c++) B[3 * i + c] = -o->mu0 * Hh[c * P + p].real() / (double)P;
+            }
+}
+
+static void demag_field(const oracle* o, const double* m, double* B) {
+    if (o->demag == OR_DEMAG_DIRECT) demag_direct(o, m, B);
+    else if (o->demag == OR_DEMAG_FFT) demag_fft(o, m, B);
+    else std::memset(B, 0, sizeof(double) * 3 * o->n);
+}
+
+// Exchange field (Sec. 2.1 term list): B = 2A/Ms_i sum_j (m_j - m_i)/d_ij^2
+// over the six face neighbours that exist and carry magnetisation (free,
+// Neumann boundaries).
+static void exchange_field(const oracle* o, const double* m, double* B) {
+#pragma omp parallel for collapse(3) if (o->n >= 32768)
+    for (int z = 0; z < o->nz; z++)
+        for (int y = 0; y < o->ny; y++)
+            for (int x = 0; x < o->nx; x++) {
+                long i = cidx(o, x, y, z);
+                double h[3] = {0, 0, 0};
+                if (o->ms[i] > 0) {
+                    const int nb[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0},
+                                          {0, 1, 0},  {0, 0, -1}, {0, 0, 1}};
+                    const double d2[3] = {o->dx * o->dx, o->dy * o->dy, o->dz * o->dz};
+                    for (int q = 0; q < 6; q++) {
+                        int xn = x + nb[q][0], yn = y + nb[q][1], zn = z + nb[q][2];
+                        if (xn < 0 || yn < 0 || zn < 0 || xn >= o->nx || yn >= o->ny || zn >= o->nz)
+                            continue;
+                        long j = cidx(o, xn, yn, zn);
+                        if (o->ms[j] <= 0) continue;
+                        for (int c = 0; c < 3; c++) h[c] += (m[3 * j + c] - m[3 * i + c]) / d2[q / 2];
+                    }
+                    double pre = 2.0 * o->Aex / o->ms[i];
+                    for (int c = 0; c < 3; c++) h[c] *= pre;
+                }
+                for (int c = 0; c < 3; c++) B[3 * i + c] = h[c];
+            }
+}
+
+// Uniaxial anisotropy (Sec. 2.1 term list): B = 2 Ku / Ms (m.u) u.
+static void anis_field(const oracle* o, const double* m, double* B) {
+    for (long i = 0; i < o->n; i++) {
+        double mu = m[3 * i] * o->u[0] + m[3 * i + 1] * o->u[1] + m[3 * i + 2] * o->u[2];
+        double pre = o->ms[i] > 0 ? 2.0 * o->Ku / o->ms[i] * mu : 0.0;
+        for (int c = 0; c < 3; c++) B[3 * i + c] = pre * o->u[c];
+    }
+}
+
+// X = V_c sum_i Ms_i m_i . B_rms,i  -- the coupling-weighted magnetisation
+// that drives the cavity (Eq. gammafinal integrand times V_c).
+static double cavity_X(const oracle* o, const double* m) {
+    double s = 0;
+    for (long i = 0; i < o->n; i++)
+        s += o->ms[i] * (m[3 * i] * o->brms[3 * i] + m[3 * i + 1] * o->brms[3 * i + 1] +
+                         m[3 * i + 2] * o->brms[3 * i + 2]);
+    return o->vc * s;
+}
+
+// Gamma(t) from the P-mode accumulators, Eq. (gammadiscretefinal), with
+// x0 = 2 Re alpha0, p0 = -2 Im alpha0 and S, C already carrying V_c.
+static double gamma_P(const oracle* o, double tc) {
+    double e = std::exp(-o->kappa * tc);
+    return e * std::cos(o->wc * tc) * (o->x0 - 2.0 * o->S / o->hbar) -
+           e * std::sin(o->wc * tc) * (o->p0 - 2.0 * o->C / o->hbar);
+}
+
+// Total effective field B_eff' = B_ext + B_demag + B_exch + B_anis + B_rms*Gamma
+// (Sec. 2.1 term list and Eq. bcav).
+static void total_field(const oracle* o, const double* m, double Gamma, double* B) {
+    std::vector<double> t1(3 * o->n), t2(3 * o->n);
+    demag_field(o, m, B);
+    exchange_field(o, m, t1.data());
+    anis_field(o, m, t2.data());
+    for (long i = 0; i < o->n; i++)
+        for (int c = 0; c < 3; c++) {
+            double b = B[3 * i + c] + t1[3 * i + c] + t2[3 * i + c] + o->bext[c];
+            if (o->cav_on) b += o->brms[3 * i + c] * Gamma;
+            B[3 * i + c] = b;
+        }
+}
+
+// LLG torque, Eq. (llg): dm/dt = -gamma/(1+alpha^2) [m x B + alpha m x (m x B)].
+static void llg_rhs(const oracle* o, const double* m, const double* B, double* dm) {
+    double pre = -o->gamma / (1.0 + o->alpha * o->alpha);
+    for (long i = 0; i < o->n; i++) {
+        const double* v = m + 3 * i;
+        const double* b = B + 3 * i;
+        double mxb[3] = {v[1] * b[2] - v[2] * b[1], v[2] * b[0] - v[0] * b[2], v[0] * b[1] - v[1] * b[0]};
+        double mxmxb[3] = {v[1] * mxb[2] - v[2] * mxb[1], v[2] * mxb[0] - v[0] * mxb[2],
+                           v[0] * mxb[1] - v[1] * mxb[0]};
+        for (int c = 0; c < 3; c++)
+            dm[3 * i + c] = o->ms[i] > 0 ? pre * (mxb[c] + o->alpha * mxmxb[c]) : 0.0;
+    }
+}
+
+// Full right-hand side at cavity time tc.  E-mode: Gamma = 2 Re(alpha) and
+// d(alpha)/dt = -(kappa + i omega_c) alpha + i X / hbar (Eq. eqmotionaclasical
+// with omega_c -> omega_c - i kappa; the spin operator is S = -Ms m V_c/gamma,
+// Sec. 2.1).  P-mode: Gamma from the accumulators, alpha not integrated.
+static void rhs(const oracle* o, const double* m, cplx a, double tc, double* dm, cplx* da,
+                double* Xout) {
+    double Gamma = 0;
+    if (o->cav_on) Gamma = (o->cav_mode == OR_CAV_E) ? 2.0 * a.real() : gamma_P(o, tc);
+    std::vector<double> B(3 * o->n);
+    total_field(o, m, Gamma, B.data());
+    llg_rhs(o, m, B.data(), dm);
+    double X = o->cav_on ? cavity_X(o, m) : 0.0;
+    if (Xout) *Xout = X;
+    if (da) {
+        if (o->cav_on && o->cav_mode == OR_CAV_E)
+            *da = -cplx(o->kappa, o->wc) * a + cplx(0.0, X / o->hbar);
+        else
+            *da = 0;
+    }
+}
+
+static void normalise(const oracle* o, double* m) {
+    for (long i = 0; i < o->n; i++) {
+        if (o->ms[i] <= 0) { m[3 * i] = m[3 * i + 1] = m[3 * i + 2] = 0; continue; }
+        double r = std::sqrt(m[3 * i] * m[3 * i] + m[3 * i + 1] * m[3 * i + 1] + m[3 * i + 2] * m[3 * i + 2]);
+        if (r > 0) for (int c = 0; c < 3; c++) m[3 * i + c] /= r;
+    }
+}
+
+// P-mode: fold the newly accepted point t_n = t_{n-1} + dt into S and C
+// (right-endpoint rectangle rule of Eq. Sdiscrete / Eq. Cdiscrete, S_0 = C_0 = 0,
+// nothing is added at t_0).  X is taken at the accepted, renormalised m(t_n).
+// Every stage of the following step then sees these S_n, C_n through
+// Eq. (gammadiscretefinal) at its own stage time.
+static void after_accept(oracle* o, double dt) {
+    o->t += dt;
+    o->tcav += dt;
+    o->n_acc++;
+    o->dt_hist.push_back(dt);
+    if (o->cav_on && o->cav_mode == OR_CAV_P) {
+        double X = cavity_X(o, o->m.data());
+        double tc = o->tcav;
+        double e = std::exp(o->kappa * tc);
+        o->S += e * std::sin(o->wc * tc) * X * dt;
+        o->C += e * std::cos(o->wc * tc) * X * dt;
+    }
+}
+
+// Classic RK4 on (m, alpha); m renormalised at the end of the step only.
+static void step_rk4(oracle* o, double dt) {
+    long n3 = 3 * o->n;
+    std::vector<double> k[4], tmp(n3);
+    cplx ka[4];
+    for (int s = 0; s < 4; s++) k[s].resize(n3);
+    const double c[4] = {0.0, 0.5, 0.5, 1.0};
+    for (int s = 0; s < 4; s++) {
+        cplx as = o->a;
+        if (s == 0) {
+            for (long q = 0; q < n3; q++) tmp[q] = o->m[q];
+        } else {
+            for (long q = 0; q < n3; q++) tmp[q] = o->m[q] + c[s] * dt * k[s - 1][q];
+            as = o->a + c[s] * dt * ka[s - 1];
+        }
+        rhs(o, tmp.data(), as, o->tcav + c[s] * dt, k[s].data(), &ka[s], nullptr);
+    }
+    for (long q = 0; q < n3; q++)
+        o->m[q] += dt / 6.0 * (k[0][q] + 2.0 * k[1][q] + 2.0 * k[2][q] + k[3][q]);
+    o->a += dt / 6.0 * (ka[0] + 2.0 * ka[1] + 2.0 * ka[2] + ka[3]);
+    normalise(o, o->m.data());
+    after_accept(o, dt);
+}
+
+// Dormand & Prince (1980) RK5(4) coefficients.
+static const double DP_C[7] = {0.0, 1.0 / 5, 3.0 / 10, 4.0 / 5, 8.0 / 9, 1.0, 1.0};
+static const double DP_A[7][6] = {
+    {0, 0, 0, 0, 0, 0},
+    {1.0 / 5, 0, 0, 0, 0, 0},
+    {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
+    {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0},
+    {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0},
+    {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0},
+    {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}};
+static const double DP_B5[7] = {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84, 0};
+static const double DP_B4[7] = {5179.0 / 57600, 0, 7571.0 / 16695, 393.0 / 640,
+                                -92097.0 / 339200, 187.0 / 2100, 1.0 / 40};
+
+// One Dormand-Prince attempt of length dt.  The 5th-order solution is
+// renormalised, the 7th stage is evaluated there, and the error is
+// max_i |m5_i - m4_i| over cells (m5 before renormalisation).  If force is
+// set the step is accepted regardless (replay of a recorded dt sequence).
+static int step_dp45(oracle* o, double dt, int force, double* err_out) {
+    long n3 = 3 * o->n;
+    std::vector<double> k[7], tmp(n3), m5(n3), m4(n3);
+    cplx ka[7];
+    for (int s = 0; s < 7; s++) k[s].resize(n3);
+    cplx a5 = o->a;
+    for (int s = 0; s < 7; s++) {
+        cplx as = o->a;
+        if (s < 6) {
+            for (long q = 0; q < n3; q++) {
+                double v = o->m[q];
+                for (int j = 0; j < s; j++) v += dt * DP_A[s][j] * k[j][q];
+                tmp[q] = v;
+            }
+            for (int j = 0; j < s; j++) as += dt * DP_A[s][j] * ka[j];
+        } else {
+            for (long q = 0; q < n3; q++) {
+                double v = o->m[q];
+                for (int j = 0; j < 6; j++) v += dt * DP_B5[j] * k[j][q];
+                m5[q] = v;
+                tmp[q] = v;
+            }
+            normalise(o, tmp.data());
+            for (int j = 0; j < 6; j++) as += dt * DP_B5[j] * ka[j];
+            a5 = as;
+        }
+        rhs(o, tmp.data(), as, o->tcav + DP_C[s] * dt, k[s].data(), &ka[s], nullptr);
+    }
+    double err = 0;
+    for (long i = 0; i < o->n; i++) {
+        double e2 = 0;
+        for (int c = 0; c < 3; c++) {
+            double v4 = o->m[3 * i + c];
+            for (int j = 0; j < 7; j++) v4 += dt * DP_B4[j] * k[j][3 * i + c];
+            double d = m5[3 * i + c] - v4;
+            e2 += d * d;
+        }
+        err = std::fmax(err, std::sqrt(e2));
+    }
+    if (err_out) *err_out = err;
+    int accept = force || err <= o->tol;
+    if (accept) {
+        std::vector<double> mn = m5;
+        normalise(o, mn.data());
+        o->m = mn;
+        o->a = a5;
+        after_accept(o, dt);
+    } else {
+        o->n_rej++;
+    }
+    return accept;
+}
+
+// Step-size controller for the adaptive integrator.
+static double dp_next_dt(double dt, double err, double tol) {
+    double f = err > 0 ? 0.9 * std::pow(tol / err, 0.2) : 5.0;
+    if (f > 5.0) f = 5.0;
+    if (f < 0.2) f = 0.2;
+    return dt * f;
+}
+
+extern "C" {
+
+// ---- tensor entry points ---------------------------------------------------
+void or_newell(double X, double Y, double Z, double dx, double dy, double dz, double* out) {
+    newell_t<double>(X, Y, Z, dx, dy, dz, out);
+}
+void or_newell_ld(double X, double Y, double Z, double dx, double dy, double dz, double* out) {
+    long double o[6];
+    newell_t<long double>(X, Y, Z, dx, dy, dz, o);
+    for (int i = 0; i < 6; i++) out[i] = (double)o[i];
+}
+void or_dipole(double X, double Y, double Z, double V, double* out) { dipole_tensor(X, Y, Z, V, out); }
+void or_demag_tensor(double X, double Y, double Z, double dx, double dy, double dz, double* out) {
+    demag_tensor(X, Y, Z, dx, dy, dz, out);
+}
+double or_r_switch(void) { return OR_R_SWITCH; }
+double or_aharoni_dz(double a, double b, double c) { return aharoni_dz(a, b, c); }
+void or_fft3d(double* re_im, int px, int py, int pz, int sign) {
+    fft3d(reinterpret_cast<cplx*>(re_im), px, py, pz, sign);
+}
+
+// ---- simulation handle -----------------------------------------------------
+oracle* or_create(int nx, int ny, int nz, double dx, double dy, double dz, double Ms, double Aex,
+                  double alpha, double Ku, const double* u, double gamma, double mu0, double hbar,
+                  int demag) {
+    if (nx < 1 || ny < 1 || nz < 1) return nullptr;
+    oracle* o = new oracle();
+    o->nx = nx; o->ny = ny; o->nz = nz;
+    o->n = (long)nx * ny * nz;
+    o->dx = dx; o->dy = dy; o->dz = dz; o->vc = dx * dy * dz;
+    o->Aex = Aex; o->alpha = alpha; o->Ku = Ku;
+    double un = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    for (int c = 0; c < 3; c++) o->u[c] = un > 0 ? u[c] / un : 0.0;
+    o->gamma = gamma; o->mu0 = mu0; o->hbar = hbar;
+    o->ms.assign(o->n, Ms);
+    o->m.assign(3 * o->n, 0.0);
+    for (long i = 0; i < o->n; i++) o->m[3 * i] = 1.0;
+    o->bext[0] = o->bext[1] = o->bext[2] = 0;
+    o->cav_on = 0; o->wc = o->kappa = o->x0 = o->p0 = 0;
+    o->brms.assign(3 * o->n, 0.0);
+    o->cav_mode = OR_CAV_E;
+    o->a = 0; o->S = o->C = 0; o->t = o->tcav = 0;
+    o->kind = OR_RK4; o->tol = 1e-6; o->dt_next = 0;
+    o->n_acc = o->n_rej = 0;
+    o->demag = demag;
+    if (demag == OR_DEMAG_DIRECT) {
+        int ox = 2 * nx - 1, oy = 2 * ny - 1, oz = 2 * nz - 1;
+        o->Nreal.resize((size_t)ox * oy * oz * 6);
+#pragma omp parallel for collapse(3) schedule(dynamic)
+        for (int k = 0; k < oz; k++)
+            for (int j = 0; j < oy; j++)
+                for (int i = 0; i < ox; i++)
+                    demag_tensor((i - nx + 1) * dx, (j - ny + 1) * dy, (k - nz + 1) * dz, dx, dy, dz,
+                                 &o->Nreal[(((size_t)k * oy + j) * ox + i) * 6]);
+    } else if (demag == OR_DEMAG_FFT) {
+        o->px = pow2_at_least(2 * nx - 1);
+        o->py = pow2_at_least(2 * ny - 1);
+        o->pz = pow2_at_least(2 * nz - 1);
+        size_t P = (size_t)o->px * o->py * o->pz;
+        o->Nhat.assign(6 * P, cplx(0, 0));
+        // Real-space tensor on the padded grid; index i maps to offset i for
+        // i < n and to i - p for i > p - n (wrap-around of the cyclic
+        // convolution); other indices are never reached and stay zero.
+#pragma omp parallel for collapse(3) schedule(dynamic)
+        for (int k = 0; k < o->pz; k++)
+            for (int j = 0; j < o->py; j++)
+                for (int i = 0; i < o->px; i++) {
+                    int X = i < nx ? i : (i > o->px - nx ? i - o->px : 1 << 30);
+                    int Y = j < ny ? j : (j > o->py - ny ? j - o->py : 1 << 30);
+                    int Z = k < nz ? k : (k > o->pz - nz ? k - o->pz : 1 << 30);
+                    if (X == 1 << 30 || Y == 1 << 30 || Z == 1 << 30) continue;
+                    double N[6];
+                    demag_tensor(X * dx, Y * dy, Z * dz, dx, dy, dz, N);
+                    size_t p = ((size_t)k * o->py + j) * o->px + i;
+                    for (int c = 0; c < 6; c++) o->Nhat[c * P + p] = N[c];
+                }
+        for (int c = 0; c < 6; c++) fft3d(&o->Nhat[c * P], o->px, o->py, o->pz, -1);
+    }
+    return o;
+}
+
+void or_destroy(oracle* o) { delete o; }
+long or_ncells(const oracle* o) { return o->n; }
+void or_pad_sizes(const oracle* o, int* out) { out[0] = o->px; out[1] = o->py; out[2] = o->pz; }
+
+void or_set_ms(oracle* o, const double* ms) {
+    for (long i = 0; i < o->n; i++) o->ms[i] = ms[i] > 0 ? ms[i] : 0.0;
+    normalise(o, o->m.data());
+}
+void or_set_m(oracle* o, const double* m) {
+    std::memcpy(o->m.data(), m, sizeof(double) * 3 * o->n);
+    normalise(o, o->m.data());
+}
+void or_get_m(const oracle* o, double* m) { std::memcpy(m, o->m.data(), sizeof(double) * 3 * o->n); }
+void or_set_bias(oracle* o, const double* B) { for (int c = 0; c < 3; c++) o->bext[c] = B[c]; }
+
+// Cavity set-up (Sec. 3.2 built-ins B_rms, Wc, Kappa).  With profile_is_brms
+// the profile is B_rms in tesla.  Otherwise B_rms,i = s * profile_i with
+// s = g sqrt(2 hbar / (gamma V_c sum_i Ms_i)), the macrospin relation
+// g = B_rms sqrt(gamma Ms V / (2 hbar)) obtained by matching the linearised
+// equations of motion to the normal-phase polariton formula
+// (Eq. dickepolaritons with the Dicke mapping of Sec. 4).  A null profile
+// means a uniform unit vector along +y.
+void or_set_cavity(oracle* o, double wc, double kappa, double g, const double* profile,
+                   int profile_is_brms) {
+    o->cav_on = 1; o->wc = wc; o->kappa = kappa;
+    double s = 1.0;
+    if (!profile_is_brms) {
+        double sm = 0;
+        for (long i = 0; i < o->n; i++) sm += o->ms[i];
+        s = sm > 0 ? g * std::sqrt(2.0 * o->hbar / (o->gamma * o->vc * sm)) : 0.0;
+    }
+    for (long i = 0; i < o->n; i++)
+        for (int c = 0; c < 3; c++) {
+            double p = profile ? profile[3 * i + c] : (c == 1 ? 1.0 : 0.0);
+            o->brms[3 * i + c] = s * p;
+        }
+    o->tcav = 0; o->S = o->C = 0;
+    o->a = cplx(0.5 * o->x0, -0.5 * o->p0);
+}
+void or_get_brms(const oracle* o, double* out) { std::memcpy(out, o->brms.data(), sizeof(double) * 3 * o->n); }
+// x0 = 2 Re alpha0, p0 = -2 Im alpha0 (Sec. 3.2 built-ins X0, P0).
+void or_set_cavity_init(oracle* o, double x0, double p0) {
+    o->x0 = x0; o->p0 = p0;
+    o->a = cplx(0.5 * x0, -0.5 * p0);
+}
+// ResetMemoryTerm(): the current state becomes the cavity's t = 0.
+void or_reset_cavity(oracle* o) {
+    o->tcav = 0; o->S = o->C = 0;
+    o->a = cplx(0.5 * o->x0, -0.5 * o->p0);
+}
+void or_disable_cavity(oracle* o) { o->cav_on = 0; }
+void or_set_integrator(oracle* o, int kind, double tol, int mode) {
+    o->kind = kind; o->tol = tol; o->cav_mode = mode;
+}
+
+// RK4: n steps of dt.  DP45: n attempts; dt > 0 sets the next trial step.
+long or_step(oracle* o, long n, double dt) {
+    long acc = 0;
+    if (o->kind == OR_RK4) {
+        for (long s = 0; s < n; s++) { step_rk4(o, dt); acc++; }
+        return acc;
+    }
+    if (dt > 0) o->dt_next = dt;
+    for (long s = 0; s < n; s++) {
+        double err;
+        double h = o->dt_next;
+        int ok = step_dp45(o, h, 0, &err);
+        acc += ok;
+        o->dt_next = dp_next_dt(h, err, o->tol);
+    }
+    return acc;
+}
+// DP45 replay: accept each given step length in turn (no controller).
+void or_replay(oracle* o, const double* dts, long n) {
+    for (long s = 0; s < n; s++) step_dp45(o, dts[s], 1, nullptr);
+}
+double or_last_error(oracle* o, double dt) {
+    // error estimate of an attempt of length dt from the current state,
+    // without changing the state
+    oracle copy = *o;
+    double err;
+    step_dp45(&copy, dt, 0, &err);
+    return err;
+}
+long or_dt_history(const oracle* o, double* out, long max) {
+    long n = (long)o->dt_hist.size();
+    if (out) for (long i = 0; i < n && i < max; i++) out[i] = o->dt_hist[i];
+    return n;
+}
+
+// out = {t, t_cav, Re alpha, Im alpha, |alpha|^2, Gamma, S, C, X, dt_next,
+//        n_accepted, n_rejected}.  In P-mode alpha is reconstructed from the
+// accumulators: alpha(t) = e^{-(kappa + i omega_c) t}[alpha0 - S/hbar + i C/hbar]
+// (Sec. 2.2, a-posteriori photon amplitude).
+void or_get_cavity(const oracle* o, double* out) {
+    double X = o->cav_on ? cavity_X(o, o->m.data()) : 0.0;
+    cplx a = o->a;
+    double G = 2.0 * a.real();
+    if (o->cav_on && o->cav_mode == OR_CAV_P) {
+        cplx a0(0.5 * o->x0, -0.5 * o->p0);
+        a = std::exp(-cplx(o->kappa, o->wc) * o->tcav) * (a0 + cplx(-o->S / o->hbar, o->C / o->hbar));
+        G = gamma_P(o, o->tcav);
+    }
+    out[6] = o->S; out[7] = o->C;
+    out[0] = o->t; out[1] = o->tcav; out[2] = a.real(); out[3] = a.imag(); out[4] = std::norm(a);
+    out[5] = o->cav_on ? G : 0.0; out[8] = X; out[9] = o->dt_next;
+    out[10] = (double)o->n_acc; out[11] = (double)o->n_rej;
+}
+
+void or_set_alpha(oracle* o, double re, double im) { o->a = cplx(re, im); }
+
+// ---- single evaluations for pins and sampled parity --------------------------
+void or_demag(const oracle* o, const double* m, double* B) { demag_field(o, m, B); }
+void or_exchange(const oracle* o, const double* m, double* B) { exchange_field(o, m, B); }
+void or_anis(const oracle* o, const double* m, double* B) { anis_field(o, m, B); }
+void or_field(const oracle* o, const double* m, double Gamma, double* B) { total_field(o, m, Gamma, B); }
+void or_rhs(const oracle* o, const double* m, double are, double aim, double tc, double* dm,
+            double* da) {
+    cplx d;
+    rhs(o, m, cplx(are, aim), tc, dm, &d, nullptr);
+    da[0] = d.real(); da[1] = d.imag();
+}
+double or_cavity_X(const oracle* o, const double* m) { return cavity_X(o, m); }
+
+// Demag field at a list of cells by the direct sum, with the tensor evaluated
+// on the fly (no table): usable on grids far too large for the O(N^2) table.
+void or_demag_at(const oracle* o, const double* m, const long* cells, long nc, double* B) {
+#pragma omp parallel for schedule(dynamic)
+    for (long q = 0; q < nc; q++) {
+        long i = cells[q];
+        int xi = (int)(i % o->nx), yi = (int)((i / o->nx) % o->ny), zi = (int)(i / ((long)o->nx * o->ny));
+        double h[3] = {0, 0, 0};
+        for (int zj = 0; zj < o->nz; zj++)
+            for (int yj = 0; yj < o->ny; yj++)
+                for (int xj = 0; xj < o->nx; xj++) {
+                    long j = cidx(o, xj, yj, zj);
+                    if (o->ms[j] <= 0) continue;
+                    double N[6];
+                    demag_tensor((xi - xj) * o->dx, (yi - yj) * o->dy, (zi - zj) * o->dz, o->dx, o->dy,
+                                 o->dz, N);
+                    double M[3] = {o->ms[j] * m[3 * j], o->ms[j] * m[3 * j + 1], o->ms[j] * m[3 * j + 2]};
+                    h[0] += N[0] * M[0] + N[3] * M[1] + N[4] * M[2];
+                    h[1] += N[3] * M[0] + N[1] * M[1] + N[5] * M[2];
+                    h[2] += N[4] * M[0] + N[5] * M[1] + N[2] * M[2];
+                }
+        for (int c = 0; c < 3; c++) B[3 * q + c] = -o->mu0 * h[c];
+    }
+}
+
+// Energy terms (J): {Zeeman, demag, exchange, anisotropy, cavity coupling,
+// photon, total}.  The cavity pair is -X * 2Re(alpha) and hbar omega_c |alpha|^2,
+// from the Hamiltonian Eq. (startH) with S = -Ms m V_c / gamma.
+void or_energy(const oracle* o, double* out) {
+    long n = o->n;
+    std::vector<double> Bd(3 * n), Bx(3 * n);
+    demag_field(o, o->m.data(), Bd.data());
+    exchange_field(o, o->m.data(), Bx.data());
+    double ez = 0, ed = 0, ex = 0, ea = 0;
+    for (long i = 0; i < n; i++) {
+        const double* v = &o->m[3 * i];
+        double w = o->ms[i] * o->vc;
+        ez -= w * (v[0] * o->bext[0] + v[1] * o->bext[1] + v[2] * o->bext[2]);
+        ed -= 0.5 * w * (v[0] * Bd[3 * i] + v[1] * Bd[3 * i + 1] + v[2] * Bd[3 * i + 2]);
+        ex -= 0.5 * w * (v[0] * Bx[3 * i] + v[1] * Bx[3 * i + 1] + v[2] * Bx[3 * i + 2]);
+        if (o->ms[i] > 0) {
+            double mu = v[0] * o->u[0] + v[1] * o->u[1] + v[2] * o->u[2];
+            ea -= o->Ku * o->vc * mu * mu;
+        }
+    }
+    double ec = 0, ep = 0;
+    if (o->cav_on) {
+        double X = cavity_X(o, o->m.data());
+        ec = -X * 2.0 * o->a.real();
+        ep = o->hbar * o->wc * std::norm(o->a);
+    }
+    out[0] = ez; out[1] = ed; out[2] = ex; out[3] = ea; out[4] = ec; out[5] = ep;
+    out[6] = ez + ed + ex + ea + ec + ep;
+}
+
+}  // extern "C"
