@@ -1,0 +1,198 @@
+/*
+ * mmcq.h -- C ABI of the GB300 (sm_103a) library for the LLG + cavity-QED hot
+ * path of Mumax3-cQED (arXiv 2410.00966).
+ *
+ * One handle holds `batch` independent instances that share a grid, a cell
+ * size, the material constants, the per-cell Ms map and the coupling-profile
+ * shape; each instance has its own magnetisation, bias field, cavity
+ * (omega_c, kappa, g, x0, p0) and integrator state (time, step size,
+ * accept/reject counters).  Every step runs on the GPU: the zero-padded FFT
+ * demag convolution, exchange, anisotropy, Zeeman, the cavity field
+ * B_rms * Gamma(t) from an FP64 reduction of the coupling-weighted
+ * magnetisation, the LLG torque and the RK4 / Dormand-Prince update with |m|
+ * renormalisation.  Nothing of the step runs on the host.
+ *
+ * Conventions for every call:
+ *   - Return 0 (MMCQ_OK) or a negative MMCQ_ERR_* code; no exception crosses
+ *     the ABI.  mmcq_last_error() gives a one-line message for the handle.
+ *   - Arrays are row-major with x fastest: cell i = (z * ny + y) * nx + x.
+ *     Vector arrays are N x 3 float (x, y, z components interleaved).
+ *   - `where` = MMCQ_HOST (host pointer, caller-owned, copied before the call
+ *     returns) or MMCQ_DEVICE (device pointer on the handle's device; the copy
+ *     is ordered on the handle's stream and has completed when the call returns).
+ *   - `inst` selects one instance (0 <= inst < batch); -1 means all instances
+ *     where the call says so.
+ *   - Stepping is enqueued on the handle's stream and returns without waiting;
+ *     errors detected on the device (non-finite values, step-size underflow)
+ *     are reported by the next call that synchronises (mmcq_sync, mmcq_get_*).
+ *   - A handle is not thread-safe; distinct handles are independent.
+ *   - Units are SI: m, s, T, A/m, J/m, J/m^3, rad/s.
+ */
+#ifndef MMCQ_H
+#define MMCQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mmcq mmcq_t;
+
+enum {
+    MMCQ_OK = 0,
+    MMCQ_ERR_ARG = -1,         /* invalid argument (sizes, pointers, indices) */
+    MMCQ_ERR_UNSUPPORTED = -2, /* valid request this build does not handle (e.g. padded size > 4096) */
+    MMCQ_ERR_CUDA = -3,        /* a CUDA runtime call failed; see mmcq_last_error */
+    MMCQ_ERR_NUMERIC = -4,     /* non-finite m / field, or adaptive step underflow */
+    MMCQ_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+    MMCQ_ERR_STATE = -6        /* call not valid in the current state */
+};
+
+enum { MMCQ_HOST = 0, MMCQ_DEVICE = 1 };
+enum { MMCQ_RK4 = 0, MMCQ_DP45 = 1 };
+enum { MMCQ_CAVITY_E = 0, MMCQ_CAVITY_P = 1 };
+
+/* field-term selection for mmcq_eval_field */
+enum {
+    MMCQ_TERM_DEMAG = 1,
+    MMCQ_TERM_EXCHANGE = 2,
+    MMCQ_TERM_ANIS = 4,
+    MMCQ_TERM_ZEEMAN = 8,
+    MMCQ_TERM_CAVITY = 16,
+    MMCQ_TERM_ALL = 31
+};
+
+typedef struct {
+    int nx, ny, nz;        /* cells per axis, >= 1 */
+    double dx, dy, dz;     /* cell size (m), > 0 */
+    int batch;             /* instances sharing this grid, >= 1 */
+} mmcq_grid;
+
+/* Device-memory hooks: when alloc is non-NULL every device buffer of the
+ * handle is obtained from alloc(bytes, ctx) (256-byte aligned) and released
+ * with free(ptr, ctx) at mmcq_destroy; otherwise cudaMalloc / cudaFree. */
+typedef void* (*mmcq_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*mmcq_free_fn)(void* ptr, void* ctx);
+
+typedef struct {
+    double gamma;          /* gyromagnetic ratio rad/(s T); 0 -> 1.7595e11 */
+    double mu0;            /* vacuum permeability; 0 -> 4 pi 1e-7 */
+    double hbar;           /* 0 -> 1.05457182e-34 (the paper's HBAR default, Sec. 3.2) */
+    int device;            /* CUDA device ordinal */
+    void* stream;          /* cudaStream_t to enqueue on; NULL -> a stream owned by the handle */
+    mmcq_alloc_fn alloc;   /* optional device allocator */
+    mmcq_free_fn free;
+    void* alloc_ctx;
+} mmcq_opts;
+
+typedef struct {
+    double t;              /* simulated time of the instance (s) */
+    double t_cav;          /* time since the cavity was set or reset (s) */
+    double re_alpha, im_alpha; /* photon amplitude alpha = <a> (Sec. 2.2) */
+    double n_photon;       /* |alpha|^2 */
+    double Gamma;          /* memory factor Gamma(t_cav), Eq. (gammafinal) */
+    double S, C;           /* P-mode accumulators (J s, include V_c), Eq. (Sdiscrete, Cdiscrete) */
+    double X;              /* V_c sum_i Ms_i m_i . B_rms,i at the current m (J) */
+    double dt;             /* next trial step (DP45) or last step (RK4) */
+    int64_t accepted, rejected;
+} mmcq_cavity;
+
+typedef struct {
+    int px, py, pz;            /* padded FFT sizes */
+    int tile;                  /* kx columns per spectrum tile */
+    size_t device_bytes;       /* device memory held by the handle */
+    double setup_ms;           /* demag-tensor set-up time */
+    int64_t launches_per_step; /* kernels launched by one RK4 step / one DP45 attempt */
+} mmcq_info;
+
+/* Create a handle: allocate device state and compute the demag kernel.
+ * The demag tensor is the Newell, Williams & Dunlop (1993) cell-averaged
+ * tensor within 16 largest-cell-edges and the point dipole beyond, evaluated
+ * in FP64 on the device and transformed with an FP64 FFT on the padded grid;
+ * the paper lists B_demag among the field terms (Sec. 2.1) without giving a
+ * method.  Ms (A/m), Aex (J/m), alpha (Gilbert damping, Eq. llg), Ku (J/m^3)
+ * and axis (normalised here) are shared by all instances.  Initial state:
+ * m = +x, uniform Ms, zero bias, cavity off, RK4, E-mode.
+ * Errors: MMCQ_ERR_ARG (null/invalid), MMCQ_ERR_UNSUPPORTED (padded size
+ * > 4096 on an axis), MMCQ_ERR_CUDA. On error *h is set to NULL. */
+int mmcq_create(mmcq_t** h, const mmcq_grid* g, double Ms, double Aex, double alpha, double Ku,
+                const double axis[3], const mmcq_opts* opts);
+void mmcq_destroy(mmcq_t* h);
+const char* mmcq_last_error(const mmcq_t* h);
+int mmcq_info_get(mmcq_t* h, mmcq_info* out);
+
+/* Per-cell saturation magnetisation (A/m), shared by all instances; 0 marks
+ * empty cells (geometry mask).  Ms enters the cavity sum as M_{s,i}
+ * (Eq. gammafinal).  N floats.  Cells that become empty get m = 0. */
+int mmcq_set_ms_map(mmcq_t* h, const float* ms, int where);
+
+/* Uniform Zeeman field B_ext (T) of one instance or all (inst = -1), Sec. 2.1. */
+int mmcq_set_bias(mmcq_t* h, int inst, const double B[3]);
+
+/* Magnetisation of one instance or of all (inst = -1: the same N x 3 array
+ * for every instance).  Normalised on entry (FP64), zero in empty cells.
+ * Invalidates the first-same-as-last stage of the adaptive integrator. */
+int mmcq_set_m(mmcq_t* h, int inst, const float* m, int where);
+int mmcq_get_m(mmcq_t* h, int inst, float* out, int where);
+
+/* Single-mode cavity of one instance or all (inst = -1): Sec. 3.2 built-ins
+ * Wc (omega_c, rad/s), Kappa (kappa, rad/s) and B_rms.  The cavity field is
+ * B_cav,i = B_rms,i Gamma(t) (Eq. bcav).
+ *   profile: N x 3 host floats shared by the whole batch, or NULL to keep the
+ *            current shape (initially the uniform unit vector +y).
+ *   profile_is_brms = 1: profile is B_rms in tesla, g is ignored.
+ *   profile_is_brms = 0: profile is a dimensionless shape p_i and
+ *            B_rms,i = g sqrt(2 hbar / (gamma V_c sum_i Ms_i)) p_i, the
+ *            macrospin relation g = B_rms sqrt(gamma Ms V / (2 hbar)) obtained
+ *            by matching the linearised equations of motion to the normal-phase
+ *            polariton formula (Eq. dickepolaritons, Sec. 4).
+ * Sets t_cav = 0, S = C = 0, alpha = alpha0 and enables the cavity
+ * (CavityFeatureStatus = 1 in the paper's terms). */
+int mmcq_set_cavity(mmcq_t* h, int inst, double omega_c, double kappa, double g, const float* profile,
+                    int profile_is_brms);
+/* x0 = 2 Re alpha0, p0 = -2 Im alpha0 (Sec. 3.2 built-ins X0, P0; the paper's
+ * wording after Eq. gammadiscretefinal is read with alpha0). Resets alpha. */
+int mmcq_set_cavity_init(mmcq_t* h, int inst, double x0, double p0);
+/* ResetMemoryTerm() (Sec. 3.2): t_cav := 0, S = C = 0, alpha := alpha0. */
+int mmcq_reset_cavity(mmcq_t* h, int inst);
+int mmcq_disable_cavity(mmcq_t* h, int inst);
+
+/* kind: MMCQ_RK4 (classic, fixed step) or MMCQ_DP45 (Dormand-Prince 5(4),
+ * adaptive: error = max_i |m5_i - m4_i|, accept if <= tol, next step
+ * dt * clamp(0.9 (tol/err)^(1/5), 0.2, 5)); m is renormalised after each
+ * accepted step.  cavity_mode: MMCQ_CAVITY_E integrates alpha with the same
+ * tableau (exact memory integral, Appendix A); MMCQ_CAVITY_P uses the paper's
+ * recursive accumulators S_n, C_n (Eq. Sdiscrete, Cdiscrete) folded in after
+ * each accepted step and Gamma from Eq. (gammadiscretefinal) at every stage. */
+int mmcq_set_integrator(mmcq_t* h, int kind, double tol, int cavity_mode);
+
+/* Optional end time per instance (or all, inst = -1) for the adaptive
+ * integrator: steps are clipped to land on t_end and further attempts are
+ * skipped.  t_end <= 0 removes the limit. */
+int mmcq_set_horizon(mmcq_t* h, int inst, double t_end);
+
+/* Advance every instance.  RK4: n steps of dt.  DP45: n attempts; dt > 0
+ * sets the next trial step of every instance.  Asynchronous on the stream. */
+int mmcq_step(mmcq_t* h, int64_t n, double dt);
+
+/* Wait for the stream; report device-side errors raised since the last sync. */
+int mmcq_sync(mmcq_t* h);
+
+/* FP64 cavity / integrator read-out of one instance (Sec. 2.2 a-posteriori
+ * photon amplitude; in P-mode alpha is rebuilt from S and C). */
+int mmcq_get_cavity(mmcq_t* h, int inst, mmcq_cavity* out);
+
+/* Accepted step lengths of one instance in order (at most max are copied;
+ * *n receives the total count).  Used to replay adaptive runs. */
+int mmcq_get_dt_history(mmcq_t* h, int inst, double* out, int64_t max, int64_t* n);
+
+/* Effective field (T) of one instance at its current m, with the selected
+ * MMCQ_TERM_* terms (cavity term uses the current Gamma); N x 3 floats. */
+int mmcq_eval_field(mmcq_t* h, int inst, int terms, float* out, int where);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MMCQ_H */

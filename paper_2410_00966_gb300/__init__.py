@@ -1,0 +1,286 @@
+"""Python binding of the mmcq library (GB300 / sm_103a LLG + cavity-QED hot path).
+
+Thin ctypes layer over the C ABI declared in include/mmcq.h: the module-level
+``mmcq_*`` functions are the C entry points with their C names and argument
+lists; ``Sim`` wraps a handle for convenience (numpy arrays are passed as host
+pointers, CUDA torch tensors as device pointers).  Every step of the method
+runs in the library's CUDA kernels; there is no Python or CPU fallback: when
+the shared library is missing the import of the binding fails.
+
+PyTorch, when present, provides device memory (through the allocator hook of
+``mmcq_opts``) and the CUDA stream the library enqueues on.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmmcq.so")
+
+MMCQ_OK = 0
+MMCQ_ERR_ARG, MMCQ_ERR_UNSUPPORTED, MMCQ_ERR_CUDA, MMCQ_ERR_NUMERIC, MMCQ_ERR_TIMEOUT, MMCQ_ERR_STATE = -1, -2, -3, -4, -5, -6
+MMCQ_HOST, MMCQ_DEVICE = 0, 1
+MMCQ_RK4, MMCQ_DP45 = 0, 1
+MMCQ_CAVITY_E, MMCQ_CAVITY_P = 0, 1
+MMCQ_TERM_DEMAG, MMCQ_TERM_EXCHANGE, MMCQ_TERM_ANIS, MMCQ_TERM_ZEEMAN, MMCQ_TERM_CAVITY = 1, 2, 4, 8, 16
+MMCQ_TERM_ALL = 31
+
+_ERRNAMES = {-1: "MMCQ_ERR_ARG", -2: "MMCQ_ERR_UNSUPPORTED", -3: "MMCQ_ERR_CUDA", -4: "MMCQ_ERR_NUMERIC",
+             -5: "MMCQ_ERR_TIMEOUT", -6: "MMCQ_ERR_STATE"}
+
+
+class mmcq_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("batch", ctypes.c_int)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class mmcq_opts(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("mu0", ctypes.c_double), ("hbar", ctypes.c_double),
+                ("device", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
+
+
+class mmcq_cavity(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in
+                ("t", "t_cav", "re_alpha", "im_alpha", "n_photon", "Gamma", "S", "C", "X", "dt")] + \
+               [("accepted", ctypes.c_int64), ("rejected", ctypes.c_int64)]
+
+
+class mmcq_info(ctypes.Structure):
+    _fields_ = [("px", ctypes.c_int), ("py", ctypes.c_int), ("pz", ctypes.c_int), ("tile", ctypes.c_int),
+                ("device_bytes", ctypes.c_size_t), ("setup_ms", ctypes.c_double),
+                ("launches_per_step", ctypes.c_int64)]
+
+
+_H = ctypes.c_void_p
+_FP = ctypes.c_void_p   # float* (host or device)
+_DP = ctypes.POINTER(ctypes.c_double)
+
+PROTOTYPES = {
+    "mmcq_create": (ctypes.c_int, [ctypes.POINTER(_H), ctypes.POINTER(mmcq_grid), ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_double, _DP, ctypes.POINTER(mmcq_opts)]),
+    "mmcq_destroy": (None, [_H]),
+    "mmcq_last_error": (ctypes.c_char_p, [_H]),
+    "mmcq_info_get": (ctypes.c_int, [_H, ctypes.POINTER(mmcq_info)]),
+    "mmcq_set_ms_map": (ctypes.c_int, [_H, _FP, ctypes.c_int]),
+    "mmcq_set_bias": (ctypes.c_int, [_H, ctypes.c_int, _DP]),
+    "mmcq_set_m": (ctypes.c_int, [_H, ctypes.c_int, _FP, ctypes.c_int]),
+    "mmcq_get_m": (ctypes.c_int, [_H, ctypes.c_int, _FP, ctypes.c_int]),
+    "mmcq_set_cavity": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, _FP,
+                                       ctypes.c_int]),
+    "mmcq_set_cavity_init": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
+    "mmcq_reset_cavity": (ctypes.c_int, [_H, ctypes.c_int]),
+    "mmcq_disable_cavity": (ctypes.c_int, [_H, ctypes.c_int]),
+    "mmcq_set_integrator": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_double, ctypes.c_int]),
+    "mmcq_set_horizon": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_double]),
+    "mmcq_step": (ctypes.c_int, [_H, ctypes.c_int64, ctypes.c_double]),
+    "mmcq_sync": (ctypes.c_int, [_H]),
+    "mmcq_get_cavity": (ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(mmcq_cavity)]),
+    "mmcq_get_dt_history": (ctypes.c_int, [_H, ctypes.c_int, _DP, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    "mmcq_eval_field": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, _FP, ctypes.c_int]),
+}
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libmmcq.so and declare its prototypes; raises if it has not been built."""
+    if not os.path.exists(path):
+        raise ImportError(f"mmcq CUDA library not built ({path}); run paper_2410_00966_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in PROTOTYPES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+def __getattr__(name):
+    # module-level mmcq_* names are the C entry points
+    if name in PROTOTYPES:
+        return getattr(lib(), name)
+    raise AttributeError(name)
+
+
+class MMCQError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _TorchAllocator:
+    """Device memory for the library from PyTorch's caching allocator."""
+
+    def __init__(self, device):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.blocks = {}
+        self.c_alloc = ALLOC_FN(self._alloc)
+        self.c_free = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, ctx):
+        try:
+            t = self.torch.empty(int(nbytes), dtype=self.torch.uint8, device=self.device)
+        except Exception:
+            return None
+        p = t.data_ptr()
+        self.blocks[p] = t
+        return p
+
+    def _free(self, p, ctx):
+        self.blocks.pop(p, None)
+
+
+def _ptr(a, n_floats):
+    """(pointer, where, keepalive) for a float32 array: numpy -> host, CUDA tensor -> device."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != torch.float32 or not a.is_contiguous() or a.numel() != n_floats:
+                raise ValueError("expected a contiguous float32 tensor of %d values" % n_floats)
+            return ctypes.c_void_p(a.data_ptr()), (MMCQ_DEVICE if a.is_cuda else MMCQ_HOST), a
+    except ImportError:
+        pass
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    if arr.size != n_floats:
+        raise ValueError("expected %d values, got %d" % (n_floats, arr.size))
+    return ctypes.c_void_p(arr.ctypes.data), MMCQ_HOST, arr
+
+
+class Sim:
+    """A handle of `batch` instances on an nx*ny*nz grid (see include/mmcq.h)."""
+
+    def __init__(self, nx, ny, nz, dx, dy, dz, Ms, Aex, alpha, Ku=0.0, axis=(1.0, 0.0, 0.0), batch=1,
+                 gamma=0.0, mu0=0.0, hbar=0.0, device=0, use_torch=True):
+        self._lib = lib()
+        self.shape = (nz, ny, nx)
+        self.n = nx * ny * nz
+        self.batch = batch
+        g = mmcq_grid(nx, ny, nz, dx, dy, dz, batch)
+        o = mmcq_opts()
+        o.gamma, o.mu0, o.hbar, o.device = gamma, mu0, hbar, device
+        self._alloc = None
+        self.stream = None
+        if use_torch:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    dev = torch.device("cuda", device)
+                    self._alloc = _TorchAllocator(dev)
+                    o.alloc, o.free = self._alloc.c_alloc, self._alloc.c_free
+                    self.stream = torch.cuda.current_stream(dev)
+                    o.stream = ctypes.c_void_p(self.stream.cuda_stream)
+            except ImportError:
+                pass
+        self._opts = o
+        ax = (ctypes.c_double * 3)(*axis)
+        h = _H()
+        rc = self._lib.mmcq_create(ctypes.byref(h), ctypes.byref(g), Ms, Aex, alpha, Ku, ax, ctypes.byref(o))
+        if rc != 0:
+            raise MMCQError(rc, "mmcq_create failed")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mmcq_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def _ck(self, rc):
+        if rc != 0:
+            raise MMCQError(rc, self._lib.mmcq_last_error(self._h).decode())
+        return rc
+
+    def info(self) -> dict:
+        i = mmcq_info()
+        self._ck(self._lib.mmcq_info_get(self._h, ctypes.byref(i)))
+        return {k: getattr(i, k) for k, _ in mmcq_info._fields_}
+
+    def set_ms_map(self, ms):
+        p, w, keep = _ptr(ms, self.n)
+        self._ck(self._lib.mmcq_set_ms_map(self._h, p, w))
+
+    def set_bias(self, B, inst=-1):
+        self._ck(self._lib.mmcq_set_bias(self._h, inst, (ctypes.c_double * 3)(*B)))
+
+    def set_m(self, m, inst=-1):
+        p, w, keep = _ptr(m, 3 * self.n)
+        self._ck(self._lib.mmcq_set_m(self._h, inst, p, w))
+
+    def get_m(self, inst=0, out=None) -> np.ndarray:
+        if out is None:
+            out = np.empty((self.n, 3), dtype=np.float32)
+        p, w, keep = _ptr(out, 3 * self.n)
+        self._ck(self._lib.mmcq_get_m(self._h, inst, p, w))
+        return out
+
+    def set_cavity(self, omega_c, kappa, g=0.0, profile=None, profile_is_brms=False, inst=-1):
+        keep = None
+        p = None
+        if profile is not None:
+            keep = np.ascontiguousarray(np.asarray(profile, dtype=np.float32).reshape(-1))
+            if keep.size != 3 * self.n:
+                raise ValueError("profile must have N x 3 values")
+            p = ctypes.c_void_p(keep.ctypes.data)
+        self._ck(self._lib.mmcq_set_cavity(self._h, inst, omega_c, kappa, g, p, int(bool(profile_is_brms))))
+
+    def set_cavity_init(self, x0, p0, inst=-1):
+        self._ck(self._lib.mmcq_set_cavity_init(self._h, inst, x0, p0))
+
+    def reset_cavity(self, inst=-1):
+        self._ck(self._lib.mmcq_reset_cavity(self._h, inst))
+
+    def disable_cavity(self, inst=-1):
+        self._ck(self._lib.mmcq_disable_cavity(self._h, inst))
+
+    def set_integrator(self, kind=MMCQ_RK4, tol=1e-6, cavity_mode=MMCQ_CAVITY_E):
+        self._ck(self._lib.mmcq_set_integrator(self._h, kind, tol, cavity_mode))
+
+    def set_horizon(self, t_end, inst=-1):
+        self._ck(self._lib.mmcq_set_horizon(self._h, inst, t_end))
+
+    def step(self, n, dt=0.0):
+        self._ck(self._lib.mmcq_step(self._h, int(n), float(dt)))
+
+    def sync(self):
+        self._ck(self._lib.mmcq_sync(self._h))
+
+    def cavity(self, inst=0) -> dict:
+        c = mmcq_cavity()
+        self._ck(self._lib.mmcq_get_cavity(self._h, inst, ctypes.byref(c)))
+        return {k: getattr(c, k) for k, _ in mmcq_cavity._fields_}
+
+    def dt_history(self, inst=0) -> np.ndarray:
+        n = ctypes.c_int64()
+        self._ck(self._lib.mmcq_get_dt_history(self._h, inst, None, 0, ctypes.byref(n)))
+        out = np.zeros(n.value)
+        if n.value:
+            self._ck(self._lib.mmcq_get_dt_history(self._h, inst, out.ctypes.data_as(_DP), n.value, ctypes.byref(n)))
+        return out
+
+    def eval_field(self, terms=MMCQ_TERM_ALL, inst=0, out=None) -> np.ndarray:
+        if out is None:
+            out = np.empty((self.n, 3), dtype=np.float32)
+        p, w, keep = _ptr(out, 3 * self.n)
+        self._ck(self._lib.mmcq_eval_field(self._h, inst, terms, p, w))
+        return out

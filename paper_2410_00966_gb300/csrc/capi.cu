@@ -1,0 +1,581 @@
+// C ABI of the mmcq library (declarations and argument contracts in
+// include/mmcq.h).  Host code only sets things up and enqueues kernels;
+// every step of the time integration runs in the kernels of stage.cu.
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "mmcq.h"
+
+namespace mq {
+void upload_tableaux();
+cudaError_t set_smem_limits();
+cudaError_t launch_xfwd(const Plan&, const Buffers&, const StageArgs&, int, cudaStream_t);
+cudaError_t launch_xinv(const Plan&, const Material&, const Buffers&, const StageArgs&, int, cudaStream_t);
+cudaError_t launch_convolution(const Plan&, const Buffers&, const StageArgs&, int, cudaStream_t);
+int convolution_launches(const Plan&);
+bool col_fits(const Plan&);
+bool fft_fits(int, int);
+size_t xinv_smem(const Plan&);
+cudaError_t launch_set_m(float4*, const float*, const float*, long long, int, int, cudaStream_t);
+cudaError_t launch_get_m(const float4*, float*, long long, cudaStream_t);
+cudaError_t launch_apply_ms(float4*, const float*, long long, int, cudaStream_t);
+cudaError_t launch_get_field(const float4*, float*, long long, cudaStream_t);
+cudaError_t launch_coupling_sum(const float4*, const float4*, double, long long, double, double*, cudaStream_t);
+cudaError_t launch_set_dt(InstState*, int, double, cudaStream_t);
+cudaError_t build_demag_kernel(const Plan&, double, double, double, double, float*, double2*, cudaStream_t);
+}  // namespace mq
+
+using namespace mq;
+
+struct mmcq {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    mmcq_alloc_fn alloc = nullptr;
+    mmcq_free_fn freefn = nullptr;
+    void* actx = nullptr;
+    Plan P{};
+    Material mat{};
+    Buffers Bf{};
+    double dx = 0, dy = 0, dz = 0, gamma = 0, mu0 = 0, hbar = 0;
+    int kind = KIND_RK4;
+    double tol = 1e-6;
+    int mode = CAV_E;
+    std::vector<InstParams> ip;
+    std::vector<double> g;          // coupling strength per instance (profile_is_brms = 0)
+    std::vector<int> g_mode;        // 1: scale from g, 0: profile is B_rms
+    std::vector<float> ms_host;
+    float* ms_dev = nullptr;
+    float* stage3 = nullptr;
+    double* dscratch = nullptr;
+    std::vector<void*> allocs;
+    size_t bytes = 0;
+    double setup_ms = 0;
+    std::string err;
+};
+
+namespace {
+
+int fail(mmcq_t* h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    return code;
+}
+
+int cuda_fail(mmcq_t* h, cudaError_t e, const char* where) {
+    return fail(h, MMCQ_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                                  \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);     \
+    } while (0)
+
+void* dev_alloc(mmcq_t* h, size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    void* p = nullptr;
+    if (h->alloc) p = h->alloc(bytes, h->actx);
+    else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+    if (p) { h->allocs.push_back(p); h->bytes += bytes; }
+    return p;
+}
+
+void dev_release(mmcq_t* h, void* p) {
+    if (!p) return;
+    if (h->freefn) h->freefn(p, h->actx);
+    else if (!h->alloc) cudaFree(p);
+}
+
+int pow2_at_least(int n) {
+    int p = 1;
+    while (p < n) p <<= 1;
+    return p;
+}
+
+bool valid_inst(mmcq_t* h, int inst, bool allow_all) {
+    return (allow_all && inst == -1) || (inst >= 0 && inst < h->P.B);
+}
+
+// Host read-modify-write of instance states (not on the hot path).
+template <typename F>
+int edit_state(mmcq_t* h, int inst, F fn) {
+    int b0 = inst < 0 ? 0 : inst, nb = inst < 0 ? h->P.B : 1;
+    std::vector<InstState> s(nb);
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpy(s.data(), h->Bf.st + b0, sizeof(InstState) * nb, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < nb; i++) fn(s[i], b0 + i);
+    CK(h, cudaMemcpy(h->Bf.st + b0, s.data(), sizeof(InstState) * nb, cudaMemcpyHostToDevice));
+    return MMCQ_OK;
+}
+
+int upload_params(mmcq_t* h) {
+    CK(h, cudaMemcpyAsync(h->Bf.ip, h->ip.data(), sizeof(InstParams) * h->P.B, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return MMCQ_OK;
+}
+
+double ms_sum(mmcq_t* h) {
+    double s = 0;
+    for (float v : h->ms_host) s += v > 0 ? v : 0;
+    return s;
+}
+
+void refresh_scales(mmcq_t* h) {
+    double sm = ms_sum(h);
+    for (int b = 0; b < h->P.B; b++)
+        if (h->g_mode[b])
+            h->ip[b].brms_scale = sm > 0 ? h->g[b] * std::sqrt(2.0 * h->hbar / (h->gamma * h->mat.vc * sm)) : 0.0;
+}
+
+void reset_alpha(const InstParams& ip, InstState& s) {
+    s.a_re = s.as_re = 0.5 * ip.x0;
+    s.a_im = s.as_im = -0.5 * ip.p0;
+    s.have_k1 = 0;
+}
+
+int run_stage(mmcq_t* h, const StageArgs& A, int nb) {
+    CK(h, launch_xfwd(h->P, h->Bf, A, nb, h->stream));
+    CK(h, launch_convolution(h->P, h->Bf, A, nb, h->stream));
+    CK(h, launch_xinv(h->P, h->mat, h->Bf, A, nb, h->stream));
+    return MMCQ_OK;
+}
+
+int check_flags(mmcq_t* h) {
+    int f = 0;
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpy(&f, h->Bf.flags, sizeof(int), cudaMemcpyDeviceToHost));
+    if (f & (FLAG_NAN | FLAG_DT_UNDERFLOW)) {
+        int z = 0;
+        CK(h, cudaMemcpy(h->Bf.flags, &z, sizeof(int), cudaMemcpyHostToDevice));
+        return fail(h, MMCQ_ERR_NUMERIC, (f & FLAG_NAN) ? "non-finite magnetisation or field" : "adaptive step underflow");
+    }
+    return MMCQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mmcq_create(mmcq_t** out, const mmcq_grid* g, double Ms, double Aex, double alpha, double Ku,
+                const double axis[3], const mmcq_opts* o) {
+    if (!out) return MMCQ_ERR_ARG;
+    *out = nullptr;
+    if (!g || g->nx < 1 || g->ny < 1 || g->nz < 1 || g->batch < 1 || !(g->dx > 0) || !(g->dy > 0) ||
+        !(g->dz > 0) || !(Ms >= 0) || !(Aex >= 0) || !(alpha >= 0) || !std::isfinite(Ku))
+        return MMCQ_ERR_ARG;
+    auto t0 = std::chrono::steady_clock::now();
+    mmcq_t* h = new mmcq();
+    h->device = o ? o->device : 0;
+    h->gamma = (o && o->gamma > 0) ? o->gamma : 1.7595e11;
+    h->mu0 = (o && o->mu0 > 0) ? o->mu0 : 4e-7 * 3.14159265358979323846;
+    h->hbar = (o && o->hbar > 0) ? o->hbar : 1.05457182e-34;
+    h->alloc = o ? o->alloc : nullptr;
+    h->freefn = o ? o->free : nullptr;
+    h->actx = o ? o->alloc_ctx : nullptr;
+    h->dx = g->dx; h->dy = g->dy; h->dz = g->dz;
+    auto bail = [&](int code) { mmcq_destroy(h); return code; };
+    if (cudaSetDevice(h->device) != cudaSuccess) return bail(MMCQ_ERR_CUDA);
+    if (o && o->stream) h->stream = (cudaStream_t)o->stream;
+    else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(MMCQ_ERR_CUDA);
+        h->own_stream = true;
+    }
+
+    Plan& P = h->P;
+    P.nx = g->nx; P.ny = g->ny; P.nz = g->nz; P.B = g->batch;
+    P.N = (long long)g->nx * g->ny * g->nz;
+    P.px = pow2_at_least(2 * g->nx - 1); if (P.px < 2) P.px = 2;
+    P.py = pow2_at_least(2 * g->ny - 1);
+    P.pz = pow2_at_least(2 * g->nz - 1);
+    if (P.px > 4096 || P.py > 4096 || P.pz > 4096) return bail(MMCQ_ERR_UNSUPPORTED);
+    P.L = P.px / 2;
+    P.hx = P.L + 1;
+    P.hyk = P.py / 2 + 1;
+    P.hzk = P.pz / 2 + 1;
+    P.nrows = g->ny * g->nz;
+    P.twn = std::max(P.px, std::max(P.py, P.pz));
+    P.TX = 8;
+    while (P.TX > 1 && P.TX / 2 >= P.hx) P.TX /= 2;
+    while (P.TX > 1 && !col_fits(P)) P.TX /= 2;
+    if (!col_fits(P) || !fft_fits(3, P.L)) return bail(MMCQ_ERR_UNSUPPORTED);
+    P.NT = (P.hx + P.TX - 1) / P.TX;
+
+    Material& M = h->mat;
+    M.exch[0] = (float)(2.0 * Aex / (g->dx * g->dx));
+    M.exch[1] = (float)(2.0 * Aex / (g->dy * g->dy));
+    M.exch[2] = (float)(2.0 * Aex / (g->dz * g->dz));
+    M.two_ku = (float)(2.0 * Ku);
+    double ax[3] = {1, 0, 0};
+    if (axis) { ax[0] = axis[0]; ax[1] = axis[1]; ax[2] = axis[2]; }
+    double an = std::sqrt(ax[0] * ax[0] + ax[1] * ax[1] + ax[2] * ax[2]);
+    for (int c = 0; c < 3; c++) M.u[c] = an > 0 ? (float)(ax[c] / an) : 0.f;
+    M.pre = (float)(-h->gamma / (1.0 + alpha * alpha));
+    M.alpha = (float)alpha;
+    M.vc = g->dx * g->dy * g->dz;
+    M.hbar = h->hbar;
+
+    const long long BN = (long long)P.B * P.N;
+    Buffers& Bf = h->Bf;
+    bool ok = true;
+    auto A = [&](size_t bytes) { void* p = dev_alloc(h, bytes); if (!p) ok = false; return p; };
+    Bf.m[0] = (float4*)A(sizeof(float4) * BN);
+    Bf.m[1] = (float4*)A(sizeof(float4) * BN);
+    Bf.ms = (float4*)A(sizeof(float4) * BN);
+    for (int k = 0; k < MAX_STAGES; k++) Bf.k[k] = (float4*)A(sizeof(float4) * BN);
+    Bf.e6 = (float4*)A(sizeof(float4) * BN);
+    const long long spec_n = (long long)P.B * P.nz * P.NT * P.ny * 3 * P.TX;
+    Bf.spec = (float2*)A(sizeof(float2) * spec_n);
+    if (P.nz > 1) Bf.spec2 = (float2*)A(sizeof(float2) * (long long)P.B * P.nz * P.NT * P.py * 3 * P.TX);
+    Bf.kern = (float*)A(sizeof(float) * 6LL * P.hzk * P.hyk * P.NT * P.TX);
+    Bf.prof = nullptr;
+    Bf.ip = (InstParams*)A(sizeof(InstParams) * P.B);
+    Bf.st = (InstState*)A(sizeof(InstState) * P.B);
+    Bf.xpart = (double*)A(sizeof(double) * (long long)P.B * P.nrows);
+    Bf.epart = (float*)A(sizeof(float) * (long long)P.B * P.nrows);
+    Bf.counter = (unsigned*)A(sizeof(unsigned) * P.B);
+    Bf.hcap = 1 << 16;
+    Bf.hist = (double*)A(sizeof(double) * (long long)P.B * Bf.hcap);
+    Bf.flags = (int*)A(sizeof(int));
+    float2* tw = (float2*)A(sizeof(float2) * P.twn);
+    Bf.tw = tw;
+    Bf.fout = (float4*)A(sizeof(float4) * P.N);
+    h->ms_dev = (float*)A(sizeof(float) * P.N);
+    h->stage3 = (float*)A(sizeof(float) * 3 * P.N);
+    h->dscratch = (double*)A(sizeof(double) * 16);
+    if (!ok) { h->err = "device allocation failed"; return bail(MMCQ_ERR_CUDA); }
+
+    upload_tableaux();
+    if (set_smem_limits() != cudaSuccess) return bail(MMCQ_ERR_CUDA);
+    {
+        std::vector<float2> t(P.twn);
+        for (int k = 0; k < P.twn; k++) {
+            double a = -2.0 * 3.14159265358979323846 * k / P.twn;
+            t[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+        if (cudaMemcpy(tw, t.data(), sizeof(float2) * P.twn, cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(MMCQ_ERR_CUDA);
+    }
+    // demag kernel, FP64 on the device
+    {
+        size_t sbytes = sizeof(double2) * (size_t)P.px * P.py * P.pz;
+        void* scratch = nullptr;
+        if (h->alloc) scratch = h->alloc((sbytes + 255) & ~(size_t)255, h->actx);
+        else if (cudaMalloc(&scratch, sbytes) != cudaSuccess) scratch = nullptr;
+        if (!scratch) { h->err = "scratch allocation failed"; return bail(MMCQ_ERR_CUDA); }
+        cudaError_t e = build_demag_kernel(P, g->dx, g->dy, g->dz, h->mu0, Bf.kern, (double2*)scratch, h->stream);
+        if (h->freefn) h->freefn(scratch, h->actx);
+        else if (!h->alloc) cudaFree(scratch);
+        if (e != cudaSuccess) { h->err = std::string("demag kernel: ") + cudaGetErrorString(e); return bail(MMCQ_ERR_CUDA); }
+    }
+    // initial state
+    h->ms_host.assign(P.N, (float)Ms);
+    h->ip.assign(P.B, InstParams{});
+    h->g.assign(P.B, 0.0);
+    h->g_mode.assign(P.B, 0);
+    std::vector<InstState> st(P.B);
+    for (auto& s : st) {
+        std::memset(&s, 0, sizeof(s));
+    }
+    if (cudaMemcpy(h->ms_dev, h->ms_host.data(), sizeof(float) * P.N, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(Bf.st, st.data(), sizeof(InstState) * P.B, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(Bf.ip, h->ip.data(), sizeof(InstParams) * P.B, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(Bf.counter, 0, sizeof(unsigned) * P.B) != cudaSuccess ||
+        cudaMemset(Bf.flags, 0, sizeof(int)) != cudaSuccess ||
+        cudaMemset(Bf.spec, 0, sizeof(float2) * spec_n) != cudaSuccess)
+        return bail(MMCQ_ERR_CUDA);
+    {
+        std::vector<float> m3(3 * P.N, 0.f);
+        for (long long i = 0; i < P.N; i++) m3[3 * i] = 1.f;
+        if (cudaMemcpy(h->stage3, m3.data(), sizeof(float) * 3 * P.N, cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(MMCQ_ERR_CUDA);
+        for (int k = 0; k < 2; k++)
+            if (launch_set_m(Bf.m[k], h->stage3, h->ms_dev, P.N, 0, P.B, h->stream) != cudaSuccess)
+                return bail(MMCQ_ERR_CUDA);
+        for (int k = 0; k < MAX_STAGES; k++)
+            if (cudaMemsetAsync(Bf.k[k], 0, sizeof(float4) * BN, h->stream) != cudaSuccess) return bail(MMCQ_ERR_CUDA);
+    }
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(MMCQ_ERR_CUDA);
+    h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = h;
+    return MMCQ_OK;
+}
+
+void mmcq_destroy(mmcq_t* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (void* p : h->allocs) dev_release(h, p);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+const char* mmcq_last_error(const mmcq_t* h) { return h ? h->err.c_str() : "null handle"; }
+
+int mmcq_info_get(mmcq_t* h, mmcq_info* out) {
+    if (!h || !out) return MMCQ_ERR_ARG;
+    out->px = h->P.px; out->py = h->P.py; out->pz = h->P.pz;
+    out->tile = h->P.TX;
+    out->device_bytes = h->bytes;
+    out->setup_ms = h->setup_ms;
+    out->launches_per_step = (int64_t)(h->kind == KIND_RK4 ? 4 : 6) * (2 + convolution_launches(h->P));
+    return MMCQ_OK;
+}
+
+int mmcq_set_ms_map(mmcq_t* h, const float* ms, int where) {
+    if (!h || !ms) return MMCQ_ERR_ARG;
+    const long long N = h->P.N;
+    if (where == MMCQ_DEVICE) {
+        CK(h, cudaMemcpyAsync(h->ms_dev, ms, sizeof(float) * N, cudaMemcpyDeviceToDevice, h->stream));
+        CK(h, cudaMemcpyAsync(h->ms_host.data(), ms, sizeof(float) * N, cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    } else if (where == MMCQ_HOST) {
+        std::memcpy(h->ms_host.data(), ms, sizeof(float) * N);
+        CK(h, cudaMemcpyAsync(h->ms_dev, ms, sizeof(float) * N, cudaMemcpyHostToDevice, h->stream));
+    } else return MMCQ_ERR_ARG;
+    for (auto& v : h->ms_host) if (!(v > 0)) v = 0;
+    for (int k = 0; k < 2; k++) CK(h, launch_apply_ms(h->Bf.m[k], h->ms_dev, N, h->P.B, h->stream));
+    refresh_scales(h);
+    int r = upload_params(h);
+    if (r) return r;
+    return edit_state(h, -1, [](InstState& s, int) { s.have_k1 = 0; });
+}
+
+int mmcq_set_bias(mmcq_t* h, int inst, const double B[3]) {
+    if (!h || !B || !valid_inst(h, inst, true)) return MMCQ_ERR_ARG;
+    for (int b = 0; b < h->P.B; b++)
+        if (inst < 0 || b == inst)
+            for (int c = 0; c < 3; c++) h->ip[b].bext[c] = B[c];
+    int r = upload_params(h);
+    if (r) return r;
+    return edit_state(h, inst, [](InstState& s, int) { s.have_k1 = 0; });
+}
+
+int mmcq_set_m(mmcq_t* h, int inst, const float* m, int where) {
+    if (!h || !m || !valid_inst(h, inst, true) || (where != MMCQ_HOST && where != MMCQ_DEVICE)) return MMCQ_ERR_ARG;
+    const long long N = h->P.N;
+    const float* src = m;
+    if (where == MMCQ_HOST) {
+        CK(h, cudaMemcpyAsync(h->stage3, m, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, h->stream));
+        src = h->stage3;
+    }
+    int b0 = inst < 0 ? 0 : inst, nb = inst < 0 ? h->P.B : 1;
+    for (int k = 0; k < 2; k++) CK(h, launch_set_m(h->Bf.m[k], src, h->ms_dev, N, b0, nb, h->stream));
+    return edit_state(h, inst, [](InstState& s, int) { s.have_k1 = 0; });
+}
+
+int mmcq_get_m(mmcq_t* h, int inst, float* out, int where) {
+    if (!h || !out || !valid_inst(h, inst, false) || (where != MMCQ_HOST && where != MMCQ_DEVICE)) return MMCQ_ERR_ARG;
+    int r = check_flags(h);
+    InstState s;
+    CK(h, cudaMemcpy(&s, h->Bf.st + inst, sizeof(InstState), cudaMemcpyDeviceToHost));
+    const long long N = h->P.N;
+    const float4* src = h->Bf.m[s.mcur] + (long long)inst * N;
+    if (where == MMCQ_DEVICE) {
+        CK(h, launch_get_m(src, out, N, h->stream));
+    } else {
+        CK(h, launch_get_m(src, h->stage3, N, h->stream));
+        CK(h, cudaMemcpyAsync(out, h->stage3, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    return r;
+}
+
+int mmcq_set_cavity(mmcq_t* h, int inst, double omega_c, double kappa, double g, const float* profile,
+                    int profile_is_brms) {
+    if (!h || !valid_inst(h, inst, true) || !std::isfinite(omega_c) || !std::isfinite(kappa) || !std::isfinite(g))
+        return MMCQ_ERR_ARG;
+    const long long N = h->P.N;
+    if (profile) {
+        if (!h->Bf.prof) {
+            h->Bf.prof = (float4*)dev_alloc(h, sizeof(float4) * N);
+            if (!h->Bf.prof) return fail(h, MMCQ_ERR_CUDA, "profile allocation failed");
+        }
+        std::vector<float4> p(N);
+        for (long long i = 0; i < N; i++) p[i] = make_float4(profile[3 * i], profile[3 * i + 1], profile[3 * i + 2], 0.f);
+        CK(h, cudaStreamSynchronize(h->stream));
+        CK(h, cudaMemcpy(h->Bf.prof, p.data(), sizeof(float4) * N, cudaMemcpyHostToDevice));
+    }
+    for (int b = 0; b < h->P.B; b++) {
+        if (inst >= 0 && b != inst) continue;
+        h->ip[b].wc = omega_c;
+        h->ip[b].kappa = kappa;
+        h->ip[b].cav_on = 1;
+        h->g[b] = g;
+        h->g_mode[b] = profile_is_brms ? 0 : 1;
+        if (profile_is_brms) h->ip[b].brms_scale = 1.0;
+    }
+    refresh_scales(h);
+    int r = upload_params(h);
+    if (r) return r;
+    std::vector<InstParams> ip = h->ip;
+    return edit_state(h, inst, [&](InstState& s, int b) {
+        s.tcav = 0; s.S = 0; s.C = 0;
+        reset_alpha(ip[b], s);
+    });
+}
+
+int mmcq_set_cavity_init(mmcq_t* h, int inst, double x0, double p0) {
+    if (!h || !valid_inst(h, inst, true) || !std::isfinite(x0) || !std::isfinite(p0)) return MMCQ_ERR_ARG;
+    for (int b = 0; b < h->P.B; b++)
+        if (inst < 0 || b == inst) { h->ip[b].x0 = x0; h->ip[b].p0 = p0; }
+    int r = upload_params(h);
+    if (r) return r;
+    std::vector<InstParams> ip = h->ip;
+    return edit_state(h, inst, [&](InstState& s, int b) { reset_alpha(ip[b], s); });
+}
+
+int mmcq_reset_cavity(mmcq_t* h, int inst) {
+    if (!h || !valid_inst(h, inst, true)) return MMCQ_ERR_ARG;
+    std::vector<InstParams> ip = h->ip;
+    return edit_state(h, inst, [&](InstState& s, int b) {
+        s.tcav = 0; s.S = 0; s.C = 0;
+        reset_alpha(ip[b], s);
+    });
+}
+
+int mmcq_disable_cavity(mmcq_t* h, int inst) {
+    if (!h || !valid_inst(h, inst, true)) return MMCQ_ERR_ARG;
+    for (int b = 0; b < h->P.B; b++)
+        if (inst < 0 || b == inst) h->ip[b].cav_on = 0;
+    int r = upload_params(h);
+    if (r) return r;
+    return edit_state(h, inst, [](InstState& s, int) { s.have_k1 = 0; });
+}
+
+int mmcq_set_integrator(mmcq_t* h, int kind, double tol, int cavity_mode) {
+    if (!h || (kind != MMCQ_RK4 && kind != MMCQ_DP45) || (cavity_mode != MMCQ_CAVITY_E && cavity_mode != MMCQ_CAVITY_P) ||
+        (kind == MMCQ_DP45 && !(tol > 0)))
+        return MMCQ_ERR_ARG;
+    h->kind = kind;
+    h->tol = tol;
+    h->mode = cavity_mode;
+    return edit_state(h, -1, [](InstState& s, int) {
+        s.have_k1 = 0;
+        s.k1slot = 0;
+        s.as_re = s.a_re;
+        s.as_im = s.a_im;
+    });
+}
+
+int mmcq_set_horizon(mmcq_t* h, int inst, double t_end) {
+    if (!h || !valid_inst(h, inst, true) || !std::isfinite(t_end)) return MMCQ_ERR_ARG;
+    return edit_state(h, inst, [&](InstState& s, int) {
+        s.t_end = t_end > 0 ? t_end : 0.0;
+        s.done = (s.t_end > 0 && s.t >= s.t_end) ? 1 : 0;
+        if (s.t_end > 0 && s.dt > 0 && s.t + s.dt > s.t_end) s.dt = s.t_end - s.t;
+    });
+}
+
+int mmcq_step(mmcq_t* h, int64_t n, double dt) {
+    if (!h || n < 0 || !std::isfinite(dt)) return MMCQ_ERR_ARG;
+    if (h->kind == KIND_RK4 && !(dt > 0)) return fail(h, MMCQ_ERR_ARG, "RK4 needs dt > 0");
+    if (n == 0) return MMCQ_OK;
+    StageArgs A{};
+    A.kind = h->kind;
+    A.mode = h->mode;
+    A.terms = MMCQ_TERM_ALL;
+    A.field_only = 0;
+    A.inst0 = 0;
+    A.tol = (float)h->tol;
+    if (dt > 0) CK(h, launch_set_dt(h->Bf.st, h->P.B, dt, h->stream));
+    const int B = h->P.B;
+    for (int64_t it = 0; it < n; it++) {
+        if (h->kind == KIND_RK4) {
+            for (int s = 0; s < 4; s++) {
+                A.stage = s;
+                int r = run_stage(h, A, B);
+                if (r) return r;
+            }
+        } else {
+            for (int s = 0; s < 7; s++) {
+                A.stage = s;
+                int r = run_stage(h, A, B);
+                if (r) return r;
+            }
+        }
+    }
+    return MMCQ_OK;
+}
+
+int mmcq_sync(mmcq_t* h) {
+    if (!h) return MMCQ_ERR_ARG;
+    return check_flags(h);
+}
+
+int mmcq_get_cavity(mmcq_t* h, int inst, mmcq_cavity* out) {
+    if (!h || !out || !valid_inst(h, inst, false)) return MMCQ_ERR_ARG;
+    int r = check_flags(h);
+    InstState s;
+    CK(h, cudaMemcpy(&s, h->Bf.st + inst, sizeof(InstState), cudaMemcpyDeviceToHost));
+    const InstParams& ip = h->ip[inst];
+    double X = 0.0;
+    if (ip.cav_on) {
+        CK(h, launch_coupling_sum(h->Bf.m[s.mcur] + (long long)inst * h->P.N, h->Bf.prof, ip.brms_scale, h->P.N,
+                                  h->mat.vc, h->dscratch, h->stream));
+        CK(h, cudaMemcpyAsync(&X, h->dscratch, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
+    std::complex<double> a(s.a_re, s.a_im);
+    double G = ip.cav_on ? 2.0 * s.a_re : 0.0;
+    if (ip.cav_on && h->mode == CAV_P) {
+        std::complex<double> a0(0.5 * ip.x0, -0.5 * ip.p0);
+        a = std::exp(-std::complex<double>(ip.kappa, ip.wc) * s.tcav) * (a0 + std::complex<double>(-s.S / h->hbar, s.C / h->hbar));
+        double e = std::exp(-ip.kappa * s.tcav);
+        G = e * std::cos(ip.wc * s.tcav) * (ip.x0 - 2.0 * s.S / h->hbar) -
+            e * std::sin(ip.wc * s.tcav) * (ip.p0 - 2.0 * s.C / h->hbar);
+    }
+    out->t = s.t;
+    out->t_cav = s.tcav;
+    out->re_alpha = a.real();
+    out->im_alpha = a.imag();
+    out->n_photon = std::norm(a);
+    out->Gamma = G;
+    out->S = s.S;
+    out->C = s.C;
+    out->X = X;
+    out->dt = s.dt;
+    out->accepted = s.nacc;
+    out->rejected = s.nrej;
+    return r;
+}
+
+int mmcq_get_dt_history(mmcq_t* h, int inst, double* out, int64_t max, int64_t* n) {
+    if (!h || !valid_inst(h, inst, false) || max < 0 || (max > 0 && !out)) return MMCQ_ERR_ARG;
+    int r = check_flags(h);
+    InstState s;
+    CK(h, cudaMemcpy(&s, h->Bf.st + inst, sizeof(InstState), cudaMemcpyDeviceToHost));
+    if (n) *n = s.nhist;
+    long long c = s.nhist < h->Bf.hcap ? s.nhist : h->Bf.hcap;
+    if (c > max) c = max;
+    if (c > 0)
+        CK(h, cudaMemcpy(out, h->Bf.hist + (long long)inst * h->Bf.hcap, sizeof(double) * c, cudaMemcpyDeviceToHost));
+    if (s.nhist > h->Bf.hcap && r == MMCQ_OK) return fail(h, MMCQ_ERR_STATE, "step history overflowed its capacity");
+    return r;
+}
+
+int mmcq_eval_field(mmcq_t* h, int inst, int terms, float* out, int where) {
+    if (!h || !out || !valid_inst(h, inst, false) || (where != MMCQ_HOST && where != MMCQ_DEVICE) ||
+        terms < 0 || terms > MMCQ_TERM_ALL)
+        return MMCQ_ERR_ARG;
+    StageArgs A{};
+    A.kind = h->kind; A.mode = h->mode; A.terms = terms; A.field_only = 1; A.inst0 = inst; A.stage = 0;
+    A.tol = (float)h->tol;
+    int r = run_stage(h, A, 1);
+    if (r) return r;
+    const long long N = h->P.N;
+    if (where == MMCQ_DEVICE) {
+        CK(h, launch_get_field(h->Bf.fout, out, N, h->stream));
+    } else {
+        CK(h, launch_get_field(h->Bf.fout, h->stage3, N, h->stream));
+        CK(h, cudaMemcpyAsync(out, h->stage3, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    return MMCQ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,100 @@
+// Internal types shared by the host side and the kernels of the mmcq library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mq {
+
+constexpr int MAX_STAGES = 7;
+constexpr int MAX_SLOTS = 4;      // 4-value FFT slots held per thread per stage
+constexpr int MAX_THREADS = 1024;
+
+enum Kind { KIND_RK4 = 0, KIND_DP45 = 1 };
+enum CavMode { CAV_E = 0, CAV_P = 1 };
+enum Flag { FLAG_NAN = 1, FLAG_DT_UNDERFLOW = 2, FLAG_HIST_FULL = 4 };
+
+// Shape of one handle: grid, padding and the spectrum tiling.
+struct Plan {
+    int nx, ny, nz, B;
+    long long N;      // cells per instance
+    int px, py, pz;   // padded FFT sizes (px >= 2)
+    int L;            // px / 2: length of the packed complex FFT along x
+    int hx;           // px / 2 + 1 half-spectrum columns
+    int TX;           // kx columns per tile
+    int NT;           // tiles per row, NT * TX >= hx
+    int hyk, hzk;     // stored kernel extent along ky, kz: py/2 + 1, pz/2 + 1
+    int nrows;        // ny * nz rows per instance
+    int twn;          // twiddle table length (power of two >= every FFT length)
+};
+
+// Constants of the material shared by every instance.
+struct Material {
+    float exch[3];    // 2 A / d_a^2 for a = x, y, z (divided by Ms_i per cell)
+    float two_ku;     // 2 Ku
+    float u[3];       // anisotropy axis (unit)
+    float pre;        // -gamma / (1 + alpha^2)
+    float alpha;
+    double vc;        // cell volume
+    double hbar;
+};
+
+// Per-instance parameters (set from the host).
+struct InstParams {
+    double bext[3];
+    double wc, kappa, x0, p0;
+    double brms_scale;   // B_rms,i = brms_scale * profile_i
+    int cav_on;
+    int pad_;
+};
+
+// Per-instance integrator and cavity state (owned by the device).
+struct InstState {
+    double t, tcav, dt, t_end;
+    double a_re, a_im;      // alpha at the start of the step (E-mode)
+    double as_re, as_im;    // alpha of the stage about to be evaluated (E-mode)
+    double S, C;            // P-mode accumulators
+    double ka_re[MAX_STAGES], ka_im[MAX_STAGES];
+    double X;               // last reduced coupling sum (includes V_c)
+    double err;             // last error estimate (DP45)
+    long long nacc, nrej, nhist;
+    int mcur;               // which m buffer holds the accepted state
+    int k1slot;             // DP45: k buffer holding stage 1 (FSAL)
+    int have_k1;            // DP45: stage 1 valid for the current state
+    int done;               // reached t_end
+};
+
+// Device buffers of one handle.
+struct Buffers {
+    float4* m[2];     // [B][N] (x, y, z, Ms); m[mcur] is the accepted state
+    float4* ms;       // [B][N] stage input
+    float4* k[MAX_STAGES];  // [B][N] stage torques (w unused)
+    float4* e6;       // [B][N] DP45 partial error vector
+    float2* spec;     // [B][nz][NT][ny][3][TX] x-half-spectrum
+    float2* spec2;    // [B][nz][NT][py][3][TX] after the y transform (3-D only)
+    float* kern;      // [hzk][hyk][NT*TX][6] demag kernel (real, scaled)
+    float4* prof;     // [N] coupling-profile shape (or null: uniform +y)
+    InstParams* ip;
+    InstState* st;
+    double* xpart;    // [B][nrows] FP64 partial coupling sums
+    float* epart;     // [B][nrows] partial error maxima
+    unsigned* counter;  // [B] blocks finished in the current kernel
+    double* hist;     // [B][hcap] accepted step lengths
+    int hcap;
+    int* flags;
+    const float2* tw; // [twn] exp(-2 pi i k / twn)
+    float4* fout;     // [N] field output of eval_field
+};
+
+// What one launch of the stage kernels does.
+struct StageArgs {
+    int kind;      // KIND_RK4 / KIND_DP45
+    int stage;     // 0-based stage index
+    int mode;      // CAV_E / CAV_P
+    int terms;     // field terms (eval_field) or 31
+    int field_only;  // eval_field: write the field, no state change
+    int inst0;     // first instance of this launch (eval_field: one instance)
+    float tol;
+};
+
+}  // namespace mq
