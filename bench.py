@@ -1,0 +1,380 @@
+"""Benchmark of the LLG + cavity hot path on GB300.
+
+Default workload: the YIG-wire omega_c sweep -- 21 instances of a 256x64x16
+grid of 5 nm cells (Ms 1.4e5 A/m, A 3.65e-12 J/m, alpha 1e-4, Ku 1e3 J/m^3
+along the wire, bias 100 mT), cavity frequencies spread over the uniform mode,
+g/2pi = 50 MHz, kappa/2pi = 10 MHz, Dormand-Prince tol 1e-6 -- integrated as one
+batch.  One step = one Dormand-Prince attempt of every instance.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `value` counts accepted cell-steps (cells x accepted
+steps, summed over instances and ranks) per second of device time; the
+roofline object reports the dominant kernel's algorithmic bytes per launch over
+its event-timed duration, against the measured HBM copy bandwidth.
+Multi-GPU (torchrun): every rank integrates its own sweep (independent
+instances, no data exchange; weak scaling).  The reference arm times the FP64
+CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "LLG cell-steps/s on 1 GB300 (plain vs batched) at max|Δm|≤1e-5; % HBM roofline"
+FALLBACK_HBM_GBS = 6800.0
+SRC_DIR = os.path.join(ROOT, "paper_2410_00966_gb300", "csrc")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for fn in sorted(os.listdir(SRC_DIR)):
+        with open(os.path.join(SRC_DIR, fn), "rb") as f:
+            h.update(fn.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or None
+    when there is none or the kernel sources changed since it was taken."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    cur = source_hash()
+    with open(TRAFFIC_FILE) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            kv = dict(zip(*[iter(line.split())] * 2))
+            if kv.get("kernel") == kernel and kv.get("workload") == workload and kv.get("source") == cur:
+                return float(kv["bytes_per_launch"])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS), "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def workload_instances(name: str, rank: int):
+    import synthetic
+    if name == "yig_wire":
+        w = synthetic.yig_wire_sweep()
+    elif name == "film":
+        w = synthetic.film_32()
+    elif name == "large":
+        w = synthetic.large_cpw()
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    if rank:
+        # weak scaling: each rank integrates its own sweep (different seeds)
+        w.instances = [synthetic.replace(I, seed=synthetic.derive_seed(100 + rank, k)) for k, I in
+                       enumerate(w.instances)]
+    return w
+
+
+def cpu_oracle_sample(w, attempts: int):
+    """Time the FP64 oracle on instance 0 of the workload for `attempts` steps."""
+    import numpy as np
+    import oracle
+    I = w.instances[0]
+    o = oracle.Oracle(I.nx, I.ny, I.nz, I.d, I.d, I.d, I.Ms, I.Aex, I.alpha, Ku=I.Ku, axis=I.axis)
+    o.set_m(I.m0().astype(np.float64))
+    o.set_bias(I.bias)
+    prof = I.coupling_profile()
+    o.set_cavity(I.omega_c, I.kappa, I.g, profile=None if prof is None else prof.astype(np.float64))
+    o.set_integrator(oracle.DP45 if w.integrator == "dp45" else oracle.RK4, w.tol, oracle.CAV_E)
+    o.step(1, w.dt)   # first attempt outside the timing (sets the trial step)
+    t0 = time.perf_counter()
+    acc = o.step(attempts, 0.0 if w.integrator == "dp45" else w.dt)
+    dt = time.perf_counter() - t0
+    return acc * I.n / dt, dt, acc
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    oracle.build()
+    w = workload_instances(args.workload, 0)
+    I = w.instances[0]
+    o = oracle.Oracle(I.nx, I.ny, I.nz, I.d, I.d, I.d, I.Ms, I.Aex, I.alpha, Ku=I.Ku, axis=I.axis)
+    o.set_m(I.m0().astype(np.float64))
+    o.set_bias(I.bias)
+    prof = I.coupling_profile()
+    o.set_cavity(I.omega_c, I.kappa, I.g, profile=None if prof is None else prof.astype(np.float64))
+    dp = w.integrator == "dp45"
+    o.set_integrator(oracle.DP45 if dp else oracle.RK4, w.tol, oracle.CAV_E)
+    o.step(1, w.dt)
+    for _ in range(args.warmup):
+        o.step(1, 0.0 if dp else w.dt)
+    t0 = time.perf_counter()
+    acc = 0
+    for _ in range(args.steps):
+        acc += o.step(1, 0.0 if dp else w.dt)
+    el = time.perf_counter() - t0
+    value = acc * I.n / el
+    cores = os.cpu_count()
+    sample = f"instance 0 of the workload ({I.nx}x{I.ny}x{I.nz} cells), one {w.integrator} attempt per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "instances_timed": 1, "cells_per_instance": I.n, "integrator": w.integrator},
+        "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2410_00966_gb300 as pkg
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = workload_instances(args.workload, rank)
+    I0 = w.instances[0]
+    B = len(w.instances)
+    dp = w.integrator == "dp45"
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        sim = pkg.Sim(I0.nx, I0.ny, I0.nz, I0.d, I0.d, I0.d, I0.Ms, I0.Aex, I0.alpha, Ku=I0.Ku, axis=I0.axis,
+                      batch=B, device=local)
+        prof = I0.coupling_profile()
+        m0 = [I.m0() for I in w.instances]
+        for b, I in enumerate(w.instances):
+            sim.set_m(m0[b], inst=b)
+            sim.set_bias(I.bias, inst=b)
+            sim.set_cavity(I.omega_c, I.kappa, I.g, profile=prof if b == 0 else None, inst=b)
+        sim.set_integrator(pkg.MMCQ_DP45 if dp else pkg.MMCQ_RK4, w.tol, pkg.MMCQ_CAVITY_E)
+        if dp:
+            sim.set_horizon(w.horizon)
+        info = sim.info()
+        # warm-up
+        sim.step(1, w.dt)
+        sim.step(max(args.warmup - 1, 0), 0.0 if dp else w.dt)
+        sim.sync()
+        acc0 = sum(c["accepted"] for c in sim.cavity(-1))
+        launches0 = sim.launch_count()
+        clocks = ClockSampler(local)
+        clocks.start()
+        time.sleep(0.3)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        sim.profile(True)
+        e0.record(stream)
+        sim.step(args.steps, 0.0 if dp else w.dt)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        sim.profile(False)
+        if dist:
+            dist.barrier()
+        clk = clocks.stop()
+        ms = e0.elapsed_time(e1)
+        cav = sim.cavity(-1)
+        sim.sync()
+        acc1 = sum(c["accepted"] for c in cav)
+        rej = sum(c["rejected"] for c in cav)
+        launches = sim.launch_count() - launches0
+        kstats = sim.profile_read()
+        cell_steps = (acc1 - acc0) * I0.n
+        ms_max = ms
+        total_cell_steps = cell_steps
+        if dist:
+            t = torch.tensor([ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_max = float(t.item())
+            c = torch.tensor([float(cell_steps)], device=dev, dtype=torch.float64)
+            dist.all_reduce(c, op=dist.ReduceOp.SUM)
+            total_cell_steps = float(c.item())
+        value = total_cell_steps / (ms_max / 1e3)
+
+        # dominant kernel and its roofline
+        top = max(kstats, key=lambda k: k["total_ms"]) if kstats else None
+        peak, peak_kind = measured_peak()
+        roof = None
+        if top:
+            per_launch_bytes = top["bytes"] / top["launches"]
+            avg_s = top["total_ms"] / top["launches"] / 1e3
+            achieved = per_launch_bytes / avg_s / 1e9
+            traffic = ncu_traffic(top["name"], args.workload)
+            roof = {"bound": "hbm", "kernel": top["name"], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                    "algorithmic_bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_s * 1e3,
+                    "share_of_step": top["total_ms"] / sum(k["total_ms"] for k in kstats)}
+        kernels = [{"name": k["name"], "launches": k["launches"], "ms": round(k["total_ms"], 3),
+                    "GB/s": round(k["bytes"] / (k["total_ms"] / 1e3) / 1e9, 1) if k["total_ms"] > 0 else None}
+                   for k in kstats]
+        step_bytes = sum(k["bytes"] for k in kstats)
+
+        # end to end through the C ABI with host buffers: pinned m of every
+        # instance in, one step, the cavity read-out of every instance back
+        # each step, the final m of every instance back.
+        e2e = None
+        if not args.no_e2e:
+            host_m = torch.empty((B, I0.n, 3), dtype=torch.float32, pin_memory=True)
+            for b in range(B):
+                host_m[b].copy_(torch.from_numpy(sim.get_m(b)))
+            out_m = torch.empty((B, I0.n, 3), dtype=torch.float32, pin_memory=True)
+            acc_a = sum(c["accepted"] for c in sim.cavity(-1))
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            for b in range(B):
+                sim.set_m(host_m[b], inst=b)
+            for _ in range(args.steps):
+                sim.step(1, 0.0 if dp else w.dt)
+                cv = sim.cavity(-1)
+            for b in range(B):
+                sim.get_m(b, out=out_m[b])
+            el = time.perf_counter() - t0
+            acc_b = sum(c["accepted"] for c in cv)
+            e2e_val = (acc_b - acc_a) * I0.n / el
+            if dist:
+                t = torch.tensor([e2e_val], device=dev, dtype=torch.float64)
+                dist.all_reduce(t, op=dist.ReduceOp.SUM)
+                e2e_val = float(t.item())
+            h2d = B * I0.n * 3 * 4 / args.steps
+            d2h = (B * I0.n * 3 * 4) / args.steps + B * ctypes_sizeof_cavity(pkg)
+            e2e = {"value": e2e_val, "unit": "cell-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                   "note": "C-ABI calls with pinned host buffers; per step one attempt + read-out of all instances"}
+        sim.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        attempts = 3 if args.workload == "yig_wire" else 20
+        v, el, acc = cpu_oracle_sample(w, attempts)
+        cpu = {"value": v, "unit": "cell-steps/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{acc} accepted {w.integrator} steps of instance 0 ({I0.nx}x{I0.ny}x{I0.nz} cells), "
+                         f"{el:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "instances_per_gpu": B, "grid": [I0.nx, I0.ny, I0.nz],
+                       "cells_per_instance": I0.n, "integrator": w.integrator, "tol": w.tol,
+                       "cavity_mode": "E", "parallelism": "independent instances per rank",
+                       "accepted_steps": acc1 - acc0, "rejected_steps": rej,
+                       "l2": f"inputs larger than L2 ({info['device_bytes'] / 1e9:.2f} GB resident)",
+                       "padded": [info["px"], info["py"], info["pz"]], "tile": info["tile"],
+                       "algorithmic_bytes_per_step": step_bytes / args.steps},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk,
+            "gpu_launches": launches,
+            "kernels": kernels,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def ctypes_sizeof_cavity(pkg):
+    import ctypes
+    return ctypes.sizeof(pkg.mmcq_cavity)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="yig_wire", choices=["yig_wire", "film", "large"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    from paper_2410_00966_gb300 import build
+    build.build()
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

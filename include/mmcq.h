@@ -180,8 +180,9 @@ int mmcq_step(mmcq_t* h, int64_t n, double dt);
 /* Wait for the stream; report device-side errors raised since the last sync. */
 int mmcq_sync(mmcq_t* h);
 
-/* FP64 cavity / integrator read-out of one instance (Sec. 2.2 a-posteriori
- * photon amplitude; in P-mode alpha is rebuilt from S and C). */
+/* FP64 cavity / integrator read-out (Sec. 2.2 a-posteriori photon amplitude;
+ * in P-mode alpha is rebuilt from S and C).  inst = -1 fills out[0..batch-1]
+ * for every instance in one call; otherwise out is one struct. */
 int mmcq_get_cavity(mmcq_t* h, int inst, mmcq_cavity* out);
 
 /* Accepted step lengths of one instance in order (at most max are copied;
@@ -191,6 +192,26 @@ int mmcq_get_dt_history(mmcq_t* h, int inst, double* out, int64_t max, int64_t* 
 /* Effective field (T) of one instance at its current m, with the selected
  * MMCQ_TERM_* terms (cavity term uses the current Gamma); N x 3 floats. */
 int mmcq_eval_field(mmcq_t* h, int inst, int terms, float* out, int where);
+
+/* ---- measurement -------------------------------------------------------
+ * Per-kernel-class timing of the launches mmcq_step enqueues.  While enabled,
+ * each launch is bracketed by two CUDA events on the handle's stream; the
+ * record also carries the launch's algorithmic bytes: the compulsory HBM
+ * traffic of that pass (every value the pass must read or write once: m,
+ * stage torques, spectra rows, one copy of the demag kernel per launch). */
+typedef struct {
+    char name[24];         /* "x_forward", "conv_2d", "y_forward", "z_convolve", "y_inverse", "x_inverse" */
+    int64_t launches;
+    double total_ms;       /* summed event-timed durations */
+    double bytes;          /* summed algorithmic bytes */
+} mmcq_kernel_stat;
+
+/* enable = 1 clears the records and starts recording; 0 stops. */
+int mmcq_profile(mmcq_t* h, int enable);
+/* Synchronises, then writes up to max per-class totals; *n = classes written. */
+int mmcq_profile_read(mmcq_t* h, mmcq_kernel_stat* out, int max, int* n);
+/* Kernels launched by mmcq_step since the handle was created (or -1 for a null handle). */
+int64_t mmcq_launch_count(const mmcq_t* h);
 
 #ifdef __cplusplus
 }

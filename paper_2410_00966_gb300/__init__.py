@@ -61,6 +61,11 @@ class mmcq_info(ctypes.Structure):
                 ("launches_per_step", ctypes.c_int64)]
 
 
+class mmcq_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
+
+
 _H = ctypes.c_void_p
 _FP = ctypes.c_void_p   # float* (host or device)
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -87,6 +92,10 @@ PROTOTYPES = {
     "mmcq_get_cavity": (ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(mmcq_cavity)]),
     "mmcq_get_dt_history": (ctypes.c_int, [_H, ctypes.c_int, _DP, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "mmcq_eval_field": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, _FP, ctypes.c_int]),
+    "mmcq_profile": (ctypes.c_int, [_H, ctypes.c_int]),
+    "mmcq_profile_read": (ctypes.c_int, [_H, ctypes.POINTER(mmcq_kernel_stat), ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int)]),
+    "mmcq_launch_count": (ctypes.c_int64, [_H]),
 }
 
 
@@ -265,10 +274,13 @@ class Sim:
     def sync(self):
         self._ck(self._lib.mmcq_sync(self._h))
 
-    def cavity(self, inst=0) -> dict:
-        c = mmcq_cavity()
-        self._ck(self._lib.mmcq_get_cavity(self._h, inst, ctypes.byref(c)))
-        return {k: getattr(c, k) for k, _ in mmcq_cavity._fields_}
+    def cavity(self, inst=0):
+        """Read-out of one instance (dict), or of all instances (list of dicts) for inst = -1."""
+        n = self.batch if inst == -1 else 1
+        c = (mmcq_cavity * n)()
+        self._ck(self._lib.mmcq_get_cavity(self._h, inst, c))
+        res = [{k: getattr(c[i], k) for k, _ in mmcq_cavity._fields_} for i in range(n)]
+        return res if inst == -1 else res[0]
 
     def dt_history(self, inst=0) -> np.ndarray:
         n = ctypes.c_int64()
@@ -277,6 +289,19 @@ class Sim:
         if n.value:
             self._ck(self._lib.mmcq_get_dt_history(self._h, inst, out.ctypes.data_as(_DP), n.value, ctypes.byref(n)))
         return out
+
+    def profile(self, enable=True):
+        self._ck(self._lib.mmcq_profile(self._h, int(bool(enable))))
+
+    def profile_read(self) -> list:
+        arr = (mmcq_kernel_stat * 16)()
+        n = ctypes.c_int()
+        self._ck(self._lib.mmcq_profile_read(self._h, arr, 16, ctypes.byref(n)))
+        return [{"name": arr[i].name.decode(), "launches": arr[i].launches, "total_ms": arr[i].total_ms,
+                 "bytes": arr[i].bytes} for i in range(n.value)]
+
+    def launch_count(self) -> int:
+        return int(self._lib.mmcq_launch_count(self._h))
 
     def eval_field(self, terms=MMCQ_TERM_ALL, inst=0, out=None) -> np.ndarray:
         if out is None:

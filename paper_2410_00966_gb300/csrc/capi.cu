@@ -18,6 +18,7 @@ cudaError_t set_smem_limits();
 cudaError_t launch_xfwd(const Plan&, const Buffers&, const StageArgs&, int, cudaStream_t);
 cudaError_t launch_xinv(const Plan&, const Material&, const Buffers&, const StageArgs&, int, cudaStream_t);
 cudaError_t launch_convolution(const Plan&, const Buffers&, const StageArgs&, int, cudaStream_t);
+cudaError_t launch_conv_part(const Plan&, const Buffers&, const StageArgs&, int, cudaStream_t, int);
 int convolution_launches(const Plan&);
 bool col_fits(const Plan&);
 bool fft_fits(int, int);
@@ -26,7 +27,7 @@ cudaError_t launch_set_m(float4*, const float*, const float*, long long, int, in
 cudaError_t launch_get_m(const float4*, float*, long long, cudaStream_t);
 cudaError_t launch_apply_ms(float4*, const float*, long long, int, cudaStream_t);
 cudaError_t launch_get_field(const float4*, float*, long long, cudaStream_t);
-cudaError_t launch_coupling_sum(const float4*, const float4*, double, long long, double, double*, cudaStream_t);
+cudaError_t launch_coupling_sum(const Buffers&, long long, double, int, int, double*, cudaStream_t);
 cudaError_t launch_set_dt(InstState*, int, double, cudaStream_t);
 cudaError_t build_demag_kernel(const Plan&, double, double, double, double, float*, double2*, cudaStream_t);
 }  // namespace mq
@@ -58,7 +59,16 @@ struct mmcq {
     size_t bytes = 0;
     double setup_ms = 0;
     std::string err;
+    // measurement
+    int64_t launches = 0;
+    bool profiling = false;
+    struct Rec { int cls; int ev; double bytes; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> events;   // pool, two per record
 };
+
+enum { CLS_XFWD = 0, CLS_CONV2D, CLS_YFWD, CLS_ZCONV, CLS_YINV, CLS_XINV, NCLS };
+static const char* CLS_NAMES[NCLS] = {"x_forward", "conv_2d", "y_forward", "z_convolve", "y_inverse", "x_inverse"};
 
 namespace {
 
@@ -139,11 +149,76 @@ void reset_alpha(const InstParams& ip, InstState& s) {
     s.have_k1 = 0;
 }
 
-int run_stage(mmcq_t* h, const StageArgs& A, int nb) {
-    CK(h, launch_xfwd(h->P, h->Bf, A, nb, h->stream));
-    CK(h, launch_convolution(h->P, h->Bf, A, nb, h->stream));
-    CK(h, launch_xinv(h->P, h->mat, h->Bf, A, nb, h->stream));
+// Algorithmic (compulsory) bytes of one launch of class cls for nb instances.
+double launch_bytes(const mmcq_t* h, int cls, const StageArgs& A, int nb) {
+    const Plan& P = h->P;
+    const double N = (double)P.N;
+    const double cplx = 8.0;
+    const double xrow = (double)P.nrows * P.NT * P.TX * 3 * cplx;      // one instance's x half-spectrum
+    const double yrow = (double)P.nz * P.py * P.NT * P.TX * 3 * cplx;  // after the y transform
+    const double kern = (double)P.hzk * P.hyk * P.NT * P.TX * 6 * 4;
+    static const int dp_kreads[7] = {0, 1, 2, 3, 4, 5, 5};
+    const int s = A.stage;
+    double per = 0.0;
+    switch (cls) {
+        case CLS_XFWD: {
+            int kr = A.field_only || s == 0 ? 0 : (A.kind == KIND_RK4 ? 1 : dp_kreads[s]);
+            int wr = A.field_only || s == 0 ? 0 : ((A.kind == KIND_DP45 && s == 6) ? 2 : 1);
+            per = N * 16.0 * (1 + kr + wr) + xrow;
+            break;
+        }
+        case CLS_CONV2D: return nb * 2.0 * xrow + kern;
+        case CLS_YFWD: per = xrow + yrow; break;
+        case CLS_ZCONV: return nb * 2.0 * yrow + kern;
+        case CLS_YINV: per = yrow + xrow; break;
+        case CLS_XINV: {
+            double spec = (double)P.nrows * (P.L + 1) * 3 * cplx;
+            double cells = 16.0;                         // stage input m_s
+            if (A.field_only) cells += 16.0;             // field out
+            else if (A.kind == KIND_RK4 && s == 3) cells += 16.0 * 5;  // m0, k1..k3 in, m out
+            else if (A.kind == KIND_DP45 && s == 6) cells += 32.0;     // e6 in, k out
+            else cells += 16.0;                          // k out
+            if (h->Bf.prof) cells += 16.0;
+            per = spec + N * cells;
+            break;
+        }
+    }
+    return per * nb;
+}
+
+int launch_timed(mmcq_t* h, int cls, const StageArgs& A, int nb, int part) {
+    int ev = -1;
+    if (h->profiling) {
+        ev = (int)h->recs.size() * 2;
+        while ((int)h->events.size() < ev + 2) {
+            cudaEvent_t e;
+            CK(h, cudaEventCreate(&e));
+            h->events.push_back(e);
+        }
+        CK(h, cudaEventRecord(h->events[ev], h->stream));
+    }
+    if (cls == CLS_XFWD) CK(h, launch_xfwd(h->P, h->Bf, A, nb, h->stream));
+    else if (cls == CLS_XINV) CK(h, launch_xinv(h->P, h->mat, h->Bf, A, nb, h->stream));
+    else CK(h, launch_conv_part(h->P, h->Bf, A, nb, h->stream, part));
+    h->launches++;
+    if (h->profiling) {
+        CK(h, cudaEventRecord(h->events[ev + 1], h->stream));
+        h->recs.push_back({cls, ev, launch_bytes(h, cls, A, nb)});
+    }
     return MMCQ_OK;
+}
+
+int run_stage(mmcq_t* h, const StageArgs& A, int nb) {
+    int r;
+    if ((r = launch_timed(h, CLS_XFWD, A, nb, 0))) return r;
+    if (h->P.nz == 1) {
+        if ((r = launch_timed(h, CLS_CONV2D, A, nb, 0))) return r;
+    } else {
+        if ((r = launch_timed(h, CLS_YFWD, A, nb, 1))) return r;
+        if ((r = launch_timed(h, CLS_ZCONV, A, nb, 2))) return r;
+        if ((r = launch_timed(h, CLS_YINV, A, nb, 3))) return r;
+    }
+    return launch_timed(h, CLS_XINV, A, nb, 0);
 }
 
 int check_flags(mmcq_t* h) {
@@ -247,7 +322,7 @@ int mmcq_create(mmcq_t** out, const mmcq_grid* g, double Ms, double Aex, double 
     Bf.fout = (float4*)A(sizeof(float4) * P.N);
     h->ms_dev = (float*)A(sizeof(float) * P.N);
     h->stage3 = (float*)A(sizeof(float) * 3 * P.N);
-    h->dscratch = (double*)A(sizeof(double) * 16);
+    h->dscratch = (double*)A(sizeof(double) * P.B);
     if (!ok) { h->err = "device allocation failed"; return bail(MMCQ_ERR_CUDA); }
 
     upload_tableaux();
@@ -310,6 +385,7 @@ void mmcq_destroy(mmcq_t* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (void* p : h->allocs) dev_release(h, p);
+    for (auto e : h->events) cudaEventDestroy(e);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -508,39 +584,42 @@ int mmcq_sync(mmcq_t* h) {
 }
 
 int mmcq_get_cavity(mmcq_t* h, int inst, mmcq_cavity* out) {
-    if (!h || !out || !valid_inst(h, inst, false)) return MMCQ_ERR_ARG;
+    if (!h || !out || !valid_inst(h, inst, true)) return MMCQ_ERR_ARG;
     int r = check_flags(h);
-    InstState s;
-    CK(h, cudaMemcpy(&s, h->Bf.st + inst, sizeof(InstState), cudaMemcpyDeviceToHost));
-    const InstParams& ip = h->ip[inst];
-    double X = 0.0;
-    if (ip.cav_on) {
-        CK(h, launch_coupling_sum(h->Bf.m[s.mcur] + (long long)inst * h->P.N, h->Bf.prof, ip.brms_scale, h->P.N,
-                                  h->mat.vc, h->dscratch, h->stream));
-        CK(h, cudaMemcpyAsync(&X, h->dscratch, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-        CK(h, cudaStreamSynchronize(h->stream));
+    const int b0 = inst < 0 ? 0 : inst, nb = inst < 0 ? h->P.B : 1;
+    std::vector<InstState> st(nb);
+    std::vector<double> X(nb, 0.0);
+    CK(h, cudaMemcpy(st.data(), h->Bf.st + b0, sizeof(InstState) * nb, cudaMemcpyDeviceToHost));
+    CK(h, launch_coupling_sum(h->Bf, h->P.N, h->mat.vc, b0, nb, h->dscratch, h->stream));
+    CK(h, cudaMemcpyAsync(X.data(), h->dscratch, sizeof(double) * nb, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (int q = 0; q < nb; q++) {
+        const InstState& s = st[q];
+        const InstParams& ip = h->ip[b0 + q];
+        std::complex<double> a(s.a_re, s.a_im);
+        double G = ip.cav_on ? 2.0 * s.a_re : 0.0;
+        if (ip.cav_on && h->mode == CAV_P) {
+            std::complex<double> a0(0.5 * ip.x0, -0.5 * ip.p0);
+            a = std::exp(-std::complex<double>(ip.kappa, ip.wc) * s.tcav) *
+                (a0 + std::complex<double>(-s.S / h->hbar, s.C / h->hbar));
+            double e = std::exp(-ip.kappa * s.tcav);
+            G = e * std::cos(ip.wc * s.tcav) * (ip.x0 - 2.0 * s.S / h->hbar) -
+                e * std::sin(ip.wc * s.tcav) * (ip.p0 - 2.0 * s.C / h->hbar);
+        }
+        mmcq_cavity& o = out[q];
+        o.t = s.t;
+        o.t_cav = s.tcav;
+        o.re_alpha = a.real();
+        o.im_alpha = a.imag();
+        o.n_photon = std::norm(a);
+        o.Gamma = G;
+        o.S = s.S;
+        o.C = s.C;
+        o.X = X[q];
+        o.dt = s.dt;
+        o.accepted = s.nacc;
+        o.rejected = s.nrej;
     }
-    std::complex<double> a(s.a_re, s.a_im);
-    double G = ip.cav_on ? 2.0 * s.a_re : 0.0;
-    if (ip.cav_on && h->mode == CAV_P) {
-        std::complex<double> a0(0.5 * ip.x0, -0.5 * ip.p0);
-        a = std::exp(-std::complex<double>(ip.kappa, ip.wc) * s.tcav) * (a0 + std::complex<double>(-s.S / h->hbar, s.C / h->hbar));
-        double e = std::exp(-ip.kappa * s.tcav);
-        G = e * std::cos(ip.wc * s.tcav) * (ip.x0 - 2.0 * s.S / h->hbar) -
-            e * std::sin(ip.wc * s.tcav) * (ip.p0 - 2.0 * s.C / h->hbar);
-    }
-    out->t = s.t;
-    out->t_cav = s.tcav;
-    out->re_alpha = a.real();
-    out->im_alpha = a.imag();
-    out->n_photon = std::norm(a);
-    out->Gamma = G;
-    out->S = s.S;
-    out->C = s.C;
-    out->X = X;
-    out->dt = s.dt;
-    out->accepted = s.nacc;
-    out->rejected = s.nrej;
     return r;
 }
 
@@ -577,5 +656,43 @@ int mmcq_eval_field(mmcq_t* h, int inst, int terms, float* out, int where) {
     CK(h, cudaStreamSynchronize(h->stream));
     return MMCQ_OK;
 }
+
+int mmcq_profile(mmcq_t* h, int enable) {
+    if (!h) return MMCQ_ERR_ARG;
+    if (enable) {
+        CK(h, cudaStreamSynchronize(h->stream));
+        h->recs.clear();
+    }
+    h->profiling = enable != 0;
+    return MMCQ_OK;
+}
+
+int mmcq_profile_read(mmcq_t* h, mmcq_kernel_stat* out, int max, int* n) {
+    if (!h || !out || max < 0) return MMCQ_ERR_ARG;
+    CK(h, cudaStreamSynchronize(h->stream));
+    double ms[NCLS] = {0}, by[NCLS] = {0};
+    int64_t cnt[NCLS] = {0};
+    for (const auto& r : h->recs) {
+        float t = 0.f;
+        CK(h, cudaEventElapsedTime(&t, h->events[r.ev], h->events[r.ev + 1]));
+        ms[r.cls] += t;
+        by[r.cls] += r.bytes;
+        cnt[r.cls]++;
+    }
+    int k = 0;
+    for (int c = 0; c < NCLS && k < max; c++) {
+        if (!cnt[c]) continue;
+        std::memset(&out[k], 0, sizeof(mmcq_kernel_stat));
+        std::snprintf(out[k].name, sizeof(out[k].name), "%s", CLS_NAMES[c]);
+        out[k].launches = cnt[c];
+        out[k].total_ms = ms[c];
+        out[k].bytes = by[c];
+        k++;
+    }
+    if (n) *n = k;
+    return MMCQ_OK;
+}
+
+int64_t mmcq_launch_count(const mmcq_t* h) { return h ? h->launches : -1; }
 
 }  // extern "C"

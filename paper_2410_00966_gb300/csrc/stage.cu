@@ -581,10 +581,13 @@ __global__ void k_get_field(const float4* f, float* dst, long long N) {
     dst[3 * i] = v.x; dst[3 * i + 1] = v.y; dst[3 * i + 2] = v.z;
 }
 
-// X = V_c sum Ms m . B_rms for one instance at its accepted state (read-out only).
-__global__ void k_coupling_sum(const float4* m, const float4* prof, double scale, long long N, double vc,
-                               double* out) {
+// X = V_c sum Ms m . B_rms of each instance at its accepted state (read-out
+// only): one block per instance, fixed-order reduction.
+__global__ void k_coupling_sum(const float4* m0, const float4* m1, const InstState* st, const InstParams* ip,
+                               const float4* prof, long long N, double vc, int b0, double* out) {
     __shared__ double red[32];
+    const int b = b0 + blockIdx.x;
+    const float4* m = (st[b].mcur ? m1 : m0) + (long long)b * N;
     double acc = 0.0;
     for (long long i = threadIdx.x; i < N; i += blockDim.x) {
         float4 v = m[i];
@@ -593,7 +596,7 @@ __global__ void k_coupling_sum(const float4* m, const float4* prof, double scale
         acc += (double)v.w * (v.x * px + v.y * py + v.z * pz);
     }
     acc = block_sum_d(acc, red);
-    if (threadIdx.x == 0) *out = acc * scale * vc;
+    if (threadIdx.x == 0) out[blockIdx.x] = ip[b].cav_on ? acc * ip[b].brms_scale * vc : 0.0;
 }
 
 __global__ void k_set_dt(InstState* st, int B, double dt) {
@@ -694,36 +697,46 @@ static void spec_strides(const Plan& P, int rows, long long& sb, long long& sz, 
     sb = (long long)P.nz * sz;          // one instance
 }
 
-cudaError_t launch_convolution(const Plan& P, const Buffers& Bf, const StageArgs& A, int nb, cudaStream_t s) {
+// One launch of the demag convolution: part 0 = 2-D (fwd y, product, inv y);
+// 3-D: part 1 = forward y, 2 = z forward / product / z inverse, 3 = inverse y.
+cudaError_t launch_conv_part(const Plan& P, const Buffers& Bf, const StageArgs& A, int nb, cudaStream_t s, int part) {
     long long sb, sz, st, sr, tb, tz, tt, tr;
     spec_strides(P, P.ny, sb, sz, st, sr);
     spec_strides(P, P.py, tb, tz, tt, tr);
-    if (P.nz == 1) {
-        ColArgs C{};
+    ColArgs C{};
+    int outer = 1;
+    if (part == 0) {
         C.in = Bf.spec; C.out = Bf.spec;
         C.in_b = C.out_b = sb; C.in_o = C.out_o = 0; C.in_t = C.out_t = st; C.in_r = C.out_r = sr;
         C.P = P.py; C.n_in = P.ny; C.n_out = P.ny;
         C.fwd = 1; C.mult = 1; C.inv = 1; C.ncomp = 3; C.ky_is_row = 1;
-        return launch_col(P, Bf, A, C, 1, nb, s);
+    } else if (part == 1) {
+        C.in = Bf.spec; C.out = Bf.spec2;
+        C.in_b = sb; C.in_o = sz; C.in_t = st; C.in_r = sr;
+        C.out_b = tb; C.out_o = tz; C.out_t = tt; C.out_r = tr;
+        C.P = P.py; C.n_in = P.ny; C.n_out = P.py; C.fwd = 1; C.ncomp = 1;
+        outer = P.nz;
+    } else if (part == 2) {
+        C.in = Bf.spec2; C.out = Bf.spec2;
+        C.in_b = C.out_b = tb; C.in_o = C.out_o = tr; C.in_t = C.out_t = tt; C.in_r = C.out_r = tz;
+        C.P = P.pz; C.n_in = P.nz; C.n_out = P.nz; C.fwd = 1; C.mult = 1; C.inv = 1; C.ncomp = 3; C.ky_is_row = 0;
+        outer = P.py;
+    } else {
+        C.in = Bf.spec2; C.out = Bf.spec;
+        C.in_b = tb; C.in_o = tz; C.in_t = tt; C.in_r = tr;
+        C.out_b = sb; C.out_o = sz; C.out_t = st; C.out_r = sr;
+        C.P = P.py; C.n_in = P.py; C.n_out = P.ny; C.inv = 1; C.ncomp = 1;
+        outer = P.nz;
     }
+    return launch_col(P, Bf, A, C, outer, nb, s);
+}
+
+cudaError_t launch_convolution(const Plan& P, const Buffers& Bf, const StageArgs& A, int nb, cudaStream_t s) {
+    if (P.nz == 1) return launch_conv_part(P, Bf, A, nb, s, 0);
     cudaError_t e;
-    ColArgs Y{};
-    Y.in = Bf.spec; Y.out = Bf.spec2;
-    Y.in_b = sb; Y.in_o = sz; Y.in_t = st; Y.in_r = sr;
-    Y.out_b = tb; Y.out_o = tz; Y.out_t = tt; Y.out_r = tr;
-    Y.P = P.py; Y.n_in = P.ny; Y.n_out = P.py; Y.fwd = 1; Y.ncomp = 1;
-    if ((e = launch_col(P, Bf, A, Y, P.nz, nb, s)) != cudaSuccess) return e;
-    ColArgs Z{};
-    Z.in = Bf.spec2; Z.out = Bf.spec2;
-    Z.in_b = Z.out_b = tb; Z.in_o = Z.out_o = tr; Z.in_t = Z.out_t = tt; Z.in_r = Z.out_r = tz;
-    Z.P = P.pz; Z.n_in = P.nz; Z.n_out = P.nz; Z.fwd = 1; Z.mult = 1; Z.inv = 1; Z.ncomp = 3; Z.ky_is_row = 0;
-    if ((e = launch_col(P, Bf, A, Z, P.py, nb, s)) != cudaSuccess) return e;
-    ColArgs I{};
-    I.in = Bf.spec2; I.out = Bf.spec;
-    I.in_b = tb; I.in_o = tz; I.in_t = tt; I.in_r = tr;
-    I.out_b = sb; I.out_o = sz; I.out_t = st; I.out_r = sr;
-    I.P = P.py; I.n_in = P.py; I.n_out = P.ny; I.inv = 1; I.ncomp = 1;
-    return launch_col(P, Bf, A, I, P.nz, nb, s);
+    for (int part = 1; part <= 3; part++)
+        if ((e = launch_conv_part(P, Bf, A, nb, s, part)) != cudaSuccess) return e;
+    return cudaSuccess;
 }
 
 int convolution_launches(const Plan& P) { return P.nz == 1 ? 1 : 3; }
@@ -750,9 +763,9 @@ cudaError_t launch_get_field(const float4* f, float* dst, long long N, cudaStrea
     k_get_field<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(f, dst, N);
     return cudaGetLastError();
 }
-cudaError_t launch_coupling_sum(const float4* m, const float4* prof, double scale, long long N, double vc,
-                                double* out, cudaStream_t s) {
-    k_coupling_sum<<<1, 1024, 0, s>>>(m, prof, scale, N, vc, out);
+cudaError_t launch_coupling_sum(const Buffers& Bf, long long N, double vc, int b0, int nb, double* out,
+                                cudaStream_t s) {
+    k_coupling_sum<<<nb, 1024, 0, s>>>(Bf.m[0], Bf.m[1], Bf.st, Bf.ip, Bf.prof, N, vc, b0, out);
     return cudaGetLastError();
 }
 cudaError_t launch_set_dt(InstState* st, int B, double dt, cudaStream_t s) {
