@@ -133,6 +133,18 @@ def workload_instances(name: str, rank: int):
     return w
 
 
+def reduce_over_ranks(dist, device, ms: float, cell_steps: float):
+    """Whole-job timing: the slowest rank's time and the sum of every rank's work."""
+    if dist is None:
+        return ms, float(cell_steps)
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(cell_steps)], device=device, dtype=torch.float64)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(c.item())
+
+
 def cpu_oracle_sample(w, attempts: int):
     """Time the FP64 oracle on instance 0 of the workload for `attempts` steps."""
     import numpy as np
@@ -256,15 +268,7 @@ def run_ours(args):
         launches = sim.launch_count() - launches0
         kstats = sim.profile_read()
         cell_steps = (acc1 - acc0) * I0.n
-        ms_max = ms
-        total_cell_steps = cell_steps
-        if dist:
-            t = torch.tensor([ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_max = float(t.item())
-            c = torch.tensor([float(cell_steps)], device=dev, dtype=torch.float64)
-            dist.all_reduce(c, op=dist.ReduceOp.SUM)
-            total_cell_steps = float(c.item())
+        ms_max, total_cell_steps = reduce_over_ranks(dist, dev, ms, cell_steps)
         value = total_cell_steps / (ms_max / 1e3)
 
         # dominant kernel and its roofline
