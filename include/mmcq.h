@@ -193,6 +193,33 @@ int mmcq_get_dt_history(mmcq_t* h, int inst, double* out, int64_t max, int64_t* 
  * MMCQ_TERM_* terms (cavity term uses the current Gamma); N x 3 floats. */
 int mmcq_eval_field(mmcq_t* h, int inst, int terms, float* out, int where);
 
+/* ---- allocation-free coupling sum ---------------------------------------
+ * The paper has no counterpart to this call.  It computes
+ * X = vc * sum_i ms[i] * (m_i . brms_i) in FP64 (the same sum that drives the
+ * cavity, reported as X by mmcq_get_cavity) for callers that cannot allocate
+ * device memory: code running inside a host framework whose own memory pool
+ * owns the device and forbids allocations behind its back, or a latency-bound
+ * loop that cannot afford cudaMalloc's implicit device synchronisation.  No
+ * handle is needed and nothing is allocated: the kernel's scratch is a fixed
+ * 32.8 KB array in the library's static device memory, which every GPU that
+ * loads the library keeps until the process exits.
+ *   m, brms: device arrays of n x 3 floats; ms: device array of n floats;
+ *   vc: cell volume (m^3); out: host pointer receiving X (J).
+ *   stream: cudaStream_t to run on (NULL = the default stream); the call
+ *   waits for its own work on that stream before returning.
+ * Limits and behaviour:
+ *   - n <= 16,777,216 cells (4096 chunks of 4096); larger n returns
+ *     MMCQ_ERR_UNSUPPORTED without touching the GPU.
+ *   - The first call on each device looks up the array's device address
+ *     (with that device current); make that first call before any stream
+ *     capture begins.
+ *   - Every call shares the one array, so calls whose work overlaps on the GPU
+ *     (different streams, threads or processes sharing the context) race and
+ *     may return wrong sums; serialise them.
+ *   - Errors: MMCQ_ERR_ARG (null pointer, n < 1, vc <= 0), MMCQ_ERR_CUDA. */
+int mmcq_coupling_sum_noalloc(const float* m, const float* ms, const float* brms, int64_t n, double vc, double* out,
+                              void* stream);
+
 /* ---- measurement -------------------------------------------------------
  * Per-kernel-class timing of the launches mmcq_step enqueues.  While enabled,
  * each launch is bracketed by two CUDA events on the handle's stream; the

@@ -96,6 +96,8 @@ PROTOTYPES = {
     "mmcq_profile_read": (ctypes.c_int, [_H, ctypes.POINTER(mmcq_kernel_stat), ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int)]),
     "mmcq_launch_count": (ctypes.c_int64, [_H]),
+    "mmcq_coupling_sum_noalloc": (ctypes.c_int, [_FP, _FP, _FP, ctypes.c_int64, ctypes.c_double, _DP,
+                                                 ctypes.c_void_p]),
 }
 
 
