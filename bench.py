@@ -220,6 +220,8 @@ def run_ours(args):
     dev = torch.device("cuda", local)
 
     w = workload_instances(args.workload, rank)
+    if args.instances:
+        w.instances = w.instances[:args.instances]
     I0 = w.instances[0]
     B = len(w.instances)
     dp = w.integrator == "dp45"
@@ -370,6 +372,7 @@ def main():
     ap.add_argument("--workload", default="yig_wire", choices=["yig_wire", "film", "large"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--instances", type=int, default=0, help="use only the first N instances (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

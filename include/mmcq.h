@@ -115,8 +115,9 @@ typedef struct {
  * method.  Ms (A/m), Aex (J/m), alpha (Gilbert damping, Eq. llg), Ku (J/m^3)
  * and axis (normalised here) are shared by all instances.  Initial state:
  * m = +x, uniform Ms, zero bias, cavity off, RK4, E-mode.
- * Errors: MMCQ_ERR_ARG (null/invalid), MMCQ_ERR_UNSUPPORTED (padded size
- * > 4096 on an axis), MMCQ_ERR_CUDA. On error *h is set to NULL. */
+ * Padding: each axis is zero-padded to the smallest power of two >= 2n - 1.
+ * Errors: MMCQ_ERR_ARG (null/invalid), MMCQ_ERR_UNSUPPORTED (nx > 1024, or
+ * ny or nz > 2048), MMCQ_ERR_CUDA. On error *h is set to NULL. */
 int mmcq_create(mmcq_t** h, const mmcq_grid* g, double Ms, double Aex, double alpha, double Ku,
                 const double axis[3], const mmcq_opts* opts);
 void mmcq_destroy(mmcq_t* h);

@@ -23,6 +23,8 @@ int convolution_launches(const Plan&);
 bool col_fits(const Plan&);
 bool fft_fits(int, int);
 size_t xinv_smem(const Plan&);
+int rows_per_block(int, int);
+bool x_fits(const Plan&);
 cudaError_t launch_set_m(float4*, const float*, const float*, long long, int, int, cudaStream_t);
 cudaError_t launch_get_m(const float4*, float*, long long, cudaStream_t);
 cudaError_t launch_apply_ms(float4*, const float*, long long, int, cudaStream_t);
@@ -59,6 +61,7 @@ struct mmcq {
     size_t bytes = 0;
     double setup_ms = 0;
     std::string err;
+    bool k1_dirty = true;   // some instance may need its first DP45 stage recomputed
     // measurement
     int64_t launches = 0;
     bool profiling = false;
@@ -121,6 +124,7 @@ int edit_state(mmcq_t* h, int inst, F fn) {
     CK(h, cudaMemcpy(s.data(), h->Bf.st + b0, sizeof(InstState) * nb, cudaMemcpyDeviceToHost));
     for (int i = 0; i < nb; i++) fn(s[i], b0 + i);
     CK(h, cudaMemcpy(h->Bf.st + b0, s.data(), sizeof(InstState) * nb, cudaMemcpyHostToDevice));
+    h->k1_dirty = true;
     return MMCQ_OK;
 }
 
@@ -268,7 +272,7 @@ int mmcq_create(mmcq_t** out, const mmcq_grid* g, double Ms, double Aex, double 
     P.px = pow2_at_least(2 * g->nx - 1); if (P.px < 2) P.px = 2;
     P.py = pow2_at_least(2 * g->ny - 1);
     P.pz = pow2_at_least(2 * g->nz - 1);
-    if (P.px > 4096 || P.py > 4096 || P.pz > 4096) return bail(MMCQ_ERR_UNSUPPORTED);
+    if (P.px > 2048 || P.py > 4096 || P.pz > 4096) return bail(MMCQ_ERR_UNSUPPORTED);
     P.L = P.px / 2;
     P.hx = P.L + 1;
     P.hyk = P.py / 2 + 1;
@@ -278,8 +282,17 @@ int mmcq_create(mmcq_t** out, const mmcq_grid* g, double Ms, double Aex, double 
     P.TX = 8;
     while (P.TX > 1 && P.TX / 2 >= P.hx) P.TX /= 2;
     while (P.TX > 1 && !col_fits(P)) P.TX /= 2;
-    if (!col_fits(P) || !fft_fits(3, P.L)) return bail(MMCQ_ERR_UNSUPPORTED);
+    if (!col_fits(P)) return bail(MMCQ_ERR_UNSUPPORTED);
     P.NT = (P.hx + P.TX - 1) / P.TX;
+    P.lt = 0;
+    while ((1 << P.lt) < P.TX) P.lt++;
+    P.R = rows_per_block(P.L, P.nrows);
+    P.nblk = (P.nrows + P.R - 1) / P.R;
+    if (!x_fits(P)) return bail(MMCQ_ERR_UNSUPPORTED);
+    P.fd_nx = make_fastdiv((unsigned)P.nx);
+    P.fd_ny = make_fastdiv((unsigned)P.ny);
+    P.fd_L1 = make_fastdiv((unsigned)(P.L + 1));
+    P.fd_half = make_fastdiv((unsigned)(P.L / 2 + 1));
 
     Material& M = h->mat;
     M.exch[0] = (float)(2.0 * Aex / (g->dx * g->dx));
@@ -311,8 +324,8 @@ int mmcq_create(mmcq_t** out, const mmcq_grid* g, double Ms, double Aex, double 
     Bf.prof = nullptr;
     Bf.ip = (InstParams*)A(sizeof(InstParams) * P.B);
     Bf.st = (InstState*)A(sizeof(InstState) * P.B);
-    Bf.xpart = (double*)A(sizeof(double) * (long long)P.B * P.nrows);
-    Bf.epart = (float*)A(sizeof(float) * (long long)P.B * P.nrows);
+    Bf.xpart = (double*)A(sizeof(double) * (long long)P.B * P.nblk);
+    Bf.epart = (float*)A(sizeof(float) * (long long)P.B * P.nblk);
     Bf.counter = (unsigned*)A(sizeof(unsigned) * P.B);
     Bf.hcap = 1 << 16;
     Bf.hist = (double*)A(sizeof(double) * (long long)P.B * Bf.hcap);
@@ -569,9 +582,13 @@ int mmcq_step(mmcq_t* h, int64_t n, double dt) {
             }
         } else {
             for (int s = 0; s < 7; s++) {
+                // stage 1 is first-same-as-last in E-mode: it only needs a launch
+                // after a host-side change (P-mode recomputes it every attempt)
+                if (s == 0 && h->mode == CAV_E && !h->k1_dirty) continue;
                 A.stage = s;
                 int r = run_stage(h, A, B);
                 if (r) return r;
+                if (s == 0 && h->mode == CAV_E) h->k1_dirty = false;
             }
         }
     }

@@ -1,0 +1,320 @@
+// Column passes of the demag convolution: FFT along y (and z) of tiles of kx
+// columns of the half-spectrum, with the pointwise product by the symmetric
+// demag kernel H = N M (6 real components, mirror-reduced storage) between the
+// forward and the inverse transform of the last axis.  The paper lists the
+// demag field among the effective-field terms (Sec. 2.1); the zero-padded
+// convolution is the standard way to evaluate it.
+//
+// k_col_reg<P>: transform length P <= 1024 in registers (fftreg.cuh); each
+//   thread owns one column and loads its strided rows straight from global
+//   memory (consecutive threads = consecutive columns = contiguous memory).
+// k_col_gen: any power-of-two length, shared-memory Stockham (fft.cuh); used
+//   for transforms longer than 1024.
+#include "common.cuh"
+#include "fft.cuh"
+#include "fftreg.cuh"
+#include "kern_common.cuh"
+
+namespace mq {
+
+struct ColArgs {
+    const float2* in;
+    float2* out;
+    long long in_b, in_o, in_t, in_r;    // strides (float2) of instance, outer index, tile, row
+    long long out_b, out_o, out_t, out_r;
+    int P;          // transform length
+    int n_in;       // rows read (the rest are zero padding)
+    int n_out;      // rows written
+    int fwd, mult, inv;
+    int ncomp;      // 3: all components per block (needed for the product); 1: one each
+    int ky_is_row;  // product index: (ky, kz) = (row, 0) if set, else (outer, row)
+    int G;          // groups per block (power of two)
+    int group_tiles;  // 1: groups are consecutive kx tiles; 0: consecutive outer indices
+    int nouter;     // extent of the outer index
+};
+
+__device__ __forceinline__ void demag_product(const Plan& P, const float* __restrict__ kern, int kx, int ky,
+                                              int kz, float2& mx, float2& my, float2& mz) {
+    if (kx >= P.hx) { mx = my = mz = make_float2(0.f, 0.f); return; }
+    float sy = 1.f, sz = 1.f;
+    int kyr = ky, kzr = kz;
+    if (ky > P.py / 2) { kyr = P.py - ky; sy = -1.f; }
+    if (kz > P.pz / 2) { kzr = P.pz - kz; sz = -1.f; }
+    const float2* K = reinterpret_cast<const float2*>(kern + (((long long)kzr * P.hyk + kyr) * (P.NT * P.TX) + kx) * 6);
+    float2 k0 = __ldg(K), k1 = __ldg(K + 1), k2 = __ldg(K + 2);
+    float xx = k0.x, yy = k0.y, zz = k1.x;
+    float xy = sy * k1.y, xz = sz * k2.x, yz = sy * sz * k2.y;
+    float2 hx = make_float2(xx * mx.x + xy * my.x + xz * mz.x, xx * mx.y + xy * my.y + xz * mz.y);
+    float2 hy = make_float2(xy * mx.x + yy * my.x + yz * mz.x, xy * mx.y + yy * my.y + yz * mz.y);
+    float2 hz = make_float2(xz * mx.x + yz * my.x + zz * mz.x, xz * mx.y + yz * my.y + zz * mz.y);
+    mx = hx; my = hy; mz = hz;
+}
+
+// The product over every (row, kx column) of a block whose shared memory holds
+// rows of W values laid out [group][comp][tx] (ncomp = 3).
+__device__ __forceinline__ void block_product(const Plan& P, const Buffers& Bf, const ColArgs& C, float2* sm, int W,
+                                              int t0, int o0) {
+    const int TX = P.TX, lt = P.lt;
+    const int gt = C.G * TX;          // kx columns of the block (power of two)
+    const int lgt = lt + __ffs(C.G) - 1;
+    const int rw = 3 * TX;
+    for (int i = threadIdx.x; i < C.P * gt; i += blockDim.x) {
+        int r = i >> lgt, q = i & (gt - 1);
+        int g = q >> lt, tx = q & (TX - 1);
+        int t = C.group_tiles ? t0 + g : t0;
+        int o = C.group_tiles ? o0 : o0 + g;
+        float2* p = sm + r * W + g * rw + tx;
+        float2 mx = p[0], my = p[TX], mz = p[2 * TX];
+        int ky = C.ky_is_row ? r : o;
+        int kz = C.ky_is_row ? 0 : r;
+        if (t < P.NT && o < C.nouter) demag_product(P, Bf.kern, t * TX + tx, ky, kz, mx, my, mz);
+        p[0] = mx; p[TX] = my; p[2 * TX] = mz;
+    }
+}
+
+// One block = G groups x ncomp x TX columns (W columns) x N1 threads per
+// column.  Groups are consecutive kx tiles (y passes) or consecutive outer
+// indices (z pass); in both cases consecutive columns are adjacent in memory.
+template <int P>
+__global__ void __launch_bounds__(512) k_col_reg(Plan Pl, Buffers Bf, StageArgs A, ColArgs C) {
+    constexpr int NPT = ColShape<P>::NPT, N1 = ColShape<P>::N1;
+    extern __shared__ float2 sm[];
+    const int bz = blockIdx.z;
+    const int b = A.inst0 + (C.ncomp == 3 ? bz : bz / 3);
+    const int c0 = C.ncomp == 3 ? 0 : bz % 3;
+    if (stage_skips(Bf.st[b], A)) return;
+    const int TX = Pl.TX;
+    const int rw = C.ncomp * TX;
+    const int W = C.G * rw;
+    const int col = threadIdx.x % W;
+    const int j = threadIdx.x / W;
+    const int g = C.ncomp == 3 ? (col >> Pl.lt) / 3 : (col >> Pl.lt);
+    const int e = col - g * rw;
+    const int t0 = C.group_tiles ? blockIdx.x * C.G : blockIdx.y;
+    const int o0 = C.group_tiles ? blockIdx.y : blockIdx.x * C.G;
+    const int t = C.group_tiles ? t0 + g : t0;
+    const int o = C.group_tiles ? o0 : o0 + g;
+    const bool valid = t < Pl.NT && o < C.nouter;
+    const float2* in = C.in + b * C.in_b + o * C.in_o + t * C.in_t + c0 * TX + e;
+    float2* out = C.out + b * C.out_b + o * C.out_o + t * C.out_t + c0 * TX + e;
+
+    float2 v[NPT];
+#pragma unroll
+    for (int n2 = 0; n2 < NPT; n2++) {
+        const int r = j + N1 * n2;
+        v[n2] = (valid && r < C.n_in) ? in[r * C.in_r] : make_float2(0.f, 0.f);
+    }
+    if (C.fwd) col_fft<P, false>(v, sm, W, col, j, Bf.tw, Pl.twn);
+    if (C.mult) {
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < NPT; i++) sm[col_out_row<P>(j, i) * W + col] = v[i];
+        __syncthreads();
+        block_product(Pl, Bf, C, sm, W, t0, o0);
+        __syncthreads();
+#pragma unroll
+        for (int n2 = 0; n2 < NPT; n2++) v[n2] = sm[(j + N1 * n2) * W + col];
+    }
+    if (C.inv) col_fft<P, true>(v, sm, W, col, j, Bf.tw, Pl.twn);
+    if (!valid) return;
+    const bool transformed = C.fwd || C.inv;
+#pragma unroll
+    for (int i = 0; i < NPT; i++) {
+        const int r = transformed ? col_out_row<P>(j, i) : j + N1 * i;
+        if (r < C.n_out) out[r * C.out_r] = v[i];
+    }
+}
+
+// Generic shared-memory version (any power-of-two P up to 4096).
+template <int SLOTS>
+__global__ void __launch_bounds__(MAX_THREADS) k_col_gen(Plan P, Buffers Bf, StageArgs A, ColArgs C) {
+    extern __shared__ float2 sm[];
+    const int bz = blockIdx.z;
+    const int b = A.inst0 + (C.ncomp == 3 ? bz : bz / 3);
+    const int c0 = C.ncomp == 3 ? 0 : bz % 3;
+    if (stage_skips(Bf.st[b], A)) return;
+    const int TX = P.TX;
+    const int rw = C.ncomp * TX;
+    const int G = C.G;
+    const int W = G * rw;
+    const int t0 = C.group_tiles ? blockIdx.x * G : blockIdx.y;
+    const int o0 = C.group_tiles ? blockIdx.y : blockIdx.x * G;
+    const float2* in = C.in + b * C.in_b + c0 * TX;
+    float2* out = C.out + b * C.out_b + c0 * TX;
+    for (int i = threadIdx.x; i < C.P * W; i += blockDim.x) {
+        int r = i / W, q = i - r * W;
+        int g = q / rw, e = q - g * rw;
+        int t = C.group_tiles ? t0 + g : t0;
+        int o = C.group_tiles ? o0 : o0 + g;
+        float2 v = make_float2(0.f, 0.f);
+        if (r < C.n_in && t < P.NT && o < C.nouter) v = in[o * C.in_o + t * C.in_t + r * C.in_r + e];
+        sm[i] = v;
+    }
+    __syncthreads();
+    if (C.fwd) block_fft<true, SLOTS>(sm, C.P, W, W, 1, false, Bf.tw, P.twn);
+    if (C.mult) {
+        block_product(P, Bf, C, sm, W, t0, o0);
+        __syncthreads();
+    }
+    if (C.inv) block_fft<true, SLOTS>(sm, C.P, W, W, 1, true, Bf.tw, P.twn);
+    for (int i = threadIdx.x; i < C.n_out * W; i += blockDim.x) {
+        int r = i / W, q = i - r * W;
+        int g = q / rw, e = q - g * rw;
+        int t = C.group_tiles ? t0 + g : t0;
+        int o = C.group_tiles ? o0 : o0 + g;
+        if (t < P.NT && o < C.nouter) out[o * C.out_o + t * C.out_t + r * C.out_r + e] = sm[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launch
+// ---------------------------------------------------------------------------
+bool fft_fits(int nlines, int L) { return (nlines * L + 3) / 4 <= MAX_SLOTS * MAX_THREADS; }
+
+static int gen_threads(int nlines, int L, int* per) {
+    int slots = (nlines * L + 3) / 4;
+    *per = slots <= 2 * MAX_THREADS ? 2 : 4;
+    int th = (slots + *per - 1) / *per;
+    th = ((th + 31) / 32) * 32;
+    return th < 32 ? 32 : (th > MAX_THREADS ? MAX_THREADS : th);
+}
+
+template <int P>
+static cudaError_t launch_reg(const Plan& Pl, const Buffers& Bf, const StageArgs& A, const ColArgs& C, dim3 grid,
+                              int W, cudaStream_t s) {
+    constexpr int N1 = ColShape<P>::N1;
+    k_col_reg<P><<<grid, W * N1, (size_t)P * W * sizeof(float2), s>>>(Pl, Bf, A, C);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_col(const Plan& P, const Buffers& Bf, const StageArgs& A, const ColArgs& C, int nb,
+                              cudaStream_t s) {
+    const int W = C.G * C.ncomp * P.TX;
+    dim3 grid;
+    if (C.group_tiles) grid = dim3((P.NT + C.G - 1) / C.G, C.nouter, nb * (C.ncomp == 3 ? 1 : 3));
+    else grid = dim3((C.nouter + C.G - 1) / C.G, P.NT, nb * (C.ncomp == 3 ? 1 : 3));
+    switch (C.P) {
+        case 1: return launch_reg<1>(P, Bf, A, C, grid, W, s);
+        case 2: return launch_reg<2>(P, Bf, A, C, grid, W, s);
+        case 4: return launch_reg<4>(P, Bf, A, C, grid, W, s);
+        case 8: return launch_reg<8>(P, Bf, A, C, grid, W, s);
+        case 16: return launch_reg<16>(P, Bf, A, C, grid, W, s);
+        case 32: return launch_reg<32>(P, Bf, A, C, grid, W, s);
+        case 64: return launch_reg<64>(P, Bf, A, C, grid, W, s);
+        case 128: return launch_reg<128>(P, Bf, A, C, grid, W, s);
+        case 256: return launch_reg<256>(P, Bf, A, C, grid, W, s);
+        case 512: return launch_reg<512>(P, Bf, A, C, grid, W, s);
+        case 1024: return launch_reg<1024>(P, Bf, A, C, grid, W, s);
+        default: break;
+    }
+    int per;
+    int th = gen_threads(W, C.P, &per);
+    size_t sm = (size_t)C.P * W * sizeof(float2);
+    if (per == 2) k_col_gen<2><<<grid, th, sm, s>>>(P, Bf, A, C);
+    else k_col_gen<4><<<grid, th, sm, s>>>(P, Bf, A, C);
+    return cudaGetLastError();
+}
+
+// Threads of a register-path block: W columns x P / min(P, 32) threads each.
+static int reg_threads(int P, int W) { return W * (P <= 32 ? 1 : P / 32); }
+
+// Group count (power of two, <= limit) for a column pass: as large as keeps
+// the block within `max_threads` threads and `smem_cap` bytes.
+static int pick_groups(int width, int P, int limit, int max_threads, size_t smem_cap) {
+    int G = 1;
+    while (G * 2 <= limit) {
+        int W = G * 2 * width;
+        size_t sm = (size_t)P * W * sizeof(float2);
+        bool ok = sm <= smem_cap && (P > 1024 ? fft_fits(W, P) : reg_threads(P, W) <= max_threads);
+        if (!ok) break;
+        G *= 2;
+    }
+    return G;
+}
+
+// Layout strides of the tiled spectra.
+static void spec_strides(const Plan& P, int rows, long long& sb, long long& sz, long long& st, long long& sr) {
+    sr = 3LL * P.TX;                    // one row (ky or y) of a tile
+    st = (long long)rows * sr;          // one tile
+    sz = (long long)P.NT * st;          // one z plane
+    sb = (long long)P.nz * sz;          // one instance
+}
+
+static const size_t COL_SMEM_CAP = 48 * 1024;
+static const int COL_MAX_THREADS = 256;
+
+// One launch of the demag convolution: part 0 = 2-D (fwd y, product, inv y);
+// 3-D: part 1 = forward y, 2 = z forward / product / z inverse, 3 = inverse y.
+cudaError_t launch_conv_part(const Plan& P, const Buffers& Bf, const StageArgs& A, int nb, cudaStream_t s, int part) {
+    long long sb, sz, st, sr, tb, tz, tt, tr;
+    spec_strides(P, P.ny, sb, sz, st, sr);
+    spec_strides(P, P.py, tb, tz, tt, tr);
+    ColArgs C{};
+    if (part == 0) {
+        C.in = Bf.spec; C.out = Bf.spec;
+        C.in_b = C.out_b = sb; C.in_o = C.out_o = 0; C.in_t = C.out_t = st; C.in_r = C.out_r = sr;
+        C.P = P.py; C.n_in = P.ny; C.n_out = P.ny;
+        C.fwd = 1; C.mult = 1; C.inv = 1; C.ncomp = 3; C.ky_is_row = 1;
+        C.group_tiles = 1; C.nouter = 1;
+        C.G = pick_groups(3 * P.TX, P.py, P.NT, COL_MAX_THREADS, COL_SMEM_CAP);
+    } else if (part == 1 || part == 3) {
+        bool fwd = part == 1;
+        C.in = fwd ? Bf.spec : Bf.spec2;
+        C.out = fwd ? Bf.spec2 : Bf.spec;
+        C.in_b = fwd ? sb : tb; C.in_o = fwd ? sz : tz; C.in_t = fwd ? st : tt; C.in_r = fwd ? sr : tr;
+        C.out_b = fwd ? tb : sb; C.out_o = fwd ? tz : sz; C.out_t = fwd ? tt : st; C.out_r = fwd ? tr : sr;
+        C.P = P.py; C.n_in = fwd ? P.ny : P.py; C.n_out = fwd ? P.py : P.ny;
+        C.fwd = fwd; C.inv = !fwd;
+        bool three = P.py <= 1024 ? reg_threads(P.py, 3 * P.TX) <= 512 && (size_t)P.py * 3 * P.TX * 8 <= COL_SMEM_CAP
+                                  : fft_fits(3 * P.TX, P.py) && (size_t)P.py * 3 * P.TX * 8 <= COL_SMEM_CAP;
+        C.ncomp = three ? 3 : 1;
+        C.group_tiles = 1; C.nouter = P.nz;
+        C.G = pick_groups(C.ncomp * P.TX, P.py, P.NT, COL_MAX_THREADS, COL_SMEM_CAP);
+    } else {
+        C.in = Bf.spec2; C.out = Bf.spec2;
+        C.in_b = C.out_b = tb; C.in_o = C.out_o = tr; C.in_t = C.out_t = tt; C.in_r = C.out_r = tz;
+        C.P = P.pz; C.n_in = P.nz; C.n_out = P.nz; C.fwd = 1; C.mult = 1; C.inv = 1; C.ncomp = 3; C.ky_is_row = 0;
+        C.group_tiles = 0; C.nouter = P.py;
+        C.G = pick_groups(3 * P.TX, P.pz, P.py, COL_MAX_THREADS, COL_SMEM_CAP);
+    }
+    return launch_col(P, Bf, A, C, nb, s);
+}
+
+cudaError_t launch_convolution(const Plan& P, const Buffers& Bf, const StageArgs& A, int nb, cudaStream_t s) {
+    if (P.nz == 1) return launch_conv_part(P, Bf, A, nb, s, 0);
+    cudaError_t e;
+    for (int part = 1; part <= 3; part++)
+        if ((e = launch_conv_part(P, Bf, A, nb, s, part)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+int convolution_launches(const Plan& P) { return P.nz == 1 ? 1 : 3; }
+
+// Whether the column passes of a plan fit (at group count 1).
+bool col_fits(const Plan& P) {
+    const size_t cap = 200 * 1024;
+    auto fits = [&](int ncomp, int L) {
+        size_t sm = (size_t)L * ncomp * P.TX * 8;
+        if (sm > cap) return false;
+        return L <= 1024 ? reg_threads(L, ncomp * P.TX) <= 512 : fft_fits(ncomp * P.TX, L);
+    };
+    if (P.nz == 1) return fits(3, P.py);
+    return fits(1, P.py) && fits(3, P.pz);
+}
+
+cudaError_t col_init() {
+    cudaError_t e;
+    if ((e = upload_tw32()) != cudaSuccess) return e;
+    const int lim = 200 * 1024;
+    if ((e = cudaFuncSetAttribute(k_col_gen<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_col_gen<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess) return e;
+#define MMCQ_SET(Pv)                                                                                              \
+    if ((e = cudaFuncSetAttribute(k_col_reg<Pv>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess) \
+        return e;
+    MMCQ_SET(1) MMCQ_SET(2) MMCQ_SET(4) MMCQ_SET(8) MMCQ_SET(16) MMCQ_SET(32) MMCQ_SET(64) MMCQ_SET(128)
+    MMCQ_SET(256) MMCQ_SET(512) MMCQ_SET(1024)
+#undef MMCQ_SET
+    return cudaSuccess;
+}
+
+}  // namespace mq

@@ -9,10 +9,28 @@ namespace mq {
 constexpr int MAX_STAGES = 7;
 constexpr int MAX_SLOTS = 4;      // 4-value FFT slots held per thread per stage
 constexpr int MAX_THREADS = 1024;
+constexpr int XINV_THREADS = 768;  // register budget of the torque kernel (85 per thread)
 
 enum Kind { KIND_RK4 = 0, KIND_DP45 = 1 };
 enum CavMode { CAV_E = 0, CAV_P = 1 };
 enum Flag { FLAG_NAN = 1, FLAG_DT_UNDERFLOW = 2, FLAG_HIST_FULL = 4 };
+
+// x / d for 0 <= x < 2^31 by multiply-high (Granlund & Montgomery 1994):
+// s = ceil(log2 d), m = floor(2^32 (2^s - d) / d) + 1, q = (mulhi(x, m) + x) >> s.
+struct FastDiv {
+    unsigned d, m, s;
+};
+
+inline FastDiv make_fastdiv(unsigned d) {
+    unsigned s = 0;
+    while ((1ull << s) < d) s++;
+    unsigned long long m = ((1ull << 32) * ((1ull << s) - d)) / d + 1;
+    return FastDiv{d, (unsigned)m, s};
+}
+
+#ifdef __CUDACC__
+__device__ __forceinline__ unsigned fdiv(unsigned x, const FastDiv& f) { return (__umulhi(x, f.m) + x) >> f.s; }
+#endif
 
 // Shape of one handle: grid, padding and the spectrum tiling.
 struct Plan {
@@ -25,6 +43,10 @@ struct Plan {
     int NT;           // tiles per row, NT * TX >= hx
     int hyk, hzk;     // stored kernel extent along ky, kz: py/2 + 1, pz/2 + 1
     int nrows;        // ny * nz rows per instance
+    int R;            // x rows per block in the x passes
+    int nblk;         // x-pass blocks per instance: ceil(nrows / R)
+    int lt;           // log2(TX)
+    FastDiv fd_nx, fd_ny, fd_L1, fd_half;   // divisions by nx, ny, L + 1, L / 2 + 1
     int twn;          // twiddle table length (power of two >= every FFT length)
 };
 

@@ -41,8 +41,8 @@ __device__ __forceinline__ void radix4(float2* v, bool inv) {
 // threads to consecutive lines (good when lines are adjacent in memory),
 // otherwise to consecutive elements of one line.  Unnormalised; the caller
 // must have synchronised before the call, and the call ends synchronised.
-// Requires nlines * L / 4 <= MAX_SLOTS * blockDim.x.
-template <bool LINE_FAST>
+// Requires nlines * L / 4 <= SLOTS * blockDim.x.
+template <bool LINE_FAST, int SLOTS>
 __device__ void block_fft(float2* s, int L, int nlines, int es, int ls, bool inv,
                           const float2* __restrict__ tw, int twn) {
     for (int Ns = 1; Ns < L;) {
@@ -51,11 +51,11 @@ __device__ void block_fft(float2* s, int L, int nlines, int es, int ls, bool inv
         const int ntask = tpl * nlines;
         const int per_slot = 4 / R;            // butterflies held in one 4-value slot
         const int twstep_base = twn / (Ns * R);
-        float2 v[MAX_SLOTS][4];
-        int off[MAX_SLOTS][2];                 // line base of each butterfly in the slot
-        int jj[MAX_SLOTS][2];
+        float2 v[SLOTS][4];
+        int off[SLOTS][2];                 // line base of each butterfly in the slot
+        int jj[SLOTS][2];
 #pragma unroll
-        for (int q = 0; q < MAX_SLOTS; q++) {
+        for (int q = 0; q < SLOTS; q++) {
 #pragma unroll
             for (int h = 0; h < 2; h++) {
                 int t = (threadIdx.x + q * blockDim.x) * per_slot + h;
@@ -85,7 +85,7 @@ __device__ void block_fft(float2* s, int L, int nlines, int es, int ls, bool inv
         }
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < MAX_SLOTS; q++) {
+        for (int q = 0; q < SLOTS; q++) {
 #pragma unroll
             for (int h = 0; h < 2; h++) {
                 if (off[q][h] >= 0) {

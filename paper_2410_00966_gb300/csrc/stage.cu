@@ -4,10 +4,8 @@
 //   k_xfwd : stage input m_s = m0 + dt sum_j a_sj k_j (Eq. llg integrated by
 //            RK4 / Dormand-Prince), M = Ms m_s, zero-padded real-to-complex FFT
 //            along x, written to a tiled half-spectrum.
-//   k_col  : FFT along y (and z) of a tile of kx columns, the pointwise product
-//            with the symmetric demag kernel H = N M (6 real components,
-//            mirror-reduced storage), inverse FFT.  2-D grids do everything
-//            in one launch; 3-D grids use y-forward, z-convolve, y-inverse.
+//   k_col  : (col.cu) FFT along y (and z) of tiles of kx columns, the
+//            pointwise product with the symmetric demag kernel, inverse FFT.
 //   k_xinv : complex-to-real inverse FFT along x giving B_demag, then per cell
 //            exchange + anisotropy + Zeeman + cavity B_rms Gamma (Sec. 2.1
 //            field terms, Eq. bcav), the LLG torque (Eq. llg), the RK
@@ -18,7 +16,8 @@
 #include <math.h>
 
 #include "common.cuh"
-#include "fft.cuh"
+#include "fftreg.cuh"
+#include "kern_common.cuh"
 
 namespace mq {
 
@@ -30,171 +29,6 @@ __constant__ double c_bd[2][MAX_STAGES];
 __constant__ double c_cd[2][MAX_STAGES];   // stage times
 __constant__ float c_ef[MAX_STAGES];       // DP45 error weights b5 - b4
 
-// Whether this instance does nothing in this launch.
-__device__ __forceinline__ bool stage_skips(const InstState& s, const StageArgs& A) {
-    if (A.field_only) return false;
-    if (s.done) return true;
-    if (A.kind == KIND_DP45 && A.stage == 0 && s.have_k1) return true;
-    return false;
-}
-
-__device__ __forceinline__ int k_slot(const InstState& s, int j) {
-    // DP45: stage 1 lives in k1slot (FSAL swap between buffers 0 and 6)
-    return j == 0 ? s.k1slot : j;
-}
-
-// ---------------------------------------------------------------------------
-// x forward: stage input, M = Ms m_s, packed real FFT of length px.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(MAX_THREADS) k_xfwd(Plan P, Buffers Bf, StageArgs A) {
-    extern __shared__ float2 sm[];
-    const int row = blockIdx.x;
-    const int b = A.inst0 + blockIdx.y;
-    const InstState st = Bf.st[b];
-    if (stage_skips(st, A)) return;
-    const int L = P.L;
-    const int y = row % P.ny, z = row / P.ny;
-    const long long base = (long long)b * P.N + (long long)row * P.nx;
-    float2* zs = sm;  // [3][L]
-    for (int i = threadIdx.x; i < 3 * L; i += blockDim.x) zs[i] = make_float2(0.f, 0.f);
-    __syncthreads();
-
-    const float4* m0 = Bf.m[st.mcur] + base;
-    const int s = A.stage;
-    const float dt = (float)st.dt;
-    const bool form = !A.field_only && s > 0;
-    const bool dp_last = A.kind == KIND_DP45 && s == 6 && !A.field_only;
-    for (int x = threadIdx.x; x < P.nx; x += blockDim.x) {
-        float4 v = m0[x];
-        if (form) {
-            float ax = 0.f, ay = 0.f, az = 0.f;
-            float ex = 0.f, ey = 0.f, ez = 0.f;
-            for (int j = 0; j < s; j++) {
-                float w = dp_last ? c_bf[1][j] : c_af[A.kind][s][j];
-                float e = dp_last ? c_ef[j] : 0.f;
-                if (w == 0.f && e == 0.f) continue;   // uniform: skips the load
-                float4 kj = Bf.k[A.kind == KIND_DP45 ? k_slot(st, j) : j][base + x];
-                ax += w * kj.x; ay += w * kj.y; az += w * kj.z;
-                ex += e * kj.x; ey += e * kj.y; ez += e * kj.z;
-            }
-            v.x += dt * ax; v.y += dt * ay; v.z += dt * az;
-            if (dp_last) {
-                // 5th-order solution, renormalised: stage 7 is evaluated there
-                float r2 = v.x * v.x + v.y * v.y + v.z * v.z;
-                float inv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-                v.x *= inv; v.y *= inv; v.z *= inv;
-                Bf.m[st.mcur ^ 1][base + x] = v;
-                Bf.e6[base + x] = make_float4(dt * ex, dt * ey, dt * ez, 0.f);
-            } else {
-                Bf.ms[base + x] = v;
-            }
-        }
-        float Mx = v.w * v.x, My = v.w * v.y, Mz = v.w * v.z;
-        int n = x >> 1;
-        if (x & 1) { zs[n].y = Mx; zs[L + n].y = My; zs[2 * L + n].y = Mz; }
-        else { zs[n].x = Mx; zs[L + n].x = My; zs[2 * L + n].x = Mz; }
-    }
-    __syncthreads();
-    block_fft<false>(zs, L, 3, 1, L, false, Bf.tw, P.twn);
-
-    // X[k] = E[k] + W^k O[k], E = (Z[k] + conj Z[L-k]) / 2, O = -i (Z[k] - conj Z[L-k]) / 2
-    const int TX = P.TX;
-    float2* out = Bf.spec + (((long long)b * P.nz + z) * P.NT * P.ny + y) * 3 * TX;
-    const long long tstride = (long long)P.ny * 3 * TX;
-    const int twstep = P.twn / P.px;
-    const int W3 = P.NT * 3 * TX;
-    for (int idx = threadIdx.x; idx < W3; idx += blockDim.x) {
-        int t = idx / (3 * TX);
-        int rem = idx - t * 3 * TX;
-        int c = rem / TX;
-        int tx = rem - c * TX;
-        int k = t * TX + tx;
-        float2 X = make_float2(0.f, 0.f);
-        if (k <= L) {
-            float2 Zk = zs[c * L + (k == L ? 0 : k)];
-            float2 Zc = conjf2(zs[c * L + (k == 0 ? 0 : L - k)]);
-            float2 E = make_float2(0.5f * (Zk.x + Zc.x), 0.5f * (Zk.y + Zc.y));
-            float2 D = make_float2(0.5f * (Zk.x - Zc.x), 0.5f * (Zk.y - Zc.y));
-            float2 wD = cmul(twiddle(Bf.tw, k * twstep, false), D);
-            X = make_float2(E.x + wD.y, E.y - wD.x);
-        }
-        out[t * tstride + c * TX + tx] = X;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// column FFT / demag product along y or z on a tile of TX kx columns.
-// ---------------------------------------------------------------------------
-struct ColArgs {
-    const float2* in;
-    float2* out;
-    long long in_b, in_o, in_t, in_r;    // strides (float2) of instance, outer index, tile, row
-    long long out_b, out_o, out_t, out_r;
-    int P;          // transform length
-    int n_in;       // rows read (the rest are zero padding)
-    int n_out;      // rows written
-    int fwd, mult, inv;
-    int ncomp;      // 3: all components per block (needed for the product); 1: one each
-    int ky_is_row;  // product index: (ky, kz) = (row, 0) if set, else (outer, row)
-};
-
-__device__ __forceinline__ void demag_product(const Plan& P, const float* __restrict__ kern, int kx, int ky,
-                                              int kz, float2& mx, float2& my, float2& mz) {
-    if (kx >= P.hx) { mx = my = mz = make_float2(0.f, 0.f); return; }
-    float sy = 1.f, sz = 1.f;
-    int kyr = ky, kzr = kz;
-    if (ky > P.py / 2) { kyr = P.py - ky; sy = -1.f; }
-    if (kz > P.pz / 2) { kzr = P.pz - kz; sz = -1.f; }
-    const float* K = kern + (((long long)kzr * P.hyk + kyr) * (P.NT * P.TX) + kx) * 6;
-    float xx = __ldg(K), yy = __ldg(K + 1), zz = __ldg(K + 2);
-    float xy = sy * __ldg(K + 3), xz = sz * __ldg(K + 4), yz = sy * sz * __ldg(K + 5);
-    float2 hx = make_float2(xx * mx.x + xy * my.x + xz * mz.x, xx * mx.y + xy * my.y + xz * mz.y);
-    float2 hy = make_float2(xy * mx.x + yy * my.x + yz * mz.x, xy * mx.y + yy * my.y + yz * mz.y);
-    float2 hz = make_float2(xz * mx.x + yz * my.x + zz * mz.x, xz * mx.y + yz * my.y + zz * mz.y);
-    mx = hx; my = hy; mz = hz;
-}
-
-__global__ void __launch_bounds__(MAX_THREADS) k_col(Plan P, Buffers Bf, StageArgs A, ColArgs C) {
-    extern __shared__ float2 sm[];
-    const int t = blockIdx.x;
-    const int outer = blockIdx.y;
-    const int bz = blockIdx.z;
-    const int b = A.inst0 + (C.ncomp == 3 ? bz : bz / 3);
-    const int c0 = C.ncomp == 3 ? 0 : bz % 3;
-    if (stage_skips(Bf.st[b], A)) return;
-    const int TX = P.TX;
-    const int rw = C.ncomp * TX;   // float2 per row in shared memory
-    const float2* in = C.in + b * C.in_b + outer * C.in_o + t * C.in_t + c0 * TX;
-    float2* out = C.out + b * C.out_b + outer * C.out_o + t * C.out_t + c0 * TX;
-    // load rows (contiguous rw values per row), zero-pad to P rows
-    for (int i = threadIdx.x; i < C.P * rw; i += blockDim.x) {
-        int r = i / rw, e = i - r * rw;
-        sm[i] = r < C.n_in ? in[r * C.in_r + e] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    if (C.fwd) block_fft<true>(sm, C.P, rw, rw, 1, false, Bf.tw, P.twn);
-    if (C.mult) {
-        for (int i = threadIdx.x; i < C.P * TX; i += blockDim.x) {
-            int r = i / TX, tx = i - r * TX;
-            float2* p = sm + r * rw + tx;
-            float2 mx = p[0], my = p[TX], mz = p[2 * TX];
-            int ky = C.ky_is_row ? r : outer;
-            int kz = C.ky_is_row ? 0 : r;
-            demag_product(P, Bf.kern, t * TX + tx, ky, kz, mx, my, mz);
-            p[0] = mx; p[TX] = my; p[2 * TX] = mz;
-        }
-        __syncthreads();
-    }
-    if (C.inv) block_fft<true>(sm, C.P, rw, rw, 1, true, Bf.tw, P.twn);
-    for (int i = threadIdx.x; i < C.n_out * rw; i += blockDim.x) {
-        int r = i / rw, e = i - r * rw;
-        out[r * C.out_r + e] = sm[i];
-    }
-}
-
-// ---------------------------------------------------------------------------
-// x inverse + local fields + torque + RK bookkeeping + cavity reduction.
-// ---------------------------------------------------------------------------
 __device__ __forceinline__ double warp_sum_d(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return v;
@@ -341,25 +175,144 @@ __device__ void finish_stage(const Plan& P, const Material& mat, const StageArgs
     }
 }
 
-__global__ void __launch_bounds__(MAX_THREADS) k_xinv(Plan P, Material mat, Buffers Bf, StageArgs A) {
+// ---------------------------------------------------------------------------
+// x forward: stage input, M = Ms m_s, packed real FFT of length px = 2L.
+// R consecutive rows per block; shared memory zs[n][line], line = 3 r + comp.
+// ---------------------------------------------------------------------------
+template <int L>
+__global__ void __launch_bounds__(512) k_xfwd(Plan P, Buffers Bf, StageArgs A) {
+    constexpr int NPT = ColShape<L>::NPT, N1 = ColShape<L>::N1;
+    extern __shared__ float2 sm[];
+    const int b = A.inst0 + blockIdx.y;
+    const InstState st = Bf.st[b];
+    if (stage_skips(st, A)) return;
+    const int nx = P.nx;
+    const int row0 = blockIdx.x * P.R;
+    const int nr = min(P.R, P.nrows - row0);
+    const int ld = 3 * P.R;
+    const long long base = (long long)b * P.N + (long long)row0 * nx;
+    float2* zs = sm;
+    for (int i = threadIdx.x; i < L * ld; i += blockDim.x) zs[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+
+    const float4* m0 = Bf.m[st.mcur] + base;
+    const int s = A.stage;
+    const float dt = (float)st.dt;
+    const bool form = !A.field_only && s > 0;
+    const bool dp_last = A.kind == KIND_DP45 && s == 6 && !A.field_only;
+    const float4* kp[MAX_STAGES - 1];
+    float kw[MAX_STAGES - 1], ke[MAX_STAGES - 1];
+    int nk = 0;
+#pragma unroll
+    for (int q = 0; q < MAX_STAGES - 1; q++) { kp[q] = Bf.k[0]; kw[q] = 0.f; ke[q] = 0.f; }
+    if (form) {
+        for (int j = 0; j < s; j++) {
+            float w = dp_last ? c_bf[1][j] : c_af[A.kind][s][j];
+            float e = dp_last ? c_ef[j] : 0.f;
+            if (w == 0.f && e == 0.f) continue;
+            kp[nk] = Bf.k[A.kind == KIND_DP45 ? k_slot(st, j) : j] + base;
+            kw[nk] = dt * w;
+            ke[nk] = dt * e;
+            nk++;
+        }
+    }
+    float4* ms_out = dp_last ? Bf.m[st.mcur ^ 1] + base : Bf.ms + base;
+    for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) {
+        float4 v = m0[i];
+        if (form) {
+            float ax = 0.f, ay = 0.f, az = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
+#pragma unroll
+            for (int q = 0; q < MAX_STAGES - 1; q++) {
+                if (q < nk) {
+                    float4 kj = kp[q][i];
+                    ax += kw[q] * kj.x; ay += kw[q] * kj.y; az += kw[q] * kj.z;
+                    ex += ke[q] * kj.x; ey += ke[q] * kj.y; ez += ke[q] * kj.z;
+                }
+            }
+            v.x += ax; v.y += ay; v.z += az;
+            if (dp_last) {
+                // 5th-order solution, renormalised: stage 7 is evaluated there
+                float r2 = v.x * v.x + v.y * v.y + v.z * v.z;
+                float inv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                v.x *= inv; v.y *= inv; v.z *= inv;
+                Bf.e6[base + i] = make_float4(ex, ey, ez, 0.f);
+            }
+            ms_out[i] = v;
+        }
+        const int r = (int)fdiv((unsigned)i, P.fd_nx), x = i - r * nx;
+        float2* zr = zs + (x >> 1) * ld + 3 * r;
+        float Mx = v.w * v.x, My = v.w * v.y, Mz = v.w * v.z;
+        if (x & 1) { zr[0].y = Mx; zr[1].y = My; zr[2].y = Mz; }
+        else { zr[0].x = Mx; zr[1].x = My; zr[2].x = Mz; }
+    }
+    __syncthreads();
+    {
+        const int line = threadIdx.x % ld, j = threadIdx.x / ld;
+        float2 v[NPT];
+#pragma unroll
+        for (int n2 = 0; n2 < NPT; n2++) v[n2] = zs[(j + N1 * n2) * ld + line];
+        col_fft<L, false>(v, zs, ld, line, j, Bf.tw, P.twn);
+#pragma unroll
+        for (int i = 0; i < NPT; i++) zs[col_out_row<L>(j, i) * ld + line] = v[i];
+    }
+    __syncthreads();
+
+    // X[k] = E[k] + W^k O[k], E = (Z[k] + conj Z[L-k]) / 2, O = -i (Z[k] - conj Z[L-k]) / 2
+    const int TX = P.TX, lt = P.lt;
+    const long long tstride = (long long)P.ny * 3 * TX;
+    const int twstep = P.twn / P.px;
+    const int W3 = P.NT * 3 * TX;
+    for (int r = 0; r < nr; r++) {
+        const int row = row0 + r;
+        const int z = (int)fdiv((unsigned)row, P.fd_ny), y = row - z * P.ny;
+        float2* out = Bf.spec + (((long long)b * P.nz + z) * P.NT * P.ny + y) * 3 * TX;
+        for (int idx = threadIdx.x; idx < W3; idx += blockDim.x) {
+            const int t = (idx >> lt) / 3;
+            const int ctx = idx - t * 3 * TX;
+            const int c = ctx >> lt, tx = ctx & (TX - 1);
+            const int k = t * TX + tx;
+            const int line = 3 * r + c;
+            float2 X = make_float2(0.f, 0.f);
+            if (k <= L) {
+                float2 Zk = zs[(k == L ? 0 : k) * ld + line];
+                float2 Zc = conjf2(zs[(k == 0 ? 0 : L - k) * ld + line]);
+                float2 E = make_float2(0.5f * (Zk.x + Zc.x), 0.5f * (Zk.y + Zc.y));
+                float2 D = make_float2(0.5f * (Zk.x - Zc.x), 0.5f * (Zk.y - Zc.y));
+                float2 wD = cmul(twiddle(Bf.tw, k * twstep, false), D);
+                X = make_float2(E.x + wD.y, E.y - wD.x);
+            }
+            out[t * tstride + ctx] = X;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// x inverse + local fields + torque + RK bookkeeping + cavity reduction.
+// Shared memory: xs[k][line] (k <= L, line = 3 r + comp), then m rows.
+// ---------------------------------------------------------------------------
+template <int L>
+__global__ void __launch_bounds__(512) k_xinv(Plan P, Material mat, Buffers Bf, StageArgs A) {
+    constexpr int NPT = ColShape<L>::NPT, N1 = ColShape<L>::N1;
     extern __shared__ float2 sm[];
     __shared__ double s_red[32];
     __shared__ float s_redf[32];
     __shared__ double s_gamma;
     __shared__ int s_last;
-    const int row = blockIdx.x;
     const int b = A.inst0 + blockIdx.y;
     const InstState st = Bf.st[b];
     if (stage_skips(st, A)) return;
     const InstParams ip = Bf.ip[b];
-    const int L = P.L, TX = P.TX, nx = P.nx;
-    const int y = row % P.ny, z = row / P.ny;
+    const int TX = P.TX, nx = P.nx, lt = P.lt;
+    const int row0 = blockIdx.x * P.R;
+    const int nr = min(P.R, P.nrows - row0);
+    const int ld = 3 * P.R;
     const long long cb = (long long)b * P.N;
-    const long long base = cb + (long long)row * nx;
+    const long long base = cb + (long long)row0 * nx;
     const int s = A.stage;
     const int K = A.kind;
-    float2* xs = sm;                                   // [3][L+1]
-    float4* mrow = reinterpret_cast<float4*>(sm + 3 * (L + 1) + ((3 * (L + 1)) & 1));  // [nx]
+    float2* xs = sm;                                   // [L + 1][ld]
+    const int xs_n = (L + 1) * ld + (((L + 1) * ld) & 1);
+    float4* mrow = reinterpret_cast<float4*>(sm + xs_n);  // [row][nx]
 
     // which buffer holds the stage input m_s
     const float4* msrc;
@@ -367,15 +320,19 @@ __global__ void __launch_bounds__(MAX_THREADS) k_xinv(Plan P, Material mat, Buff
     else if (K == KIND_DP45 && s == 6) msrc = Bf.m[st.mcur ^ 1];
     else msrc = Bf.ms;
 
-    // load the half spectrum row X[0..L] of the three components
-    const float2* in = Bf.spec + (((long long)b * P.nz + z) * P.NT * P.ny + y) * 3 * TX;
+    // half-spectrum rows X[0..L] of the three components of every row
     const long long tstride = (long long)P.ny * 3 * TX;
-    for (int idx = threadIdx.x; idx < 3 * (L + 1); idx += blockDim.x) {
-        int c = idx / (L + 1), k = idx - c * (L + 1);
-        int t = k / TX, tx = k - t * TX;
-        xs[idx] = in[t * tstride + c * TX + tx];
+    for (int r = 0; r < nr; r++) {
+        const int row = row0 + r;
+        const int z = (int)fdiv((unsigned)row, P.fd_ny), y = row - z * P.ny;
+        const float2* in = Bf.spec + (((long long)b * P.nz + z) * P.NT * P.ny + y) * 3 * TX;
+        for (int idx = threadIdx.x; idx < 3 * (L + 1); idx += blockDim.x) {
+            const int c = (int)fdiv((unsigned)idx, P.fd_L1), k = idx - c * (L + 1);
+            const int t = k >> lt, tx = k & (TX - 1);
+            xs[k * ld + 3 * r + c] = in[t * tstride + c * TX + tx];
+        }
     }
-    for (int x = threadIdx.x; x < nx; x += blockDim.x) mrow[x] = msrc[base + x];
+    for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) mrow[i] = msrc[base + i];
     if (threadIdx.x == 0) {
         double G = 0.0;
         if (ip.cav_on) {
@@ -387,44 +344,56 @@ __global__ void __launch_bounds__(MAX_THREADS) k_xinv(Plan P, Material mat, Buff
     __syncthreads();
     // Z[k] = (X[k] + conj X[L-k]) + i e^{+2 pi i k / px} (X[k] - conj X[L-k]), in place by pairs
     const int twstep = P.twn / P.px;
-    for (int idx = threadIdx.x; idx < 3 * (L / 2 + 1); idx += blockDim.x) {
-        int c = idx / (L / 2 + 1), k = idx - c * (L / 2 + 1);
-        float2* X = xs + c * (L + 1);
-        int kk = L - k;
-        float2 a = X[k], bq = X[kk];
-        // Z[k]
+    constexpr int HALF = L / 2 + 1;
+    for (int idx = threadIdx.x; idx < 3 * nr * HALF; idx += blockDim.x) {
+        const int line = idx / HALF, k = idx - line * HALF;
+        const int kk = L - k;
+        float2 a = xs[k * ld + line], bq = xs[kk * ld + line];
         float2 ca = conjf2(bq);
         float2 sum = cadd(a, ca), dif = csub(a, ca);
-        float2 w = twiddle(Bf.tw, k * twstep, true);
-        float2 wd = cmul(w, dif);
+        float2 wd = cmul(twiddle(Bf.tw, k * twstep, true), dif);
         float2 zk = make_float2(sum.x - wd.y, sum.y + wd.x);   // sum + i wd
         if (k != 0 && kk != k) {
             float2 cb2 = conjf2(a);
             float2 sum2 = cadd(bq, cb2), dif2 = csub(bq, cb2);
-            float2 w2 = twiddle(Bf.tw, kk * twstep, true);
-            float2 wd2 = cmul(w2, dif2);
-            X[kk] = make_float2(sum2.x - wd2.y, sum2.y + wd2.x);
+            float2 wd2 = cmul(twiddle(Bf.tw, kk * twstep, true), dif2);
+            xs[kk * ld + line] = make_float2(sum2.x - wd2.y, sum2.y + wd2.x);
         }
-        X[k] = zk;
+        xs[k * ld + line] = zk;
     }
     __syncthreads();
-    block_fft<false>(xs, L, 3, 1, L + 1, true, Bf.tw, P.twn);
+    {
+        const int line = threadIdx.x % ld, j = threadIdx.x / ld;
+        float2 v[NPT];
+#pragma unroll
+        for (int n2 = 0; n2 < NPT; n2++) v[n2] = xs[(j + N1 * n2) * ld + line];
+        col_fft<L, true>(v, xs, ld, line, j, Bf.tw, P.twn);
+#pragma unroll
+        for (int i = 0; i < NPT; i++) xs[col_out_row<L>(j, i) * ld + line] = v[i];
+    }
+    __syncthreads();
 
     const bool want_demag = A.terms & 1, want_exch = A.terms & 2, want_anis = A.terms & 4,
                want_zee = A.terms & 8, want_cav = A.terms & 16;
     const float G = (float)s_gamma;
     const float bs = (float)ip.brms_scale;
     const float dt = (float)st.dt;
+    const float bex = (float)ip.bext[0], bey = (float)ip.bext[1], bez = (float)ip.bext[2];
+    const long long pl = (long long)nx * P.ny;
     double xacc = 0.0;
     float emax = 0.f;
     bool bad = false;
-    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
-        const long long i = base + x;
-        float4 m = mrow[x];
+    for (int ii = threadIdx.x; ii < nr * nx; ii += blockDim.x) {
+        const int r = (int)fdiv((unsigned)ii, P.fd_nx), x = ii - r * nx;
+        const int row = row0 + r;
+        const int z = (int)fdiv((unsigned)row, P.fd_ny), y = row - z * P.ny;
+        const long long i = base + ii;
+        float4 m = mrow[ii];
         const float Ms = m.w;
         float Bx = 0.f, By = 0.f, Bz = 0.f;
         if (want_demag) {
-            float2 zx = xs[x >> 1], zy = xs[(L + 1) + (x >> 1)], zz = xs[2 * (L + 1) + (x >> 1)];
+            const float2* zr = xs + (x >> 1) * ld + 3 * r;
+            float2 zx = zr[0], zy = zr[1], zz = zr[2];
             if (x & 1) { Bx = zx.y; By = zy.y; Bz = zz.y; }
             else { Bx = zx.x; By = zy.x; Bz = zz.x; }
         }
@@ -433,13 +402,22 @@ __global__ void __launch_bounds__(MAX_THREADS) k_xinv(Plan P, Material mat, Buff
             if (want_exch) {
                 float hx = 0.f, hy = 0.f, hz = 0.f;
                 float4 q;
-                if (x > 0) { q = mrow[x - 1]; if (q.w > 0.f) { hx += mat.exch[0] * (q.x - m.x); hy += mat.exch[0] * (q.y - m.y); hz += mat.exch[0] * (q.z - m.z); } }
-                if (x + 1 < nx) { q = mrow[x + 1]; if (q.w > 0.f) { hx += mat.exch[0] * (q.x - m.x); hy += mat.exch[0] * (q.y - m.y); hz += mat.exch[0] * (q.z - m.z); } }
-                if (y > 0) { q = __ldg(msrc + i - nx); if (q.w > 0.f) { hx += mat.exch[1] * (q.x - m.x); hy += mat.exch[1] * (q.y - m.y); hz += mat.exch[1] * (q.z - m.z); } }
-                if (y + 1 < P.ny) { q = __ldg(msrc + i + nx); if (q.w > 0.f) { hx += mat.exch[1] * (q.x - m.x); hy += mat.exch[1] * (q.y - m.y); hz += mat.exch[1] * (q.z - m.z); } }
-                const long long pl = (long long)nx * P.ny;
-                if (z > 0) { q = __ldg(msrc + i - pl); if (q.w > 0.f) { hx += mat.exch[2] * (q.x - m.x); hy += mat.exch[2] * (q.y - m.y); hz += mat.exch[2] * (q.z - m.z); } }
-                if (z + 1 < P.nz) { q = __ldg(msrc + i + pl); if (q.w > 0.f) { hx += mat.exch[2] * (q.x - m.x); hy += mat.exch[2] * (q.y - m.y); hz += mat.exch[2] * (q.z - m.z); } }
+#define MMCQ_NB(Q, C)                                                                   \
+    q = (Q);                                                                            \
+    if (q.w > 0.f) { hx += (C) * (q.x - m.x); hy += (C) * (q.y - m.y); hz += (C) * (q.z - m.z); }
+                if (x > 0) { MMCQ_NB(mrow[ii - 1], mat.exch[0]) }
+                if (x + 1 < nx) { MMCQ_NB(mrow[ii + 1], mat.exch[0]) }
+                if (y > 0) {
+                    if (r > 0) { MMCQ_NB(mrow[ii - nx], mat.exch[1]) }
+                    else { MMCQ_NB(__ldg(msrc + i - nx), mat.exch[1]) }
+                }
+                if (y + 1 < P.ny) {
+                    if (r + 1 < nr) { MMCQ_NB(mrow[ii + nx], mat.exch[1]) }
+                    else { MMCQ_NB(__ldg(msrc + i + nx), mat.exch[1]) }
+                }
+                if (z > 0) { MMCQ_NB(__ldg(msrc + i - pl), mat.exch[2]) }
+                if (z + 1 < P.nz) { MMCQ_NB(__ldg(msrc + i + pl), mat.exch[2]) }
+#undef MMCQ_NB
                 float inv = 1.f / Ms;
                 Bx += hx * inv; By += hy * inv; Bz += hz * inv;
             }
@@ -448,9 +426,7 @@ __global__ void __launch_bounds__(MAX_THREADS) k_xinv(Plan P, Material mat, Buff
                 float f = mat.two_ku / Ms * mu;
                 Bx += f * mat.u[0]; By += f * mat.u[1]; Bz += f * mat.u[2];
             }
-            if (want_zee) {
-                Bx += (float)ip.bext[0]; By += (float)ip.bext[1]; Bz += (float)ip.bext[2];
-            }
+            if (want_zee) { Bx += bex; By += bey; Bz += bez; }
             if (ip.cav_on) {
                 if (Bf.prof) { float4 p = __ldg(Bf.prof + (i - cb)); px_ = bs * p.x; py_ = bs * p.y; pz_ = bs * p.z; }
                 else { py_ = bs; }
@@ -506,20 +482,20 @@ __global__ void __launch_bounds__(MAX_THREADS) k_xinv(Plan P, Material mat, Buff
     // block partials, then the last block of this instance finishes the stage
     double xb = block_sum_d(xacc, s_red);
     float eb = block_max_f(emax, s_redf);
-    const long long pb = (long long)b * P.nrows;
+    const long long pb = (long long)b * P.nblk;
     if (threadIdx.x == 0) {
-        Bf.xpart[pb + row] = xb;
-        Bf.epart[pb + row] = eb;
+        Bf.xpart[pb + blockIdx.x] = xb;
+        Bf.epart[pb + blockIdx.x] = eb;
         __threadfence();
         unsigned prev = atomicAdd(Bf.counter + b, 1u);
-        s_last = prev == (unsigned)(P.nrows - 1);
+        s_last = prev == (unsigned)(P.nblk - 1);
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
     double xsum = 0.0;
     float em = 0.f;
-    for (int r = threadIdx.x; r < P.nrows; r += blockDim.x) {
+    for (int r = threadIdx.x; r < P.nblk; r += blockDim.x) {
         xsum += __ldcg(Bf.xpart + pb + r);
         em = fmaxf(em, __ldcg(Bf.epart + pb + r));
     }
@@ -646,105 +622,55 @@ void upload_tableaux() {
     cudaMemcpyToSymbol(c_ef, ef, sizeof(ef));
 }
 
-static int threads_for(int nlines, int L, int minimum) {
-    int slots = (nlines * L + 3) / 4;
-    int t = (slots + 1) / 2;
-    t = ((t + 31) / 32) * 32;
-    if (t < minimum) t = minimum;
-    if (t > MAX_THREADS) t = MAX_THREADS;
-    return t;
+// Rows per x-pass block: R lines of 3 components times N1 = L / 32 threads
+// each, aiming at ~192 threads per block.
+int rows_per_block(int L, int nrows) {
+    int n1 = L <= 32 ? 1 : L / 32;
+    int R = 64 / n1;
+    if (R < 1) R = 1;
+    if (R > nrows) R = nrows;
+    return R;
 }
 
-bool fft_fits(int nlines, int L) { return (nlines * L + 3) / 4 <= MAX_SLOTS * MAX_THREADS; }
+static int xthreads(const Plan& P) { return 3 * P.R * (P.L <= 32 ? 1 : P.L / 32); }
+
+size_t xfwd_smem(const Plan& P) { return (size_t)P.L * 3 * P.R * sizeof(float2); }
 
 size_t xinv_smem(const Plan& P) {
-    size_t n2 = 3 * (size_t)(P.L + 1);
+    size_t n2 = (size_t)(P.L + 1) * 3 * P.R;
     n2 += n2 & 1;
-    return n2 * sizeof(float2) + (size_t)P.nx * sizeof(float4);
+    return n2 * sizeof(float2) + (size_t)P.nx * P.R * sizeof(float4);
 }
 
+bool x_fits(const Plan& P) { return P.L <= 1024 && xthreads(P) <= 512 && xinv_smem(P) <= 200 * 1024; }
+
+#define MMCQ_XCASES(F) F(1) F(2) F(4) F(8) F(16) F(32) F(64) F(128) F(256) F(512) F(1024)
+
 cudaError_t launch_xfwd(const Plan& P, const Buffers& Bf, const StageArgs& A, int nb, cudaStream_t s) {
-    int th = threads_for(3, P.L, 64);
-    size_t sm = 3 * (size_t)P.L * sizeof(float2);
-    dim3 grid(P.nrows, nb);
-    k_xfwd<<<grid, th, sm, s>>>(P, Bf, A);
+    dim3 grid(P.nblk, nb);
+    const int th = xthreads(P);
+    const size_t sm = xfwd_smem(P);
+    switch (P.L) {
+#define MMCQ_CASE(Lv) case Lv: k_xfwd<Lv><<<grid, th, sm, s>>>(P, Bf, A); break;
+        MMCQ_XCASES(MMCQ_CASE)
+#undef MMCQ_CASE
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_xinv(const Plan& P, const Material& mat, const Buffers& Bf, const StageArgs& A, int nb,
                         cudaStream_t s) {
-    int th = threads_for(3, P.L, 64);
-    dim3 grid(P.nrows, nb);
-    k_xinv<<<grid, th, xinv_smem(P), s>>>(P, mat, Bf, A);
-    return cudaGetLastError();
-}
-
-static cudaError_t launch_col(const Plan& P, const Buffers& Bf, const StageArgs& A, const ColArgs& C,
-                              int outer, int nb, cudaStream_t s) {
-    int rw = C.ncomp * P.TX;
-    int th = threads_for(rw, C.P, 32);
-    size_t sm = (size_t)C.P * rw * sizeof(float2);
-    dim3 grid(P.NT, outer, nb * (C.ncomp == 3 ? 1 : 3));
-    k_col<<<grid, th, sm, s>>>(P, Bf, A, C);
-    return cudaGetLastError();
-}
-
-// Layout strides of the tiled spectra.
-static void spec_strides(const Plan& P, int rows, long long& sb, long long& sz, long long& st, long long& sr) {
-    sr = 3LL * P.TX;                    // one row (ky or y) of a tile
-    st = (long long)rows * sr;          // one tile
-    sz = (long long)P.NT * st;          // one z plane
-    sb = (long long)P.nz * sz;          // one instance
-}
-
-// One launch of the demag convolution: part 0 = 2-D (fwd y, product, inv y);
-// 3-D: part 1 = forward y, 2 = z forward / product / z inverse, 3 = inverse y.
-cudaError_t launch_conv_part(const Plan& P, const Buffers& Bf, const StageArgs& A, int nb, cudaStream_t s, int part) {
-    long long sb, sz, st, sr, tb, tz, tt, tr;
-    spec_strides(P, P.ny, sb, sz, st, sr);
-    spec_strides(P, P.py, tb, tz, tt, tr);
-    ColArgs C{};
-    int outer = 1;
-    if (part == 0) {
-        C.in = Bf.spec; C.out = Bf.spec;
-        C.in_b = C.out_b = sb; C.in_o = C.out_o = 0; C.in_t = C.out_t = st; C.in_r = C.out_r = sr;
-        C.P = P.py; C.n_in = P.ny; C.n_out = P.ny;
-        C.fwd = 1; C.mult = 1; C.inv = 1; C.ncomp = 3; C.ky_is_row = 1;
-    } else if (part == 1) {
-        C.in = Bf.spec; C.out = Bf.spec2;
-        C.in_b = sb; C.in_o = sz; C.in_t = st; C.in_r = sr;
-        C.out_b = tb; C.out_o = tz; C.out_t = tt; C.out_r = tr;
-        C.P = P.py; C.n_in = P.ny; C.n_out = P.py; C.fwd = 1; C.ncomp = 1;
-        outer = P.nz;
-    } else if (part == 2) {
-        C.in = Bf.spec2; C.out = Bf.spec2;
-        C.in_b = C.out_b = tb; C.in_o = C.out_o = tr; C.in_t = C.out_t = tt; C.in_r = C.out_r = tz;
-        C.P = P.pz; C.n_in = P.nz; C.n_out = P.nz; C.fwd = 1; C.mult = 1; C.inv = 1; C.ncomp = 3; C.ky_is_row = 0;
-        outer = P.py;
-    } else {
-        C.in = Bf.spec2; C.out = Bf.spec;
-        C.in_b = tb; C.in_o = tz; C.in_t = tt; C.in_r = tr;
-        C.out_b = sb; C.out_o = sz; C.out_t = st; C.out_r = sr;
-        C.P = P.py; C.n_in = P.py; C.n_out = P.ny; C.inv = 1; C.ncomp = 1;
-        outer = P.nz;
+    dim3 grid(P.nblk, nb);
+    const int th = xthreads(P);
+    const size_t sm = xinv_smem(P);
+    switch (P.L) {
+#define MMCQ_CASE(Lv) case Lv: k_xinv<Lv><<<grid, th, sm, s>>>(P, mat, Bf, A); break;
+        MMCQ_XCASES(MMCQ_CASE)
+#undef MMCQ_CASE
+        default: return cudaErrorInvalidValue;
     }
-    return launch_col(P, Bf, A, C, outer, nb, s);
-}
-
-cudaError_t launch_convolution(const Plan& P, const Buffers& Bf, const StageArgs& A, int nb, cudaStream_t s) {
-    if (P.nz == 1) return launch_conv_part(P, Bf, A, nb, s, 0);
-    cudaError_t e;
-    for (int part = 1; part <= 3; part++)
-        if ((e = launch_conv_part(P, Bf, A, nb, s, part)) != cudaSuccess) return e;
-    return cudaSuccess;
-}
-
-int convolution_launches(const Plan& P) { return P.nz == 1 ? 1 : 3; }
-
-bool col_fits(const Plan& P) {
-    if (P.nz == 1) return fft_fits(3 * P.TX, P.py) && (size_t)P.py * 3 * P.TX * 8 <= 200 * 1024;
-    return fft_fits(P.TX, P.py) && (size_t)P.py * P.TX * 8 <= 200 * 1024 && fft_fits(3 * P.TX, P.pz) &&
-           (size_t)P.pz * 3 * P.TX * 8 <= 200 * 1024;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_set_m(float4* m, const float* src, const float* ms, long long N, int b0, int nb, cudaStream_t s) {
@@ -773,11 +699,20 @@ cudaError_t launch_set_dt(InstState* st, int B, double dt, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t col_init();
+
 cudaError_t set_smem_limits() {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_xfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_xinv, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_col, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if ((e = upload_tw32()) != cudaSuccess) return e;
+    const int lim = 200 * 1024;
+#define MMCQ_CASE(Lv)                                                                                         \
+    if ((e = cudaFuncSetAttribute(k_xfwd<Lv>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess) \
+        return e;                                                                                             \
+    if ((e = cudaFuncSetAttribute(k_xinv<Lv>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess) \
+        return e;
+    MMCQ_XCASES(MMCQ_CASE)
+#undef MMCQ_CASE
+    return col_init();
 }
 
 }  // namespace mq
