@@ -215,8 +215,8 @@ static cudaError_t launch_col(const Plan& P, const Buffers& Bf, const StageArgs&
     return cudaGetLastError();
 }
 
-// Threads of a register-path block: W columns x P / min(P, 32) threads each.
-static int reg_threads(int P, int W) { return W * (P <= 32 ? 1 : P / 32); }
+// Threads of a register-path block: W columns x N1 threads each.
+static int reg_threads(int P, int W) { return W * col_threads_per_column(P); }
 
 // Group count (power of two, <= limit) for a column pass: as large as keeps
 // the block within `max_threads` threads and `smem_cap` bytes.

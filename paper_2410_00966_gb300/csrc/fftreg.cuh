@@ -6,7 +6,7 @@
 // register renaming.
 //
 // col_fft<P>: a P-point transform of one column shared by N1 = P / NPT
-// threads (NPT = min(P, 32) points each), by the four-step factorisation
+// threads (NPT = 16 or 32 points each, see ColShape), by the four-step factorisation
 // P = N1 * NPT: thread j transforms x[j + N1 n2] over n2 (fft_reg<NPT>),
 // multiplies by W_P^{j k2}, the block transposes through shared memory, and
 // each thread finishes NPT / N1 transforms of length N1 (needs N1 <= NPT,
@@ -83,12 +83,16 @@ __device__ __forceinline__ void fft_reg(float2* v) {
     }
 }
 
+// Points per thread: 16 up to P = 256 (keeps the register footprint small),
+// 32 above (four-step needs N1 = P / NPT <= NPT).
 template <int P>
 struct ColShape {
-    static constexpr int NPT = P < 32 ? P : 32;   // points per thread
+    static constexpr int NPT = P <= 16 ? P : (P <= 256 ? 16 : 32);   // points per thread
     static constexpr int N1 = P / NPT;            // threads per column
     static constexpr int Q = NPT / N1;            // length-N1 transforms per thread in step 3
 };
+
+inline int col_threads_per_column(int P) { return P <= 16 ? 1 : (P <= 256 ? P / 16 : P / 32); }
 
 // Row of output element i of thread j (see file comment).
 template <int P>

@@ -21,6 +21,10 @@
 
 namespace mq {
 
+// Shared-memory pitch of the x passes: 3 R lines rounded up to an odd count,
+// so that consecutive cells (stride one pitch) fall in different banks.
+__host__ __device__ __forceinline__ int xpass_ld(int R) { return (3 * R) | 1; }
+
 // Butcher tableaux: [kind][stage][j].
 __constant__ float c_af[2][MAX_STAGES][MAX_STAGES];
 __constant__ double c_ad[2][MAX_STAGES][MAX_STAGES];
@@ -184,12 +188,12 @@ __global__ void __launch_bounds__(512) k_xfwd(Plan P, Buffers Bf, StageArgs A) {
     constexpr int NPT = ColShape<L>::NPT, N1 = ColShape<L>::N1;
     extern __shared__ float2 sm[];
     const int b = A.inst0 + blockIdx.y;
-    const InstState st = Bf.st[b];
+    const InstState& st = Bf.st[b];
     if (stage_skips(st, A)) return;
     const int nx = P.nx;
     const int row0 = blockIdx.x * P.R;
     const int nr = min(P.R, P.nrows - row0);
-    const int ld = 3 * P.R;
+    const int ld = xpass_ld(P.R);
     const long long base = (long long)b * P.N + (long long)row0 * nx;
     float2* zs = sm;
     for (int i = threadIdx.x; i < L * ld; i += blockDim.x) zs[i] = make_float2(0.f, 0.f);
@@ -247,7 +251,8 @@ __global__ void __launch_bounds__(512) k_xfwd(Plan P, Buffers Bf, StageArgs A) {
     }
     __syncthreads();
     {
-        const int line = threadIdx.x % ld, j = threadIdx.x / ld;
+        const int nl = 3 * P.R;
+        const int line = threadIdx.x % nl, j = threadIdx.x / nl;
         float2 v[NPT];
 #pragma unroll
         for (int n2 = 0; n2 < NPT; n2++) v[n2] = zs[(j + N1 * n2) * ld + line];
@@ -299,13 +304,13 @@ __global__ void __launch_bounds__(512) k_xinv(Plan P, Material mat, Buffers Bf, 
     __shared__ double s_gamma;
     __shared__ int s_last;
     const int b = A.inst0 + blockIdx.y;
-    const InstState st = Bf.st[b];
+    const InstState& st = Bf.st[b];
     if (stage_skips(st, A)) return;
-    const InstParams ip = Bf.ip[b];
+    const InstParams& ip = Bf.ip[b];
     const int TX = P.TX, nx = P.nx, lt = P.lt;
     const int row0 = blockIdx.x * P.R;
     const int nr = min(P.R, P.nrows - row0);
-    const int ld = 3 * P.R;
+    const int ld = xpass_ld(P.R);
     const long long cb = (long long)b * P.N;
     const long long base = cb + (long long)row0 * nx;
     const int s = A.stage;
@@ -363,7 +368,8 @@ __global__ void __launch_bounds__(512) k_xinv(Plan P, Material mat, Buffers Bf, 
     }
     __syncthreads();
     {
-        const int line = threadIdx.x % ld, j = threadIdx.x / ld;
+        const int nl = 3 * P.R;
+        const int line = threadIdx.x % nl, j = threadIdx.x / nl;
         float2 v[NPT];
 #pragma unroll
         for (int n2 = 0; n2 < NPT; n2++) v[n2] = xs[(j + N1 * n2) * ld + line];
@@ -378,6 +384,11 @@ __global__ void __launch_bounds__(512) k_xinv(Plan P, Material mat, Buffers Bf, 
     const float G = (float)s_gamma;
     const float bs = (float)ip.brms_scale;
     const float dt = (float)st.dt;
+    const bool cav_on = ip.cav_on != 0;
+    // outputs of this stage
+    const int k1slot = st.k1slot;
+    float4* const kout = K == KIND_RK4 ? (s < 3 ? Bf.k[s] : nullptr)
+                                       : (s < 6 ? Bf.k[s == 0 ? k1slot : s] : Bf.k[k1slot == 0 ? 6 : 0]);
     const float bex = (float)ip.bext[0], bey = (float)ip.bext[1], bez = (float)ip.bext[2];
     const long long pl = (long long)nx * P.ny;
     double xacc = 0.0;
@@ -427,7 +438,7 @@ __global__ void __launch_bounds__(512) k_xinv(Plan P, Material mat, Buffers Bf, 
                 Bx += f * mat.u[0]; By += f * mat.u[1]; Bz += f * mat.u[2];
             }
             if (want_zee) { Bx += bex; By += bey; Bz += bez; }
-            if (ip.cav_on) {
+            if (cav_on) {
                 if (Bf.prof) { float4 p = __ldg(Bf.prof + (i - cb)); px_ = bs * p.x; py_ = bs * p.y; pz_ = bs * p.z; }
                 else { py_ = bs; }
                 if (want_cav) { Bx += G * px_; By += G * py_; Bz += G * pz_; }
@@ -448,7 +459,7 @@ __global__ void __launch_bounds__(512) k_xinv(Plan P, Material mat, Buffers Bf, 
         float4 mx = m;
         if (K == KIND_RK4) {
             if (s < 3) {
-                Bf.k[s][i] = kk;
+                kout[i] = kk;
             } else {
                 float4 m0 = Bf.m[0][i];
                 float4 k0 = Bf.k[0][i], k1 = Bf.k[1][i], k2 = Bf.k[2][i];
@@ -466,16 +477,18 @@ __global__ void __launch_bounds__(512) k_xinv(Plan P, Material mat, Buffers Bf, 
             }
         } else {
             if (s < 6) {
-                Bf.k[k_slot(st, s)][i] = kk;
+                kout[i] = kk;
             } else {
-                Bf.k[st.k1slot == 0 ? 6 : 0][i] = kk;
+                kout[i] = kk;
                 float4 e = Bf.e6[i];
                 float c7 = c_ef[6] * dt;
                 float exx = e.x + c7 * kk.x, eyy = e.y + c7 * kk.y, ezz = e.z + c7 * kk.z;
                 emax = fmaxf(emax, sqrtf(exx * exx + eyy * eyy + ezz * ezz));
             }
         }
-        if (ip.cav_on) xacc += (double)Ms * ((double)mx.x * px_ + (double)mx.y * py_ + (double)mx.z * pz_);
+        // per-cell product in FP32, accumulated in FP64 (the sum over cells is
+        // the quantity that needs the range; FP64 arithmetic is ~1/64 rate here)
+        if (cav_on) xacc += (double)(Ms * (mx.x * px_ + mx.y * py_ + mx.z * pz_));
     }
     if (A.field_only) return;
     if (bad) atomicOr(Bf.flags, FLAG_NAN);
@@ -625,19 +638,19 @@ void upload_tableaux() {
 // Rows per x-pass block: R lines of 3 components times N1 = L / 32 threads
 // each, aiming at ~192 threads per block.
 int rows_per_block(int L, int nrows) {
-    int n1 = L <= 32 ? 1 : L / 32;
+    int n1 = col_threads_per_column(L);
     int R = 64 / n1;
     if (R < 1) R = 1;
     if (R > nrows) R = nrows;
     return R;
 }
 
-static int xthreads(const Plan& P) { return 3 * P.R * (P.L <= 32 ? 1 : P.L / 32); }
+static int xthreads(const Plan& P) { return 3 * P.R * col_threads_per_column(P.L); }
 
-size_t xfwd_smem(const Plan& P) { return (size_t)P.L * 3 * P.R * sizeof(float2); }
+size_t xfwd_smem(const Plan& P) { return (size_t)P.L * xpass_ld(P.R) * sizeof(float2); }
 
 size_t xinv_smem(const Plan& P) {
-    size_t n2 = (size_t)(P.L + 1) * 3 * P.R;
+    size_t n2 = (size_t)(P.L + 1) * xpass_ld(P.R);
     n2 += n2 & 1;
     return n2 * sizeof(float2) + (size_t)P.nx * P.R * sizeof(float4);
 }
