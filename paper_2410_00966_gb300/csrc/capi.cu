@@ -13,7 +13,6 @@
 #include "mmcq.h"
 
 namespace mq {
-void upload_tableaux();
 cudaError_t set_smem_limits();
 cudaError_t launch_xfwd(const Plan&, const Buffers&, const StageArgs&, int, cudaStream_t);
 cudaError_t launch_xinv(const Plan&, const Material&, const Buffers&, const StageArgs&, int, cudaStream_t);
@@ -338,7 +337,6 @@ int mmcq_create(mmcq_t** out, const mmcq_grid* g, double Ms, double Aex, double 
     h->dscratch = (double*)A(sizeof(double) * P.B);
     if (!ok) { h->err = "device allocation failed"; return bail(MMCQ_ERR_CUDA); }
 
-    upload_tableaux();
     if (set_smem_limits() != cudaSuccess) return bail(MMCQ_ERR_CUDA);
     {
         std::vector<float2> t(P.twn);

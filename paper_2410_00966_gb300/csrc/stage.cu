@@ -18,166 +18,13 @@
 #include "common.cuh"
 #include "fftreg.cuh"
 #include "kern_common.cuh"
+#include "stagecore.cuh"
 
 namespace mq {
 
 // Shared-memory pitch of the x passes: 3 R lines rounded up to an odd count,
 // so that consecutive cells (stride one pitch) fall in different banks.
 __host__ __device__ __forceinline__ int xpass_ld(int R) { return (3 * R) | 1; }
-
-// Butcher tableaux: [kind][stage][j].
-__constant__ float c_af[2][MAX_STAGES][MAX_STAGES];
-__constant__ double c_ad[2][MAX_STAGES][MAX_STAGES];
-__constant__ float c_bf[2][MAX_STAGES];    // weights of the propagated solution
-__constant__ double c_bd[2][MAX_STAGES];
-__constant__ double c_cd[2][MAX_STAGES];   // stage times
-__constant__ float c_ef[MAX_STAGES];       // DP45 error weights b5 - b4
-
-__device__ __forceinline__ double warp_sum_d(double v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-__device__ __forceinline__ float warp_max_f(float v) {
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
-    return v;
-}
-// Fixed-shape block reductions (deterministic for a given blockDim).
-__device__ double block_sum_d(double v, double* red) {
-    v = warp_sum_d(v);
-    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) red[w] = v;
-    __syncthreads();
-    int nw = (blockDim.x + 31) >> 5;
-    double r = 0.0;
-    if (w == 0) {
-        r = l < nw ? red[l] : 0.0;
-        r = warp_sum_d(r);
-    }
-    __syncthreads();
-    return r;  // valid in thread 0
-}
-__device__ float block_max_f(float v, float* red) {
-    v = warp_max_f(v);
-    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) red[w] = v;
-    __syncthreads();
-    int nw = (blockDim.x + 31) >> 5;
-    float r = 0.f;
-    if (w == 0) {
-        r = l < nw ? red[l] : 0.f;
-        r = warp_max_f(r);
-    }
-    __syncthreads();
-    return r;
-}
-
-// Gamma(t) from the P-mode accumulators, Eq. (gammadiscretefinal).
-__device__ double gamma_p(const InstParams& ip, const InstState& s, double tc, double hbar) {
-    double e = exp(-ip.kappa * tc);
-    double sn, cs;
-    sincos(ip.wc * tc, &sn, &cs);
-    return e * cs * (ip.x0 - 2.0 * s.S / hbar) - e * sn * (ip.p0 - 2.0 * s.C / hbar);
-}
-
-// FP64 scalar work after the last block of an instance has finished a stage:
-// cavity amplitude (E-mode: d alpha/dt = -(kappa + i omega_c) alpha + i X / hbar,
-// Eq. eqmotionaclasical with omega_c -> omega_c - i kappa), accumulators
-// (P-mode, Eq. Sdiscrete / Cdiscrete), time, accept / reject and step size.
-__device__ void finish_stage(const Plan& P, const Material& mat, const StageArgs& A, const InstParams& ip,
-                             InstState& s, double Xsum, float errmax, double* hist, int hcap, int* flags) {
-    const double X = Xsum * mat.vc;
-    const int k = A.stage;
-    const bool ecav = ip.cav_on && A.mode == CAV_E;
-    const bool pcav = ip.cav_on && A.mode == CAV_P;
-    const int K = A.kind;
-    const double dt = s.dt;
-    s.X = X;
-    if (ecav) {
-        // derivative of alpha at this stage
-        s.ka_re[k] = -ip.kappa * s.as_re + ip.wc * s.as_im;
-        s.ka_im[k] = -ip.kappa * s.as_im - ip.wc * s.as_re + X / mat.hbar;
-    }
-    const int nst = K == KIND_RK4 ? 4 : 7;
-    const bool last = k == nst - 1;
-    if (!last) {
-        if (ecav) {
-            // alpha of the next stage (DP45 stage 7 takes the 5th-order weights)
-            const bool to_b = (K == KIND_DP45 && k + 1 == 6);
-            double re = s.a_re, im = s.a_im;
-            for (int j = 0; j <= k; j++) {
-                double w = to_b ? c_bd[1][j] : c_ad[K][k + 1][j];
-                re += dt * w * s.ka_re[j];
-                im += dt * w * s.ka_im[j];
-            }
-            s.as_re = re;
-            s.as_im = im;
-        }
-        if (K == KIND_DP45 && k == 0) s.have_k1 = 1;
-        return;
-    }
-    int accept = 1;
-    if (K == KIND_DP45) {
-        float tol = A.tol;
-        accept = errmax <= tol;
-        if (!(errmax == errmax)) { accept = 0; atomicOr(flags, FLAG_NAN); }
-    }
-    if (accept) {
-        if (K == KIND_RK4) {
-            if (ecav) {
-                double re = s.a_re, im = s.a_im;
-                for (int j = 0; j < 4; j++) {
-                    re += dt * c_bd[0][j] * s.ka_re[j];
-                    im += dt * c_bd[0][j] * s.ka_im[j];
-                }
-                s.a_re = re; s.a_im = im;
-            }
-        } else {
-            s.mcur ^= 1;
-            s.k1slot = s.k1slot == 0 ? 6 : 0;
-            if (ecav) {
-                s.a_re = s.as_re; s.a_im = s.as_im;   // alpha5
-                s.ka_re[0] = s.ka_re[6]; s.ka_im[0] = s.ka_im[6];
-            }
-            if (A.mode == CAV_P) s.have_k1 = 0;   // Gamma at t_n changes with S_n, C_n
-        }
-        s.t += dt;
-        s.tcav += dt;
-        s.nacc++;
-        if (s.nhist < hcap) hist[s.nhist] = dt;
-        else atomicOr(flags, FLAG_HIST_FULL);
-        s.nhist++;
-        if (pcav) {
-            double e = exp(ip.kappa * s.tcav), sn, cs;
-            sincos(ip.wc * s.tcav, &sn, &cs);
-            s.S += e * sn * X * dt;
-            s.C += e * cs * X * dt;
-        }
-    } else {
-        s.nrej++;
-    }
-    if (K == KIND_DP45) {
-        double err = (double)errmax;
-        double f = err > 0.0 ? 0.9 * pow((double)A.tol / err, 0.2) : 5.0;
-        if (!(f == f)) f = 0.2;
-        f = fmin(5.0, fmax(0.2, f));
-        double nd = dt * f;
-        s.err = err;
-        if (s.t_end > 0.0) {
-            if (s.t >= s.t_end * (1.0 - 1e-14)) s.done = 1;
-            else if (s.t + nd > s.t_end) nd = s.t_end - s.t;
-        }
-        if (nd < 1e-20 && !s.done) { atomicOr(flags, FLAG_DT_UNDERFLOW); s.done = 1; }
-        s.dt = nd;
-    }
-    if (ecav) {
-        if (K == KIND_DP45) {
-            s.as_re = s.a_re + s.dt * c_ad[1][1][0] * s.ka_re[0];
-            s.as_im = s.a_im + s.dt * c_ad[1][1][0] * s.ka_im[0];
-        } else {
-            s.as_re = s.a_re; s.as_im = s.a_im;
-        }
-    }
-}
 
 // ---------------------------------------------------------------------------
 // x forward: stage input, M = Ms m_s, packed real FFT of length px = 2L.
@@ -200,49 +47,11 @@ __global__ void __launch_bounds__(512) k_xfwd(Plan P, Buffers Bf, StageArgs A) {
     __syncthreads();
 
     const float4* m0 = Bf.m[st.mcur] + base;
-    const int s = A.stage;
-    const float dt = (float)st.dt;
-    const bool form = !A.field_only && s > 0;
-    const bool dp_last = A.kind == KIND_DP45 && s == 6 && !A.field_only;
-    const float4* kp[MAX_STAGES - 1];
-    float kw[MAX_STAGES - 1], ke[MAX_STAGES - 1];
-    int nk = 0;
-#pragma unroll
-    for (int q = 0; q < MAX_STAGES - 1; q++) { kp[q] = Bf.k[0]; kw[q] = 0.f; ke[q] = 0.f; }
-    if (form) {
-        for (int j = 0; j < s; j++) {
-            float w = dp_last ? c_bf[1][j] : c_af[A.kind][s][j];
-            float e = dp_last ? c_ef[j] : 0.f;
-            if (w == 0.f && e == 0.f) continue;
-            kp[nk] = Bf.k[A.kind == KIND_DP45 ? k_slot(st, j) : j] + base;
-            kw[nk] = dt * w;
-            ke[nk] = dt * e;
-            nk++;
-        }
-    }
-    float4* ms_out = dp_last ? Bf.m[st.mcur ^ 1] + base : Bf.ms + base;
+    StageInput si;
+    si.init(Bf, A, st, base);
     for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) {
         float4 v = m0[i];
-        if (form) {
-            float ax = 0.f, ay = 0.f, az = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
-#pragma unroll
-            for (int q = 0; q < MAX_STAGES - 1; q++) {
-                if (q < nk) {
-                    float4 kj = kp[q][i];
-                    ax += kw[q] * kj.x; ay += kw[q] * kj.y; az += kw[q] * kj.z;
-                    ex += ke[q] * kj.x; ey += ke[q] * kj.y; ez += ke[q] * kj.z;
-                }
-            }
-            v.x += ax; v.y += ay; v.z += az;
-            if (dp_last) {
-                // 5th-order solution, renormalised: stage 7 is evaluated there
-                float r2 = v.x * v.x + v.y * v.y + v.z * v.z;
-                float inv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-                v.x *= inv; v.y *= inv; v.z *= inv;
-                Bf.e6[base + i] = make_float4(ex, ey, ez, 0.f);
-            }
-            ms_out[i] = v;
-        }
+        si.apply(v, i);
         const int r = (int)fdiv((unsigned)i, P.fd_nx), x = i - r * nx;
         float2* zr = zs + (x >> 1) * ld + 3 * r;
         float Mx = v.w * v.x, My = v.w * v.y, Mz = v.w * v.z;
@@ -338,14 +147,7 @@ __global__ void __launch_bounds__(512) k_xinv(Plan P, Material mat, Buffers Bf, 
         }
     }
     for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) mrow[i] = msrc[base + i];
-    if (threadIdx.x == 0) {
-        double G = 0.0;
-        if (ip.cav_on) {
-            if (A.mode == CAV_E) G = 2.0 * (A.field_only ? st.a_re : st.as_re);
-            else G = gamma_p(ip, st, st.tcav + (A.field_only ? 0.0 : c_cd[K][s] * st.dt), mat.hbar);
-        }
-        s_gamma = G;
-    }
+    if (threadIdx.x == 0) s_gamma = stage_gamma(A, ip, st, mat);
     __syncthreads();
     // Z[k] = (X[k] + conj X[L-k]) + i e^{+2 pi i k / px} (X[k] - conj X[L-k]), in place by pairs
     const int twstep = P.twn / P.px;
@@ -379,17 +181,9 @@ __global__ void __launch_bounds__(512) k_xinv(Plan P, Material mat, Buffers Bf, 
     }
     __syncthreads();
 
-    const bool want_demag = A.terms & 1, want_exch = A.terms & 2, want_anis = A.terms & 4,
-               want_zee = A.terms & 8, want_cav = A.terms & 16;
-    const float G = (float)s_gamma;
-    const float bs = (float)ip.brms_scale;
-    const float dt = (float)st.dt;
-    const bool cav_on = ip.cav_on != 0;
-    // outputs of this stage
-    const int k1slot = st.k1slot;
-    float4* const kout = K == KIND_RK4 ? (s < 3 ? Bf.k[s] : nullptr)
-                                       : (s < 6 ? Bf.k[s == 0 ? k1slot : s] : Bf.k[k1slot == 0 ? 6 : 0]);
-    const float bex = (float)ip.bext[0], bey = (float)ip.bext[1], bez = (float)ip.bext[2];
+    const bool want_demag = A.terms & 1, want_exch = A.terms & 2;
+    CellUpdate cu;
+    cu.init(mat, Bf, A, st, ip, (float)s_gamma, cb);
     const long long pl = (long long)nx * P.ny;
     double xacc = 0.0;
     float emax = 0.f;
@@ -408,118 +202,32 @@ __global__ void __launch_bounds__(512) k_xinv(Plan P, Material mat, Buffers Bf, 
             if (x & 1) { Bx = zx.y; By = zy.y; Bz = zz.y; }
             else { Bx = zx.x; By = zy.x; Bz = zz.x; }
         }
-        float px_ = 0.f, py_ = 0.f, pz_ = 0.f;   // coupling profile at this cell
-        if (Ms > 0.f) {
-            if (want_exch) {
-                float hx = 0.f, hy = 0.f, hz = 0.f;
-                float4 q;
+        if (Ms > 0.f && want_exch) {
+            float hx = 0.f, hy = 0.f, hz = 0.f;
+            float4 q;
 #define MMCQ_NB(Q, C)                                                                   \
     q = (Q);                                                                            \
     if (q.w > 0.f) { hx += (C) * (q.x - m.x); hy += (C) * (q.y - m.y); hz += (C) * (q.z - m.z); }
-                if (x > 0) { MMCQ_NB(mrow[ii - 1], mat.exch[0]) }
-                if (x + 1 < nx) { MMCQ_NB(mrow[ii + 1], mat.exch[0]) }
-                if (y > 0) {
-                    if (r > 0) { MMCQ_NB(mrow[ii - nx], mat.exch[1]) }
-                    else { MMCQ_NB(__ldg(msrc + i - nx), mat.exch[1]) }
-                }
-                if (y + 1 < P.ny) {
-                    if (r + 1 < nr) { MMCQ_NB(mrow[ii + nx], mat.exch[1]) }
-                    else { MMCQ_NB(__ldg(msrc + i + nx), mat.exch[1]) }
-                }
-                if (z > 0) { MMCQ_NB(__ldg(msrc + i - pl), mat.exch[2]) }
-                if (z + 1 < P.nz) { MMCQ_NB(__ldg(msrc + i + pl), mat.exch[2]) }
+            if (x > 0) { MMCQ_NB(mrow[ii - 1], mat.exch[0]) }
+            if (x + 1 < nx) { MMCQ_NB(mrow[ii + 1], mat.exch[0]) }
+            if (y > 0) {
+                if (r > 0) { MMCQ_NB(mrow[ii - nx], mat.exch[1]) }
+                else { MMCQ_NB(__ldg(msrc + i - nx), mat.exch[1]) }
+            }
+            if (y + 1 < P.ny) {
+                if (r + 1 < nr) { MMCQ_NB(mrow[ii + nx], mat.exch[1]) }
+                else { MMCQ_NB(__ldg(msrc + i + nx), mat.exch[1]) }
+            }
+            if (z > 0) { MMCQ_NB(__ldg(msrc + i - pl), mat.exch[2]) }
+            if (z + 1 < P.nz) { MMCQ_NB(__ldg(msrc + i + pl), mat.exch[2]) }
 #undef MMCQ_NB
-                float inv = 1.f / Ms;
-                Bx += hx * inv; By += hy * inv; Bz += hz * inv;
-            }
-            if (want_anis) {
-                float mu = m.x * mat.u[0] + m.y * mat.u[1] + m.z * mat.u[2];
-                float f = mat.two_ku / Ms * mu;
-                Bx += f * mat.u[0]; By += f * mat.u[1]; Bz += f * mat.u[2];
-            }
-            if (want_zee) { Bx += bex; By += bey; Bz += bez; }
-            if (cav_on) {
-                if (Bf.prof) { float4 p = __ldg(Bf.prof + (i - cb)); px_ = bs * p.x; py_ = bs * p.y; pz_ = bs * p.z; }
-                else { py_ = bs; }
-                if (want_cav) { Bx += G * px_; By += G * py_; Bz += G * pz_; }
-            }
+            float inv = 1.f / Ms;
+            Bx += hx * inv; By += hy * inv; Bz += hz * inv;
         }
-        if (A.field_only) {
-            Bf.fout[i - cb] = make_float4(Bx, By, Bz, 0.f);
-            continue;
-        }
-        // LLG torque, Eq. (llg)
-        float cx = m.y * Bz - m.z * By, cy = m.z * Bx - m.x * Bz, cz = m.x * By - m.y * Bx;
-        float dx = m.y * cz - m.z * cy, dy = m.z * cx - m.x * cz, dz = m.x * cy - m.y * cx;
-        float4 kk = make_float4(mat.pre * (cx + mat.alpha * dx), mat.pre * (cy + mat.alpha * dy),
-                                mat.pre * (cz + mat.alpha * dz), 0.f);
-        if (!(Ms > 0.f)) kk = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (!isfinite(kk.x) || !isfinite(kk.y) || !isfinite(kk.z)) bad = true;
-        // m used for the coupling sum of this launch
-        float4 mx = m;
-        if (K == KIND_RK4) {
-            if (s < 3) {
-                kout[i] = kk;
-            } else {
-                float4 m0 = Bf.m[0][i];
-                float4 k0 = Bf.k[0][i], k1 = Bf.k[1][i], k2 = Bf.k[2][i];
-                float h = dt * (1.f / 6.f);
-                float4 mn;
-                mn.x = m0.x + h * (k0.x + 2.f * k1.x + 2.f * k2.x + kk.x);
-                mn.y = m0.y + h * (k0.y + 2.f * k1.y + 2.f * k2.y + kk.y);
-                mn.z = m0.z + h * (k0.z + 2.f * k1.z + 2.f * k2.z + kk.z);
-                float r2 = mn.x * mn.x + mn.y * mn.y + mn.z * mn.z;
-                float inv = (Ms > 0.f && r2 > 0.f) ? rsqrtf(r2) : 0.f;
-                mn.x *= inv; mn.y *= inv; mn.z *= inv;
-                mn.w = m0.w;
-                Bf.m[0][i] = mn;
-                if (A.mode == CAV_P) mx = mn;
-            }
-        } else {
-            if (s < 6) {
-                kout[i] = kk;
-            } else {
-                kout[i] = kk;
-                float4 e = Bf.e6[i];
-                float c7 = c_ef[6] * dt;
-                float exx = e.x + c7 * kk.x, eyy = e.y + c7 * kk.y, ezz = e.z + c7 * kk.z;
-                emax = fmaxf(emax, sqrtf(exx * exx + eyy * eyy + ezz * ezz));
-            }
-        }
-        // per-cell product in FP32, accumulated in FP64 (the sum over cells is
-        // the quantity that needs the range; FP64 arithmetic is ~1/64 rate here)
-        if (cav_on) xacc += (double)(Ms * (mx.x * px_ + mx.y * py_ + mx.z * pz_));
+        cu.run(i, m, Bx, By, Bz, xacc, emax, bad);
     }
     if (A.field_only) return;
-    if (bad) atomicOr(Bf.flags, FLAG_NAN);
-    // block partials, then the last block of this instance finishes the stage
-    double xb = block_sum_d(xacc, s_red);
-    float eb = block_max_f(emax, s_redf);
-    const long long pb = (long long)b * P.nblk;
-    if (threadIdx.x == 0) {
-        Bf.xpart[pb + blockIdx.x] = xb;
-        Bf.epart[pb + blockIdx.x] = eb;
-        __threadfence();
-        unsigned prev = atomicAdd(Bf.counter + b, 1u);
-        s_last = prev == (unsigned)(P.nblk - 1);
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    double xsum = 0.0;
-    float em = 0.f;
-    for (int r = threadIdx.x; r < P.nblk; r += blockDim.x) {
-        xsum += __ldcg(Bf.xpart + pb + r);
-        em = fmaxf(em, __ldcg(Bf.epart + pb + r));
-    }
-    xsum = block_sum_d(xsum, s_red);
-    em = block_max_f(em, s_redf);
-    if (threadIdx.x == 0) {
-        InstState ns = Bf.st[b];
-        finish_stage(P, mat, A, ip, ns, xsum, em, Bf.hist + (long long)b * Bf.hcap, Bf.hcap, Bf.flags);
-        Bf.st[b] = ns;
-        Bf.counter[b] = 0u;
-    }
+    stage_epilogue(P, mat, Bf, A, b, blockIdx.x, P.nblk, xacc, emax, bad, s_red, s_redf, &s_last);
 }
 
 // ---------------------------------------------------------------------------
@@ -596,45 +304,6 @@ __global__ void k_set_dt(InstState* st, int B, double dt) {
 // ---------------------------------------------------------------------------
 // host-side launchers (called from the C ABI)
 // ---------------------------------------------------------------------------
-void upload_tableaux() {
-    float af[2][MAX_STAGES][MAX_STAGES] = {};
-    double ad[2][MAX_STAGES][MAX_STAGES] = {};
-    float bf[2][MAX_STAGES] = {};
-    double bd[2][MAX_STAGES] = {};
-    double cd[2][MAX_STAGES] = {};
-    float ef[MAX_STAGES] = {};
-    // classic RK4
-    ad[0][1][0] = 0.5; ad[0][2][1] = 0.5; ad[0][3][2] = 1.0;
-    double b4[4] = {1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6};
-    double c4[4] = {0.0, 0.5, 0.5, 1.0};
-    for (int j = 0; j < 4; j++) { bd[0][j] = b4[j]; cd[0][j] = c4[j]; }
-    // Dormand & Prince (1980) RK5(4)7FM
-    const double A5[7][6] = {
-        {0, 0, 0, 0, 0, 0},
-        {1.0 / 5, 0, 0, 0, 0, 0},
-        {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
-        {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0},
-        {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0},
-        {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0},
-        {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}};
-    const double B5[7] = {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84, 0};
-    const double B4[7] = {5179.0 / 57600, 0, 7571.0 / 16695, 393.0 / 640, -92097.0 / 339200, 187.0 / 2100, 1.0 / 40};
-    const double C5[7] = {0, 1.0 / 5, 3.0 / 10, 4.0 / 5, 8.0 / 9, 1, 1};
-    for (int s = 0; s < 7; s++)
-        for (int j = 0; j < 6; j++) ad[1][s][j] = A5[s][j];
-    for (int j = 0; j < 7; j++) { bd[1][j] = B5[j]; cd[1][j] = C5[j]; ef[j] = (float)(B5[j] - B4[j]); }
-    for (int k = 0; k < 2; k++) {
-        for (int s = 0; s < 7; s++) for (int j = 0; j < 7; j++) af[k][s][j] = (float)ad[k][s][j];
-        for (int j = 0; j < 7; j++) bf[k][j] = (float)bd[k][j];
-    }
-    cudaMemcpyToSymbol(c_af, af, sizeof(af));
-    cudaMemcpyToSymbol(c_ad, ad, sizeof(ad));
-    cudaMemcpyToSymbol(c_bf, bf, sizeof(bf));
-    cudaMemcpyToSymbol(c_bd, bd, sizeof(bd));
-    cudaMemcpyToSymbol(c_cd, cd, sizeof(cd));
-    cudaMemcpyToSymbol(c_ef, ef, sizeof(ef));
-}
-
 // Rows per x-pass block: R lines of 3 components times N1 = L / 32 threads
 // each, aiming at ~192 threads per block.
 int rows_per_block(int L, int nrows) {
@@ -716,6 +385,7 @@ cudaError_t col_init();
 
 cudaError_t set_smem_limits() {
     cudaError_t e;
+    upload_tableaux();
     if ((e = upload_tw32()) != cudaSuccess) return e;
     const int lim = 200 * 1024;
 #define MMCQ_CASE(Lv)                                                                                         \
