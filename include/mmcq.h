@@ -134,6 +134,8 @@ int mmcq_set_bias(mmcq_t* h, int inst, const double B[3]);
 
 /* Magnetisation of one instance or of all (inst = -1: the same N x 3 array
  * for every instance).  Normalised on entry (FP64), zero in empty cells.
+ * A non-finite direction is stored as zero and reported as MMCQ_ERR_NUMERIC
+ * by the next call that synchronises (mmcq_sync, mmcq_get_*).
  * Invalidates the first-same-as-last stage of the adaptive integrator. */
 int mmcq_set_m(mmcq_t* h, int inst, const float* m, int where);
 int mmcq_get_m(mmcq_t* h, int inst, float* out, int where);

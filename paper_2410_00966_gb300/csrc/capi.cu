@@ -24,7 +24,7 @@ bool fft_fits(int, int);
 size_t xinv_smem(const Plan&);
 int rows_per_block(int, int);
 bool x_fits(const Plan&);
-cudaError_t launch_set_m(float4*, const float*, const float*, long long, int, int, cudaStream_t);
+cudaError_t launch_set_m(float4*, const float*, const float*, long long, int, int, int*, cudaStream_t);
 cudaError_t launch_get_m(const float4*, float*, long long, cudaStream_t);
 cudaError_t launch_apply_ms(float4*, const float*, long long, int, cudaStream_t);
 cudaError_t launch_get_field(const float4*, float*, long long, cudaStream_t);
@@ -381,7 +381,7 @@ int mmcq_create(mmcq_t** out, const mmcq_grid* g, double Ms, double Aex, double 
         if (cudaMemcpy(h->stage3, m3.data(), sizeof(float) * 3 * P.N, cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(MMCQ_ERR_CUDA);
         for (int k = 0; k < 2; k++)
-            if (launch_set_m(Bf.m[k], h->stage3, h->ms_dev, P.N, 0, P.B, h->stream) != cudaSuccess)
+            if (launch_set_m(Bf.m[k], h->stage3, h->ms_dev, P.N, 0, P.B, Bf.flags, h->stream) != cudaSuccess)
                 return bail(MMCQ_ERR_CUDA);
         for (int k = 0; k < MAX_STAGES; k++)
             if (cudaMemsetAsync(Bf.k[k], 0, sizeof(float4) * BN, h->stream) != cudaSuccess) return bail(MMCQ_ERR_CUDA);
@@ -451,7 +451,7 @@ int mmcq_set_m(mmcq_t* h, int inst, const float* m, int where) {
         src = h->stage3;
     }
     int b0 = inst < 0 ? 0 : inst, nb = inst < 0 ? h->P.B : 1;
-    for (int k = 0; k < 2; k++) CK(h, launch_set_m(h->Bf.m[k], src, h->ms_dev, N, b0, nb, h->stream));
+    for (int k = 0; k < 2; k++) CK(h, launch_set_m(h->Bf.m[k], src, h->ms_dev, N, b0, nb, h->Bf.flags, h->stream));
     return edit_state(h, inst, [](InstState& s, int) { s.have_k1 = 0; });
 }
 

@@ -125,6 +125,85 @@ __global__ void __launch_bounds__(512) k_col_reg(Plan Pl, Buffers Bf, StageArgs 
     }
 }
 
+// z pass of the 3-D convolution for pz <= 32, one thread per (component, ky,
+// kx) column holding all pz rows in registers:
+//   1. forward FFT along z of the nz data rows (rows nz..pz/2-1 are read as
+//      zero, rows pz/2.. are compile-time zeros, so the first butterfly
+//      stage needs no additions);
+//   2. the three component spectra of a (ky, kx) column meet in shared
+//      memory, and the thread of component c forms row c of H m at every kz;
+//   3. inverse FFT along z of that row, keeping the nz output rows.
+// The mirror-reduced kernel is read once per stored kz row (kz and pz - kz
+// share it, with the sign of the xz and yz entries flipped).  nz <= pz / 2
+// always holds for the zero-padded convolution (pz >= 2 nz - 1, a power of 2).
+template <int P>
+__global__ void __launch_bounds__(256) k_zconv(Plan Pl, Buffers Bf, StageArgs A, ColArgs C) {
+    extern __shared__ float2 sm[];      // [P][W]
+    const int b = A.inst0 + blockIdx.z;
+    if (stage_skips(Bf.st[b], A)) return;
+    const int TX = Pl.TX, lt = Pl.lt;
+    const int W = C.G * 3 * TX;
+    const int col = threadIdx.x;        // blockDim.x == W
+    const int q = col >> lt;            // 3 g + c
+    const int g = q / 3, c = q - 3 * g, tx = col & (TX - 1);
+    const int t = blockIdx.y, o = blockIdx.x * C.G + g;   // tile, ky
+    const float2* in = C.in + b * C.in_b + o * C.in_o + t * C.in_t + c * TX + tx;
+    float2* out = C.out + b * C.out_b + o * C.out_o + t * C.out_t + c * TX + tx;
+
+    float2 v[P];
+#pragma unroll
+    for (int r = 0; r < P / 2; r++) v[r] = r < C.n_in ? in[r * C.in_r] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int r = P / 2; r < P; r++) v[r] = make_float2(0.f, 0.f);
+    fft_reg<P, false>(v);
+#pragma unroll
+    for (int k = 0; k < P; k++) sm[k * W + col] = v[k];
+    __syncthreads();
+
+    // row c of the symmetric kernel [[xx xy xz] [xy yy yz] [xz yz zz]], stored
+    // per (kz, ky, kx) as (xx, yy, zz, xy, xz, yz); an entry is odd in ky
+    // (kz) when exactly one of its two indices is y (z).
+    const int kx = t * TX + tx;
+    const bool live = kx < Pl.hx;
+    int kyr = o;
+    float sy = 1.f;
+    if (o > Pl.py / 2) { kyr = Pl.py - o; sy = -1.f; }
+    const int i0 = c == 0 ? 0 : (c == 1 ? 3 : 4);
+    const int i1 = c == 0 ? 3 : (c == 1 ? 1 : 5);
+    const int i2 = c == 0 ? 4 : (c == 1 ? 5 : 2);
+    float fp[3], fn[3];                 // signs for kz <= pz/2 and kz > pz/2
+#pragma unroll
+    for (int jj = 0; jj < 3; jj++) {
+        const float y = ((c == 1) != (jj == 1)) ? sy : 1.f;
+        fp[jj] = live ? y : 0.f;
+        fn[jj] = ((c == 2) != (jj == 2)) ? -fp[jj] : fp[jj];
+    }
+    const long long zs = (long long)Pl.hyk * Pl.NT * TX * 6;
+    const float* K = Bf.kern + ((long long)kyr * Pl.NT * TX + (live ? kx : 0)) * 6;
+    const float2* mcol = sm + g * 3 * TX + tx;
+#pragma unroll
+    for (int kz = 0; kz <= P / 2; kz++) {
+        const float* Kz = K + kz * zs;
+        const float a0 = __ldg(Kz + i0), a1 = __ldg(Kz + i1), a2 = __ldg(Kz + i2);
+        {
+            const float2* mm = mcol + kz * W;
+            const float2 mx = mm[0], my = mm[TX], mz = mm[2 * TX];
+            const float c0 = a0 * fp[0], c1 = a1 * fp[1], c2 = a2 * fp[2];
+            v[kz] = make_float2(c0 * mx.x + c1 * my.x + c2 * mz.x, c0 * mx.y + c1 * my.y + c2 * mz.y);
+        }
+        if (kz > 0 && kz < P / 2) {
+            const float2* mm = mcol + (P - kz) * W;
+            const float2 mx = mm[0], my = mm[TX], mz = mm[2 * TX];
+            const float c0 = a0 * fn[0], c1 = a1 * fn[1], c2 = a2 * fn[2];
+            v[P - kz] = make_float2(c0 * mx.x + c1 * my.x + c2 * mz.x, c0 * mx.y + c1 * my.y + c2 * mz.y);
+        }
+    }
+    fft_reg<P, true>(v);
+#pragma unroll
+    for (int r = 0; r < P / 2; r++)
+        if (r < C.n_out) out[r * C.out_r] = v[r];
+}
+
 // Generic shared-memory version (any power-of-two P up to 4096).
 template <int SLOTS>
 __global__ void __launch_bounds__(MAX_THREADS) k_col_gen(Plan P, Buffers Bf, StageArgs A, ColArgs C) {
@@ -185,6 +264,24 @@ static cudaError_t launch_reg(const Plan& Pl, const Buffers& Bf, const StageArgs
     constexpr int N1 = ColShape<P>::N1;
     k_col_reg<P><<<grid, W * N1, (size_t)P * W * sizeof(float2), s>>>(Pl, Bf, A, C);
     return cudaGetLastError();
+}
+
+template <int P>
+static cudaError_t launch_z(const Plan& Pl, const Buffers& Bf, const StageArgs& A, const ColArgs& C, int nb,
+                            cudaStream_t s) {
+    const int W = C.G * 3 * Pl.TX;
+    dim3 grid((Pl.py + C.G - 1) / C.G, Pl.NT, nb);
+    k_zconv<P><<<grid, W, (size_t)P * W * sizeof(float2), s>>>(Pl, Bf, A, C);
+    return cudaGetLastError();
+}
+
+// z pass with one thread per column (pz <= 32); false if it does not apply.
+static bool zconv_applies(const Plan& P) { return P.nz > 1 && P.pz <= 32 && 2 * P.nz <= P.pz; }
+
+static int zconv_groups(const Plan& P) {
+    int G = 1;
+    while (G * 2 <= P.py && G * 2 * 3 * P.TX <= 256) G *= 2;
+    return G;
 }
 
 static cudaError_t launch_col(const Plan& P, const Buffers& Bf, const StageArgs& A, const ColArgs& C, int nb,
@@ -276,6 +373,17 @@ cudaError_t launch_conv_part(const Plan& P, const Buffers& Bf, const StageArgs& 
         C.P = P.pz; C.n_in = P.nz; C.n_out = P.nz; C.fwd = 1; C.mult = 1; C.inv = 1; C.ncomp = 3; C.ky_is_row = 0;
         C.group_tiles = 0; C.nouter = P.py;
         C.G = pick_groups(3 * P.TX, P.pz, P.py, COL_MAX_THREADS, COL_SMEM_CAP);
+        if (zconv_applies(P)) {
+            C.G = zconv_groups(P);
+            switch (P.pz) {
+                case 2: return launch_z<2>(P, Bf, A, C, nb, s);
+                case 4: return launch_z<4>(P, Bf, A, C, nb, s);
+                case 8: return launch_z<8>(P, Bf, A, C, nb, s);
+                case 16: return launch_z<16>(P, Bf, A, C, nb, s);
+                case 32: return launch_z<32>(P, Bf, A, C, nb, s);
+                default: break;
+            }
+        }
     }
     return launch_col(P, Bf, A, C, nb, s);
 }
@@ -313,6 +421,11 @@ cudaError_t col_init() {
         return e;
     MMCQ_SET(1) MMCQ_SET(2) MMCQ_SET(4) MMCQ_SET(8) MMCQ_SET(16) MMCQ_SET(32) MMCQ_SET(64) MMCQ_SET(128)
     MMCQ_SET(256) MMCQ_SET(512) MMCQ_SET(1024)
+#undef MMCQ_SET
+#define MMCQ_SET(Pv)                                                                                            \
+    if ((e = cudaFuncSetAttribute(k_zconv<Pv>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess) \
+        return e;
+    MMCQ_SET(2) MMCQ_SET(4) MMCQ_SET(8) MMCQ_SET(16) MMCQ_SET(32)
 #undef MMCQ_SET
     return cudaSuccess;
 }

@@ -235,12 +235,14 @@ __global__ void __launch_bounds__(512) k_xinv(Plan P, Material mat, Buffers Bf, 
 // ---------------------------------------------------------------------------
 
 // m of one instance (or all) from an N x 3 float array: FP64 normalisation,
-// zero in empty cells, Ms into w.
-__global__ void k_set_m(float4* m, const float* src, const float* ms, long long N, int b0, int nb) {
+// zero in empty cells, Ms into w.  A non-finite direction is stored as zero
+// and raises FLAG_NAN (reported by the next synchronising call).
+__global__ void k_set_m(float4* m, const float* src, const float* ms, long long N, int b0, int nb, int* flags) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N) return;
     double x = src[3 * i], y = src[3 * i + 1], zz = src[3 * i + 2];
     double r = sqrt(x * x + y * y + zz * zz);
+    if (!isfinite(r)) { atomicOr(flags, FLAG_NAN); r = 0.0; }
     float w = ms[i];
     float4 v;
     if (w > 0.f && r > 0.0) v = make_float4((float)(x / r), (float)(y / r), (float)(zz / r), w);
@@ -355,8 +357,9 @@ cudaError_t launch_xinv(const Plan& P, const Material& mat, const Buffers& Bf, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_set_m(float4* m, const float* src, const float* ms, long long N, int b0, int nb, cudaStream_t s) {
-    k_set_m<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(m, src, ms, N, b0, nb);
+cudaError_t launch_set_m(float4* m, const float* src, const float* ms, long long N, int b0, int nb, int* flags,
+                         cudaStream_t s) {
+    k_set_m<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(m, src, ms, N, b0, nb, flags);
     return cudaGetLastError();
 }
 cudaError_t launch_get_m(const float4* m, float* dst, long long N, cudaStream_t s) {

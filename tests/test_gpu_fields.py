@@ -25,6 +25,9 @@ GRIDS = [
     (9, 1, 5, (5e-9, 5e-9, 5e-9)),
     (33, 17, 4, (4e-9, 4e-9, 4e-9)),
     (64, 40, 2, (4e-9, 4e-9, 4e-9)),
+    (20, 12, 16, (5e-9, 5e-9, 5e-9)),
+    (24, 20, 9, (4e-9, 4e-9, 3e-9)),
+    (6, 5, 17, (4e-9, 4e-9, 4e-9)),
 ]
 
 

@@ -1,0 +1,95 @@
+"""Parity at the full workload sizes, in the launch configuration bench.py times.
+
+* YIG-wire sweep (21 x 256x64x16, DP45 tol 1e-6): the batched handle takes a
+  few adaptive attempts; two instances are checked against the oracle, which
+  integrates each at full size replaying the GPU's accepted step sequence.
+* Large CPW-like film (1024x1024x8, 8.4 M cells, Lorentzian coupling profile):
+  the oracle cannot hold the full FFT convolution, so the demag field is
+  checked at sampled cells by the direct sum (each sample is a sum over all
+  8.4 M cells), and the local terms at the same cells in closed form.
+"""
+import numpy as np
+import pytest
+
+from gpu_common import require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def test_yig_wire_sweep_batched_dp45_full_size():
+    require_gpu()
+    import oracle
+    import paper_2410_00966_gb300 as pkg
+    import synthetic
+    w = synthetic.yig_wire_sweep()
+    I0 = w.instances[0]
+    sim = pkg.Sim(I0.nx, I0.ny, I0.nz, I0.d, I0.d, I0.d, I0.Ms, I0.Aex, I0.alpha, Ku=I0.Ku, axis=I0.axis,
+                  batch=len(w.instances))
+    for b, I in enumerate(w.instances):
+        sim.set_m(I.m0(), inst=b)
+        sim.set_bias(I.bias, inst=b)
+        sim.set_cavity(I.omega_c, I.kappa, I.g, inst=b)
+    sim.set_integrator(pkg.MMCQ_DP45, w.tol, pkg.MMCQ_CAVITY_E)
+    sim.set_horizon(w.horizon)
+    sim.step(4, w.dt)
+    for b in (0, len(w.instances) - 1):
+        I = w.instances[b]
+        hist = sim.dt_history(b)
+        assert len(hist) >= 2
+        o = oracle.Oracle(I.nx, I.ny, I.nz, I.d, I.d, I.d, I.Ms, I.Aex, I.alpha, Ku=I.Ku, axis=I.axis)
+        o.set_m(I.m0().astype(np.float64))
+        o.set_bias(I.bias)
+        o.set_cavity(I.omega_c, I.kappa, I.g)
+        o.set_integrator(oracle.DP45, w.tol, oracle.CAV_E)
+        o.replay(hist)
+        dm = np.abs(sim.get_m(b).astype(np.float64) - o.get_m()).max()
+        c, oc = sim.cavity(b), o.cavity()
+        print(f"instance {b}: {len(hist)} steps, max|dm| = {dm:.3e}")
+        assert dm <= 1e-5
+        a, ao = complex(c["re_alpha"], c["im_alpha"]), complex(oc["re_alpha"], oc["im_alpha"])
+        assert abs(a - ao) <= 1e-4 * abs(ao)
+    sim.close()
+
+
+def test_large_cpw_fields_at_sampled_cells():
+    require_gpu()
+    import oracle
+    import paper_2410_00966_gb300 as pkg
+    import synthetic
+    w = synthetic.large_cpw()
+    I = w.instances[0]
+    n = I.n
+    sim = pkg.Sim(I.nx, I.ny, I.nz, I.d, I.d, I.d, I.Ms, I.Aex, I.alpha)
+    m0 = synthetic.tilted_m(n, I.seed, 0.3)
+    sim.set_m(m0)
+    sim.set_bias(I.bias)
+    prof = I.coupling_profile()
+    sim.set_cavity(I.omega_c, I.kappa, I.g, profile=prof)
+    x0 = 2.0
+    sim.set_cavity_init(x0, 0.0)
+    m = sim.get_m().astype(np.float64)
+    Bd = sim.eval_field(pkg.MMCQ_TERM_DEMAG).astype(np.float64)
+    Bt = sim.eval_field(pkg.MMCQ_TERM_ALL).astype(np.float64)
+    # sampled cells: corners, edges, centre and seeded interior points
+    rng = np.random.default_rng(5)
+    nx, ny, nz = I.nx, I.ny, I.nz
+    pts = [(0, 0, 0), (nx - 1, ny - 1, nz - 1), (nx // 2, ny // 2, nz // 2), (0, ny - 1, 3), (nx - 1, 0, 4)]
+    pts += [tuple(int(v) for v in (rng.integers(nx), rng.integers(ny), rng.integers(nz))) for _ in range(7)]
+    cells = np.array([(z * ny + y) * nx + x for x, y, z in pts])
+    o = oracle.Oracle(nx, ny, nz, I.d, I.d, I.d, I.Ms, I.Aex, I.alpha, demag=oracle.DEMAG_NONE)
+    ref = o.demag_at(m, cells)
+    scale = np.abs(ref).max()
+    err = np.abs(Bd[cells] - ref).max()
+    print(f"demag at {len(cells)} cells: max err {err:.3e} T of {scale:.3e} T")
+    assert err <= 2e-6 * scale
+    # local terms (exchange, bias, cavity x0 * B_rms) from the oracle's own
+    # definitions on the full grid (O(N) each), added to the sampled demag
+    local = oracle.Oracle(nx, ny, nz, I.d, I.d, I.d, I.Ms, I.Aex, I.alpha, demag=oracle.DEMAG_NONE)
+    local.set_bias(I.bias)
+    local.set_cavity(I.omega_c, I.kappa, I.g, profile=prof.astype(np.float64))
+    Bl = local.field(m, Gamma=x0)[cells]
+    expect = ref + Bl
+    err_t = np.abs(Bt[cells] - expect).max()
+    print(f"total field at sampled cells: max err {err_t:.3e} T of {np.abs(expect).max():.3e} T")
+    assert err_t <= 2e-6 * scale + 2e-6 * np.abs(Bl).max()
+    sim.close()
