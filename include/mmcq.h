@@ -192,6 +192,25 @@ int mmcq_get_cavity(mmcq_t* h, int inst, mmcq_cavity* out);
  * *n receives the total count).  Used to replay adaptive runs. */
 int mmcq_get_dt_history(mmcq_t* h, int inst, double* out, int64_t max, int64_t* n);
 
+/* ---- checkpoint / resume -----------------------------------------------
+ * A snapshot holds everything that evolves in time or was set per instance:
+ * for every instance the accepted m, the first Dormand-Prince stage kept for
+ * first-same-as-last reuse, the integrator and cavity state (t, t_cav, dt,
+ * alpha, S, C, counters) and the instance parameters (bias, omega_c, kappa,
+ * g, x0, p0), plus the integrator choice.  Configuration that is shared by
+ * all instances (grid, material, Ms map, coupling profile) is not stored: the
+ * handle that restores must have been created and configured the same way.
+ * Resuming from a snapshot continues bit-for-bit as the original run.  The
+ * dt history restarts empty.
+ *
+ * mmcq_get_state: synchronises; writes the snapshot (host memory, caller
+ *   owned) when buf is non-NULL and cap >= its size; *size = its size.
+ *   buf == NULL only reports the size.  MMCQ_ERR_ARG if cap is too small.
+ * mmcq_set_state: MMCQ_ERR_ARG if the snapshot is truncated, is not one, or
+ *   was taken on a handle of another grid or batch size; nothing changes then. */
+int mmcq_get_state(mmcq_t* h, void* buf, int64_t cap, int64_t* size);
+int mmcq_set_state(mmcq_t* h, const void* buf, int64_t size);
+
 /* Effective field (T) of one instance at its current m, with the selected
  * MMCQ_TERM_* terms (cavity term uses the current Gamma); N x 3 floats. */
 int mmcq_eval_field(mmcq_t* h, int inst, int terms, float* out, int where);

@@ -92,6 +92,8 @@ PROTOTYPES = {
     "mmcq_get_cavity": (ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(mmcq_cavity)]),
     "mmcq_get_dt_history": (ctypes.c_int, [_H, ctypes.c_int, _DP, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "mmcq_eval_field": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, _FP, ctypes.c_int]),
+    "mmcq_get_state": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    "mmcq_set_state": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int64]),
     "mmcq_profile": (ctypes.c_int, [_H, ctypes.c_int]),
     "mmcq_profile_read": (ctypes.c_int, [_H, ctypes.POINTER(mmcq_kernel_stat), ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int)]),
@@ -304,6 +306,19 @@ class Sim:
 
     def launch_count(self) -> int:
         return int(self._lib.mmcq_launch_count(self._h))
+
+    def get_state(self) -> bytes:
+        """Snapshot of every instance (checkpoint), as bytes."""
+        n = ctypes.c_int64()
+        self._ck(self._lib.mmcq_get_state(self._h, None, 0, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        self._ck(self._lib.mmcq_get_state(self._h, buf, n.value, ctypes.byref(n)))
+        return buf.raw
+
+    def set_state(self, snap: bytes):
+        """Resume from a snapshot taken by get_state on an identically configured handle."""
+        buf = ctypes.create_string_buffer(bytes(snap), len(snap))
+        self._ck(self._lib.mmcq_set_state(self._h, buf, len(snap)))
 
     def eval_field(self, terms=MMCQ_TERM_ALL, inst=0, out=None) -> np.ndarray:
         if out is None:

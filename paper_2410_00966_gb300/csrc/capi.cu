@@ -541,7 +541,18 @@ int mmcq_set_integrator(mmcq_t* h, int kind, double tol, int cavity_mode) {
     h->kind = kind;
     h->tol = tol;
     h->mode = cavity_mode;
+    // the accepted state moves to buffer 0 (RK4 keeps it there)
+    const int B = h->P.B;
+    const long long N = h->P.N;
+    std::vector<InstState> st(B);
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpy(st.data(), h->Bf.st, sizeof(InstState) * B, cudaMemcpyDeviceToHost));
+    for (int b = 0; b < B; b++)
+        if (st[b].mcur == 1)
+            CK(h, cudaMemcpyAsync(h->Bf.m[0] + (long long)b * N, h->Bf.m[1] + (long long)b * N, sizeof(float4) * N,
+                                  cudaMemcpyDeviceToDevice, h->stream));
     return edit_state(h, -1, [](InstState& s, int) {
+        s.mcur = 0;
         s.have_k1 = 0;
         s.k1slot = 0;
         s.as_re = s.a_re;
@@ -709,5 +720,100 @@ int mmcq_profile_read(mmcq_t* h, mmcq_kernel_stat* out, int max, int* n) {
 }
 
 int64_t mmcq_launch_count(const mmcq_t* h) { return h ? h->launches : -1; }
+
+// ---- checkpoint / resume ---------------------------------------------------
+// Snapshot: SnapHeader, then per instance (B of each, in this order)
+// InstState, InstParams, g (double), g_mode (int32), then m of every instance
+// (B x N float4) and the kept first DP45 stage (B x N float4).
+namespace {
+struct SnapHeader {
+    char magic[8];
+    int32_t version, nx, ny, nz, B, kind, mode, pad;
+    double tol;
+    int64_t N, st_bytes, ip_bytes;
+};
+const char SNAP_MAGIC[8] = {'M', 'M', 'C', 'Q', 'S', 'N', 'A', 'P'};
+
+int64_t snap_size(const mmcq_t* h) {
+    const int64_t B = h->P.B;
+    return (int64_t)sizeof(SnapHeader) + B * (int64_t)(sizeof(InstState) + sizeof(InstParams) + 8 + 4) +
+           2 * B * h->P.N * (int64_t)sizeof(float4);
+}
+}  // namespace
+
+int mmcq_get_state(mmcq_t* h, void* buf, int64_t cap, int64_t* size) {
+    if (!h || cap < 0) return MMCQ_ERR_ARG;
+    const int64_t need = snap_size(h);
+    if (size) *size = need;
+    if (!buf) return MMCQ_OK;
+    if (cap < need) return fail(h, MMCQ_ERR_ARG, "snapshot buffer too small");
+    const int B = h->P.B;
+    const long long N = h->P.N;
+    std::vector<InstState> st(B);
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpy(st.data(), h->Bf.st, sizeof(InstState) * B, cudaMemcpyDeviceToHost));
+    char* p = static_cast<char*>(buf);
+    SnapHeader hd{};
+    std::memcpy(hd.magic, SNAP_MAGIC, 8);
+    hd.version = 1;
+    hd.nx = h->P.nx; hd.ny = h->P.ny; hd.nz = h->P.nz; hd.B = B;
+    hd.kind = h->kind; hd.mode = h->mode; hd.tol = h->tol;
+    hd.N = N; hd.st_bytes = sizeof(InstState); hd.ip_bytes = sizeof(InstParams);
+    std::memcpy(p, &hd, sizeof(hd)); p += sizeof(hd);
+    std::memcpy(p, st.data(), sizeof(InstState) * B); p += sizeof(InstState) * B;
+    std::memcpy(p, h->ip.data(), sizeof(InstParams) * B); p += sizeof(InstParams) * B;
+    std::memcpy(p, h->g.data(), sizeof(double) * B); p += sizeof(double) * B;
+    for (int b = 0; b < B; b++) { int32_t v = h->g_mode[b]; std::memcpy(p, &v, 4); p += 4; }
+    const size_t row = sizeof(float4) * N;
+    for (int b = 0; b < B; b++, p += row)
+        CK(h, cudaMemcpy(p, h->Bf.m[st[b].mcur] + (long long)b * N, row, cudaMemcpyDeviceToHost));
+    for (int b = 0; b < B; b++, p += row)
+        CK(h, cudaMemcpy(p, h->Bf.k[st[b].k1slot] + (long long)b * N, row, cudaMemcpyDeviceToHost));
+    return MMCQ_OK;
+}
+
+int mmcq_set_state(mmcq_t* h, const void* buf, int64_t size) {
+    if (!h || !buf || size < (int64_t)sizeof(SnapHeader)) return MMCQ_ERR_ARG;
+    const char* p = static_cast<const char*>(buf);
+    SnapHeader hd;
+    std::memcpy(&hd, p, sizeof(hd)); p += sizeof(hd);
+    const int B = h->P.B;
+    const long long N = h->P.N;
+    if (std::memcmp(hd.magic, SNAP_MAGIC, 8) != 0 || hd.version != 1)
+        return fail(h, MMCQ_ERR_ARG, "not an mmcq snapshot");
+    if (hd.nx != h->P.nx || hd.ny != h->P.ny || hd.nz != h->P.nz || hd.B != B || hd.N != N ||
+        hd.st_bytes != (int64_t)sizeof(InstState) || hd.ip_bytes != (int64_t)sizeof(InstParams))
+        return fail(h, MMCQ_ERR_ARG, "snapshot of another grid, batch or build");
+    if (size != snap_size(h)) return fail(h, MMCQ_ERR_ARG, "snapshot size mismatch");
+    if ((hd.kind != KIND_RK4 && hd.kind != KIND_DP45) || (hd.mode != CAV_E && hd.mode != CAV_P))
+        return fail(h, MMCQ_ERR_ARG, "snapshot integrator fields invalid");
+    std::vector<InstState> st(B);
+    std::memcpy(st.data(), p, sizeof(InstState) * B); p += sizeof(InstState) * B;
+    for (const InstState& s : st)
+        if ((s.k1slot != 0 && s.k1slot != MAX_STAGES - 1) || (s.mcur != 0 && s.mcur != 1))
+            return fail(h, MMCQ_ERR_ARG, "snapshot state fields invalid");
+    std::vector<InstParams> ip(B);
+    std::memcpy(ip.data(), p, sizeof(InstParams) * B); p += sizeof(InstParams) * B;
+    std::vector<double> g(B);
+    std::memcpy(g.data(), p, sizeof(double) * B); p += sizeof(double) * B;
+    std::vector<int> gm(B);
+    for (int b = 0; b < B; b++) { int32_t v; std::memcpy(&v, p, 4); p += 4; gm[b] = v; }
+    CK(h, cudaStreamSynchronize(h->stream));
+    const size_t row = sizeof(float4) * N;
+    for (int b = 0; b < B; b++, p += row)
+        for (int k = 0; k < 2; k++) CK(h, cudaMemcpy(h->Bf.m[k] + (long long)b * N, p, row, cudaMemcpyHostToDevice));
+    for (int b = 0; b < B; b++, p += row)
+        CK(h, cudaMemcpy(h->Bf.k[st[b].k1slot] + (long long)b * N, p, row, cudaMemcpyHostToDevice));
+    for (InstState& s : st) { s.mcur = 0; s.nhist = 0; }
+    CK(h, cudaMemcpy(h->Bf.st, st.data(), sizeof(InstState) * B, cudaMemcpyHostToDevice));
+    h->ip = ip;
+    h->g = g;
+    h->g_mode = gm;
+    h->kind = hd.kind;
+    h->mode = hd.mode;
+    h->tol = hd.tol;
+    h->k1_dirty = true;
+    return upload_params(h);
+}
 
 }  // extern "C"

@@ -10,6 +10,8 @@
 //   memory (consecutive threads = consecutive columns = contiguous memory).
 // k_col_gen: any power-of-two length, shared-memory Stockham (fft.cuh); used
 //   for transforms longer than 1024.
+#include <algorithm>
+
 #include "common.cuh"
 #include "fft.cuh"
 #include "fftreg.cuh"
@@ -204,6 +206,112 @@ __global__ void __launch_bounds__(256) k_zconv(Plan Pl, Buffers Bf, StageArgs A,
         if (r < C.n_out) out[r * C.out_r] = v[r];
 }
 
+// The same z pass with two threads per (component, ky, kx) column, each
+// holding H = pz / 2 rows in registers (about half the registers of k_zconv,
+// so about twice the resident warps).  With the data in rows < H, the DIF
+// split of the P-point transform gives X[2m] = DFT_H(x)[m] and X[2m+1] =
+// DFT_H(x W_P^r)[m]: thread half J = 0 takes the even, J = 1 the odd
+// frequencies.  The product H m runs over the shared-memory copy of the whole
+// spectrum, one (kz, ky, kx) point per thread and step.  The inverse is split
+// the same way, y[n] = IDFT_H(h_even)[n] + W_P^{-n} IDFT_H(h_odd)[n] for the
+// n < H rows kept; the halves add their parts through shared memory, each
+// storing H / 2 rows.  Threads [0, W) form half 0, [W, 2W) half 1.
+template <int P, int J>
+__device__ __forceinline__ void zsplit_forward(const ColArgs& C, float2* sm, int W, int col, const float2* in) {
+    constexpr int H = P / 2;
+    float2 v[H];
+#pragma unroll
+    for (int r = 0; r < H; r++) v[r] = r < C.n_in ? in[r * C.in_r] : make_float2(0.f, 0.f);
+    if (J == 1) {
+#pragma unroll
+        for (int r = 1; r < H; r++) {
+            const int e = r * (32 / P);           // W_P^r = W_32^e
+            if (e == 8) v[r] = make_float2(v[r].y, -v[r].x);
+            else v[r] = cmul(v[r], c_tw32[e]);
+        }
+    }
+    fft_reg<H, false>(v);
+#pragma unroll
+    for (int m = 0; m < H; m++) sm[(2 * m + J) * W + col] = v[m];
+}
+
+template <int P, int J>
+__device__ __forceinline__ void zsplit_inverse(const ColArgs& C, float2* sm, int W, int col, float2* out) {
+    constexpr int H = P / 2, Q = H / 2;
+    float2 v[H];
+#pragma unroll
+    for (int m = 0; m < H; m++) v[m] = sm[(2 * m + J) * W + col];
+    fft_reg<H, true>(v);
+    if (J == 1) {
+#pragma unroll
+        for (int n = 1; n < H; n++) {
+            const int e = n * (32 / P);           // W_P^{-n} = conj(W_32^e)
+            if (e == 8) v[n] = make_float2(-v[n].y, v[n].x);
+            else { float2 w = c_tw32[e]; w.y = -w.y; v[n] = cmul(v[n], w); }
+        }
+    }
+    __syncthreads();                              // both halves have read the product
+#pragma unroll
+    for (int n = 0; n < Q; n++) sm[((J == 0 ? Q : 0) + n) * W + col] = v[(J == 0 ? Q : 0) + n];
+    __syncthreads();
+#pragma unroll
+    for (int n = 0; n < Q; n++) {
+        const int r = (J == 0 ? 0 : Q) + n;
+        const float2 u = sm[r * W + col];
+        if (r < C.n_out) out[r * C.out_r] = make_float2(v[r].x + u.x, v[r].y + u.y);
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(192, 5) k_zconv2(Plan Pl, Buffers Bf, StageArgs A, ColArgs C) {
+    extern __shared__ float2 sm[];      // [P][W]
+    const int b = A.inst0 + blockIdx.z;
+    if (stage_skips(Bf.st[b], A)) return;
+    const int TX = Pl.TX, lt = Pl.lt;
+    const int W = C.G * 3 * TX;
+    const int half = threadIdx.x >= W;
+    const int col = threadIdx.x - half * W;
+    const int q = col >> lt;
+    const int g = q / 3, c = q - 3 * g, tx = col & (TX - 1);
+    const int t = blockIdx.y, o0 = blockIdx.x * C.G;
+    const long long off_in = b * C.in_b + (o0 + g) * C.in_o + t * C.in_t + c * TX + tx;
+    const long long off_out = b * C.out_b + (o0 + g) * C.out_o + t * C.out_t + c * TX + tx;
+    if (half == 0) zsplit_forward<P, 0>(C, sm, W, col, C.in + off_in);
+    else zsplit_forward<P, 1>(C, sm, W, col, C.in + off_in);
+    __syncthreads();
+
+    // product at every (kz, g, tx) point of the block: symmetric kernel
+    // (xx, yy, zz, xy, xz, yz) at (|kz|, |ky|, kx); xy is odd in ky, xz in kz,
+    // yz in both
+    const int GT = C.G * TX;                      // power of two
+    const int lgt = __ffs(GT) - 1;
+    const long long zs = (long long)Pl.hyk * Pl.NT * TX * 6;
+    for (int idx = threadIdx.x; idx < P * GT; idx += 2 * W) {
+        const int kz = idx >> lgt, p = idx & (GT - 1);
+        const int gg = p >> lt, xx = p & (TX - 1);
+        const int ky = o0 + gg, kx = t * TX + xx;
+        float2* pm = sm + kz * W + gg * 3 * TX + xx;
+        float2 mx = pm[0], my = pm[TX], mz = pm[2 * TX];
+        float2 hx = make_float2(0.f, 0.f), hy = hx, hz = hx;
+        if (kx < Pl.hx) {
+            const bool ny_ = ky > Pl.py / 2, nz_ = kz > P / 2;
+            const int kyr = ny_ ? Pl.py - ky : ky, kzr = nz_ ? P - kz : kz;
+            const float2* Kp =
+                reinterpret_cast<const float2*>(Bf.kern + kzr * zs + ((long long)kyr * Pl.NT * TX + kx) * 6);
+            const float2 k0 = __ldg(Kp), k1 = __ldg(Kp + 1), k2 = __ldg(Kp + 2);
+            const float sy = ny_ ? -1.f : 1.f, sz = nz_ ? -1.f : 1.f;
+            const float Kxx = k0.x, Kyy = k0.y, Kzz = k1.x, Kxy = sy * k1.y, Kxz = sz * k2.x, Kyz = sy * sz * k2.y;
+            hx = make_float2(Kxx * mx.x + Kxy * my.x + Kxz * mz.x, Kxx * mx.y + Kxy * my.y + Kxz * mz.y);
+            hy = make_float2(Kxy * mx.x + Kyy * my.x + Kyz * mz.x, Kxy * mx.y + Kyy * my.y + Kyz * mz.y);
+            hz = make_float2(Kxz * mx.x + Kyz * my.x + Kzz * mz.x, Kxz * mx.y + Kyz * my.y + Kzz * mz.y);
+        }
+        pm[0] = hx; pm[TX] = hy; pm[2 * TX] = hz;
+    }
+    __syncthreads();
+    if (half == 0) zsplit_inverse<P, 0>(C, sm, W, col, C.out + off_out);
+    else zsplit_inverse<P, 1>(C, sm, W, col, C.out + off_out);
+}
+
 // Generic shared-memory version (any power-of-two P up to 4096).
 template <int SLOTS>
 __global__ void __launch_bounds__(MAX_THREADS) k_col_gen(Plan P, Buffers Bf, StageArgs A, ColArgs C) {
@@ -275,8 +383,25 @@ static cudaError_t launch_z(const Plan& Pl, const Buffers& Bf, const StageArgs& 
     return cudaGetLastError();
 }
 
+template <int P>
+static cudaError_t launch_z2(const Plan& Pl, const Buffers& Bf, const StageArgs& A, const ColArgs& C, int nb,
+                             cudaStream_t s) {
+    const int W = C.G * 3 * Pl.TX;
+    dim3 grid((Pl.py + C.G - 1) / C.G, Pl.NT, nb);
+    k_zconv2<P><<<grid, 2 * W, (size_t)P * W * sizeof(float2), s>>>(Pl, Bf, A, C);
+    return cudaGetLastError();
+}
+
 // z pass with one thread per column (pz <= 32); false if it does not apply.
 static bool zconv_applies(const Plan& P) { return P.nz > 1 && P.pz <= 32 && 2 * P.nz <= P.pz; }
+
+// k_zconv2: 2 W = 6 G TX threads, at most ZSPLIT_THREADS (its launch bound)
+static const int ZSPLIT_THREADS = 192;
+static int zsplit_groups(const Plan& P) {
+    int G = 1;
+    while (G * 2 <= P.py && 2 * G * 2 * 3 * P.TX <= ZSPLIT_THREADS) G *= 2;
+    return G;
+}
 
 static int zconv_groups(const Plan& P) {
     int G = 1;
@@ -375,6 +500,10 @@ cudaError_t launch_conv_part(const Plan& P, const Buffers& Bf, const StageArgs& 
         C.G = pick_groups(3 * P.TX, P.pz, P.py, COL_MAX_THREADS, COL_SMEM_CAP);
         if (zconv_applies(P)) {
             C.G = zconv_groups(P);
+            if (P.pz == 32) {
+                C.G = zsplit_groups(P);
+                return launch_z2<32>(P, Bf, A, C, nb, s);
+            }
             switch (P.pz) {
                 case 2: return launch_z<2>(P, Bf, A, C, nb, s);
                 case 4: return launch_z<4>(P, Bf, A, C, nb, s);
@@ -427,6 +556,10 @@ cudaError_t col_init() {
         return e;
     MMCQ_SET(2) MMCQ_SET(4) MMCQ_SET(8) MMCQ_SET(16) MMCQ_SET(32)
 #undef MMCQ_SET
+    if ((e = cudaFuncSetAttribute(k_zconv2<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_zconv2<32>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
+        return e;
     return cudaSuccess;
 }
 

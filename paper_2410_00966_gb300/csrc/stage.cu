@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(512) k_xfwd(Plan P, Buffers Bf, StageArgs A) {
     StageInput si;
     si.init(Bf, A, st, base);
     for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) {
-        float4 v = m0[i];
+        float4 v = __ldg(m0 + i);
         si.apply(v, i);
         const int r = (int)fdiv((unsigned)i, P.fd_nx), x = i - r * nx;
         float2* zr = zs + (x >> 1) * ld + 3 * r;
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(512) k_xinv(Plan P, Material mat, Buffers Bf, 
             xs[k * ld + 3 * r + c] = in[t * tstride + c * TX + tx];
         }
     }
-    for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) mrow[i] = msrc[base + i];
+    for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) mrow[i] = __ldg(msrc + base + i);
     if (threadIdx.x == 0) s_gamma = stage_gamma(A, ip, st, mat);
     __syncthreads();
     // Z[k] = (X[k] + conj X[L-k]) + i e^{+2 pi i k / px} (X[k] - conj X[L-k]), in place by pairs

@@ -249,7 +249,7 @@ struct StageInput {
 #pragma unroll
         for (int q = 0; q < MAX_STAGES - 1; q++) {
             if (q < nk) {
-                float4 kj = kp[q][i];
+                float4 kj = __ldg(kp[q] + i);
                 ax += kw[q] * kj.x; ay += kw[q] * kj.y; az += kw[q] * kj.z;
                 ex += ke[q] * kj.x; ey += ke[q] * kj.y; ez += ke[q] * kj.z;
             }
@@ -329,7 +329,7 @@ struct CellUpdate {
                 kout[i] = kk;
             } else {
                 float4 m0 = Bf->m[0][i];
-                float4 k0 = Bf->k[0][i], k1 = Bf->k[1][i], k2 = Bf->k[2][i];
+                float4 k0 = __ldg(Bf->k[0] + i), k1 = __ldg(Bf->k[1] + i), k2 = __ldg(Bf->k[2] + i);
                 float h = dt * (1.f / 6.f);
                 float4 mn;
                 mn.x = m0.x + h * (k0.x + 2.f * k1.x + 2.f * k2.x + kk.x);
@@ -345,7 +345,7 @@ struct CellUpdate {
         } else {
             kout[i] = kk;
             if (s == 6) {
-                float4 e = Bf->e6[i];
+                float4 e = __ldg(Bf->e6 + i);
                 float c7 = c_ef[6] * dt;
                 float exx = e.x + c7 * kk.x, eyy = e.y + c7 * kk.y, ezz = e.z + c7 * kk.z;
                 emax = fmaxf(emax, sqrtf(exx * exx + eyy * eyy + ezz * ezz));
