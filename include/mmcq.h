@@ -242,6 +242,30 @@ int mmcq_eval_field(mmcq_t* h, int inst, int terms, float* out, int where);
 int mmcq_coupling_sum_noalloc(const float* m, const float* ms, const float* brms, int64_t n, double vc, double* out,
                               void* stream);
 
+/* ---- groups: several handles stepped as one CUDA graph -----------------
+ * A group advances handles of different grids (a sweep over mixed grid
+ * sizes) or settings together.  The kernels of every handle for `chunk`
+ * steps are captured once into a CUDA graph, each handle on its own branch so
+ * that independent handles run concurrently, and the graph is replayed
+ * n / chunk times (the remainder is enqueued directly).
+ *
+ * mmcq_group_step(g, n, dt) has the effect of mmcq_step(h, n, dt) on every
+ * handle h of the group: work already queued on a handle's stream comes
+ * first, and later calls on that stream see the result.  A handle whose
+ * integrator (kind, tolerance, cavity mode) changed since the capture is
+ * captured again; while any handle is profiling the group steps the handles
+ * one by one without a graph.  MMCQ_ERR_ARG for an empty list, a NULL or
+ * repeated handle, handles on different devices, chunk < 1, or RK4 with
+ * dt <= 0.  The handles must outlive the group; the group owns its streams,
+ * events and graph. */
+typedef struct mmcq_group mmcq_group_t;
+int mmcq_group_create(mmcq_group_t** g, mmcq_t* const* handles, int n, int chunk);
+int mmcq_group_step(mmcq_group_t* g, int64_t n, double dt);
+/* graph replays since creation (0 when every step ran without a graph) */
+int64_t mmcq_group_replays(const mmcq_group_t* g);
+void mmcq_group_destroy(mmcq_group_t* g);
+const char* mmcq_group_last_error(const mmcq_group_t* g);
+
 /* ---- measurement -------------------------------------------------------
  * Per-kernel-class timing of the launches mmcq_step enqueues.  While enabled,
  * each launch is bracketed by two CUDA events on the handle's stream; the

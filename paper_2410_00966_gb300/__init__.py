@@ -93,6 +93,12 @@ PROTOTYPES = {
     "mmcq_get_dt_history": (ctypes.c_int, [_H, ctypes.c_int, _DP, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "mmcq_eval_field": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, _FP, ctypes.c_int]),
     "mmcq_get_state": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    "mmcq_group_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(_H), ctypes.c_int,
+                                         ctypes.c_int]),
+    "mmcq_group_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double]),
+    "mmcq_group_replays": (ctypes.c_int64, [ctypes.c_void_p]),
+    "mmcq_group_destroy": (None, [ctypes.c_void_p]),
+    "mmcq_group_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "mmcq_set_state": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int64]),
     "mmcq_profile": (ctypes.c_int, [_H, ctypes.c_int]),
     "mmcq_profile_read": (ctypes.c_int, [_H, ctypes.POINTER(mmcq_kernel_stat), ctypes.c_int,
@@ -326,3 +332,34 @@ class Sim:
         p, w, keep = _ptr(out, 3 * self.n)
         self._ck(self._lib.mmcq_eval_field(self._h, inst, terms, p, w))
         return out
+
+
+class Group:
+    """Several Sim handles (any mix of grids) stepped together as one CUDA graph
+    (mmcq_group_*): ``step(n, dt)`` has the effect of ``sim.step(n, dt)`` on each."""
+
+    def __init__(self, sims, chunk: int = 16):
+        self._lib = lib()
+        self.sims = list(sims)
+        arr = (_H * len(self.sims))(*[s._h for s in self.sims])
+        g = ctypes.c_void_p()
+        rc = self._lib.mmcq_group_create(ctypes.byref(g), arr, len(self.sims), int(chunk))
+        if rc:
+            raise MMCQError(rc, "mmcq_group_create failed")
+        self._g = g
+
+    def step(self, n, dt=0.0):
+        rc = self._lib.mmcq_group_step(self._g, int(n), float(dt))
+        if rc:
+            raise MMCQError(rc, self._lib.mmcq_group_last_error(self._g).decode())
+
+    def replays(self) -> int:
+        return int(self._lib.mmcq_group_replays(self._g))
+
+    def close(self):
+        if getattr(self, "_g", None):
+            self._lib.mmcq_group_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        self.close()

@@ -236,6 +236,38 @@ int check_flags(mmcq_t* h) {
     return MMCQ_OK;
 }
 
+// n steps (RK4) or attempts (DP45) of every instance, enqueued on h->stream.
+int enqueue_steps(mmcq_t* h, int64_t n) {
+    StageArgs A{};
+    A.kind = h->kind;
+    A.mode = h->mode;
+    A.terms = MMCQ_TERM_ALL;
+    A.field_only = 0;
+    A.inst0 = 0;
+    A.tol = (float)h->tol;
+    const int B = h->P.B;
+    for (int64_t it = 0; it < n; it++) {
+        if (h->kind == KIND_RK4) {
+            for (int s = 0; s < 4; s++) {
+                A.stage = s;
+                int r = run_stage(h, A, B);
+                if (r) return r;
+            }
+        } else {
+            for (int s = 0; s < 7; s++) {
+                // stage 1 is first-same-as-last in E-mode: it only needs a launch
+                // after a host-side change (P-mode recomputes it every attempt)
+                if (s == 0 && h->mode == CAV_E && !h->k1_dirty) continue;
+                A.stage = s;
+                int r = run_stage(h, A, B);
+                if (r) return r;
+                if (s == 0 && h->mode == CAV_E) h->k1_dirty = false;
+            }
+        }
+    }
+    return MMCQ_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -573,35 +605,8 @@ int mmcq_step(mmcq_t* h, int64_t n, double dt) {
     if (!h || n < 0 || !std::isfinite(dt)) return MMCQ_ERR_ARG;
     if (h->kind == KIND_RK4 && !(dt > 0)) return fail(h, MMCQ_ERR_ARG, "RK4 needs dt > 0");
     if (n == 0) return MMCQ_OK;
-    StageArgs A{};
-    A.kind = h->kind;
-    A.mode = h->mode;
-    A.terms = MMCQ_TERM_ALL;
-    A.field_only = 0;
-    A.inst0 = 0;
-    A.tol = (float)h->tol;
     if (dt > 0) CK(h, launch_set_dt(h->Bf.st, h->P.B, dt, h->stream));
-    const int B = h->P.B;
-    for (int64_t it = 0; it < n; it++) {
-        if (h->kind == KIND_RK4) {
-            for (int s = 0; s < 4; s++) {
-                A.stage = s;
-                int r = run_stage(h, A, B);
-                if (r) return r;
-            }
-        } else {
-            for (int s = 0; s < 7; s++) {
-                // stage 1 is first-same-as-last in E-mode: it only needs a launch
-                // after a host-side change (P-mode recomputes it every attempt)
-                if (s == 0 && h->mode == CAV_E && !h->k1_dirty) continue;
-                A.stage = s;
-                int r = run_stage(h, A, B);
-                if (r) return r;
-                if (s == 0 && h->mode == CAV_E) h->k1_dirty = false;
-            }
-        }
-    }
-    return MMCQ_OK;
+    return enqueue_steps(h, n);
 }
 
 int mmcq_sync(mmcq_t* h) {
@@ -815,5 +820,206 @@ int mmcq_set_state(mmcq_t* h, const void* buf, int64_t size) {
     h->k1_dirty = true;
     return upload_params(h);
 }
+
+
+// ---- groups ------------------------------------------------------------------
+struct mmcq_group {
+    std::vector<mmcq_t*> hs;
+    int chunk = 1;
+    int device = 0;
+    cudaStream_t origin = nullptr;          // graph launch stream
+    std::vector<cudaStream_t> side;         // capture branch of each handle
+    cudaEvent_t fork = nullptr, done = nullptr;
+    std::vector<cudaEvent_t> join, in;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int> cap_kind, cap_mode;
+    std::vector<double> cap_tol;
+    std::vector<int64_t> cap_launches;      // kernel launches per replay, per handle
+    int64_t replays = 0;
+    std::string err;
+};
+
+namespace {
+
+int gfail(mmcq_group_t* g, int code, const std::string& msg) {
+    g->err = msg;
+    return code;
+}
+
+#define GCK(g, call)                                                                          \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) return gfail((g), MMCQ_ERR_CUDA, std::string(#call) + ": " +   \
+                                                                     cudaGetErrorString(e_)); \
+    } while (0)
+
+bool group_stale(const mmcq_group_t* g) {
+    if (!g->exec) return true;
+    for (size_t i = 0; i < g->hs.size(); i++) {
+        const mmcq_t* h = g->hs[i];
+        if (h->kind != g->cap_kind[i] || h->mode != g->cap_mode[i] || h->tol != g->cap_tol[i]) return true;
+    }
+    return false;
+}
+
+// Capture `chunk` steps of every handle, each on its own branch, into g->exec.
+// The handles' streams are swapped for the branch streams while capturing.
+int group_capture(mmcq_group_t* g) {
+    if (g->exec) { cudaGraphExecDestroy(g->exec); g->exec = nullptr; }
+    const size_t nh = g->hs.size();
+    std::vector<cudaStream_t> saved(nh);
+    std::vector<int64_t> before(nh);
+    for (size_t i = 0; i < nh; i++) {
+        saved[i] = g->hs[i]->stream;
+        before[i] = g->hs[i]->launches;
+    }
+    GCK(g, cudaStreamBeginCapture(g->origin, cudaStreamCaptureModeThreadLocal));
+    int r = MMCQ_OK;
+    cudaError_t e = cudaEventRecord(g->fork, g->origin);
+    for (size_t i = 0; i < nh && e == cudaSuccess && r == MMCQ_OK; i++) {
+        e = cudaStreamWaitEvent(g->side[i], g->fork, 0);
+        if (e != cudaSuccess) break;
+        g->hs[i]->stream = g->side[i];
+        r = enqueue_steps(g->hs[i], g->chunk);
+        g->hs[i]->stream = saved[i];
+        if (r == MMCQ_OK) e = cudaEventRecord(g->join[i], g->side[i]);
+        if (r == MMCQ_OK && e == cudaSuccess) e = cudaStreamWaitEvent(g->origin, g->join[i], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(g->origin, &graph);
+    for (size_t i = 0; i < nh; i++) {
+        g->hs[i]->stream = saved[i];
+        g->cap_launches[i] = g->hs[i]->launches - before[i];
+        g->hs[i]->launches = before[i];
+        g->cap_kind[i] = g->hs[i]->kind;
+        g->cap_mode[i] = g->hs[i]->mode;
+        g->cap_tol[i] = g->hs[i]->tol;
+    }
+    if (r != MMCQ_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return gfail(g, r, "capture: a handle failed to enqueue its steps");
+    }
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return gfail(g, MMCQ_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&g->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        g->exec = nullptr;
+        return gfail(g, MMCQ_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+    return MMCQ_OK;
+}
+
+}  // namespace
+
+int mmcq_group_create(mmcq_group_t** out, mmcq_t* const* handles, int n, int chunk) {
+    if (!out) return MMCQ_ERR_ARG;
+    *out = nullptr;
+    if (!handles || n < 1 || chunk < 1) return MMCQ_ERR_ARG;
+    for (int i = 0; i < n; i++) {
+        if (!handles[i] || handles[i]->device != handles[0]->device) return MMCQ_ERR_ARG;
+        for (int j = 0; j < i; j++)
+            if (handles[j] == handles[i]) return MMCQ_ERR_ARG;
+    }
+    mmcq_group_t* g = new mmcq_group();
+    g->hs.assign(handles, handles + n);
+    g->chunk = chunk;
+    g->device = handles[0]->device;
+    g->side.assign(n, nullptr);
+    g->join.assign(n, nullptr);
+    g->in.assign(n, nullptr);
+    g->cap_kind.assign(n, -1);
+    g->cap_mode.assign(n, -1);
+    g->cap_tol.assign(n, -1.0);
+    g->cap_launches.assign(n, 0);
+    bool ok = cudaSetDevice(g->device) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&g->origin, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; i < n && ok; i++)
+        ok = cudaStreamCreateWithFlags(&g->side[i], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&g->join[i], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&g->in[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        mmcq_group_destroy(g);
+        return MMCQ_ERR_CUDA;
+    }
+    *out = g;
+    return MMCQ_OK;
+}
+
+int mmcq_group_step(mmcq_group_t* g, int64_t n, double dt) {
+    if (!g || n < 0 || !std::isfinite(dt)) return MMCQ_ERR_ARG;
+    for (mmcq_t* h : g->hs)
+        if (h->kind == KIND_RK4 && !(dt > 0)) return gfail(g, MMCQ_ERR_ARG, "RK4 needs dt > 0");
+    if (n == 0) return MMCQ_OK;
+    GCK(g, cudaSetDevice(g->device));
+    bool eager = n < g->chunk;
+    for (mmcq_t* h : g->hs) {
+        if (dt > 0 && launch_set_dt(h->Bf.st, h->P.B, dt, h->stream) != cudaSuccess)
+            return gfail(g, MMCQ_ERR_CUDA, "set_dt launch failed");
+        // the first DP45 stage after a host-side change runs before the graph
+        // (the captured attempts reuse it, first-same-as-last)
+        if (h->kind == KIND_DP45 && h->mode == CAV_E && h->k1_dirty) {
+            StageArgs A{};
+            A.kind = h->kind; A.mode = h->mode; A.terms = MMCQ_TERM_ALL; A.tol = (float)h->tol; A.stage = 0;
+            int r = run_stage(h, A, h->P.B);
+            if (r) return gfail(g, r, "first stage launch failed");
+            h->k1_dirty = false;
+        }
+        if (h->profiling) eager = true;
+    }
+    if (eager) {
+        for (mmcq_t* h : g->hs) {
+            int r = enqueue_steps(h, n);
+            if (r) return gfail(g, r, "step launch failed");
+        }
+        return MMCQ_OK;
+    }
+    if (group_stale(g)) {
+        int r = group_capture(g);
+        if (r) return r;
+    }
+    const size_t nh = g->hs.size();
+    for (size_t i = 0; i < nh; i++) {
+        GCK(g, cudaEventRecord(g->in[i], g->hs[i]->stream));
+        GCK(g, cudaStreamWaitEvent(g->origin, g->in[i], 0));
+    }
+    const int64_t reps = n / g->chunk;
+    for (int64_t q = 0; q < reps; q++) GCK(g, cudaGraphLaunch(g->exec, g->origin));
+    g->replays += reps;
+    GCK(g, cudaEventRecord(g->done, g->origin));
+    for (size_t i = 0; i < nh; i++) {
+        mmcq_t* h = g->hs[i];
+        h->launches += reps * g->cap_launches[i];
+        GCK(g, cudaStreamWaitEvent(h->stream, g->done, 0));
+        const int64_t rem = n - reps * g->chunk;
+        if (rem > 0) {
+            int r = enqueue_steps(h, rem);
+            if (r) return gfail(g, r, "step launch failed");
+        }
+    }
+    return MMCQ_OK;
+}
+
+int64_t mmcq_group_replays(const mmcq_group_t* g) { return g ? g->replays : -1; }
+
+void mmcq_group_destroy(mmcq_group_t* g) {
+    if (!g) return;
+    cudaSetDevice(g->device);
+    if (g->origin) cudaStreamSynchronize(g->origin);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    for (cudaStream_t s : g->side) if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : g->join) if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : g->in) if (e) cudaEventDestroy(e);
+    if (g->fork) cudaEventDestroy(g->fork);
+    if (g->done) cudaEventDestroy(g->done);
+    if (g->origin) cudaStreamDestroy(g->origin);
+    delete g;
+}
+
+const char* mmcq_group_last_error(const mmcq_group_t* g) { return g ? g->err.c_str() : "null group"; }
 
 }  // extern "C"

@@ -105,7 +105,10 @@ __device__ __forceinline__ int col_out_row(int j, int i) {
 // v[n2] holds x[j + N1 n2] on entry and the outputs (rows col_out_row) on
 // exit.  `buf` (ld floats2 per row, at least P rows) is used for the transpose
 // when N1 > 1; every thread of the block must call this (it synchronises).
-template <int P, bool INV>
+// Twiddles come from `tw`, a table of exp(-2 pi i k / twn) for k < twn (a
+// multiple of P), in global memory (TW_SHARED = false, read through the
+// read-only cache) or in shared memory.
+template <int P, bool INV, bool TW_SHARED = false>
 __device__ __forceinline__ void col_fft(float2* v, float2* buf, int ld, int col, int j, const float2* __restrict__ tw,
                                         int twn) {
     constexpr int NPT = ColShape<P>::NPT, N1 = ColShape<P>::N1, Q = ColShape<P>::Q;
@@ -114,7 +117,16 @@ __device__ __forceinline__ void col_fft(float2* v, float2* buf, int ld, int col,
     // twiddle W_P^{j k2}
     const int step = twn / P;
 #pragma unroll
-    for (int k2 = 1; k2 < NPT; k2++) v[k2] = cmul(v[k2], twiddle(tw, j * k2 * step, INV));
+    for (int k2 = 1; k2 < NPT; k2++) {
+        float2 w;
+        if (TW_SHARED) {
+            w = tw[j * k2 * step];
+            if (INV) w.y = -w.y;
+        } else {
+            w = twiddle(tw, j * k2 * step, INV);
+        }
+        v[k2] = cmul(v[k2], w);
+    }
     __syncthreads();
 #pragma unroll
     for (int k2 = 0; k2 < NPT; k2++) buf[(k2 * N1 + j) * ld + col] = v[k2];

@@ -26,12 +26,19 @@ namespace mq {
 // so that consecutive cells (stride one pitch) fall in different banks.
 __host__ __device__ __forceinline__ int xpass_ld(int R) { return (3 * R) | 1; }
 
+// Threads of an x-pass block: 3 R lines x N1 threads per line with R = 64 / N1
+// rows (fewer when the grid has fewer rows), so never more than 192.
+constexpr int XPASS_THREADS = 192;
+// Resident blocks asked of the compiler: 5 (64 registers) while a thread
+// holds 16 points of the x transform, 3 when it holds 32 (L >= 512).
+constexpr int xpass_min_blocks(int L) { return L >= 512 ? 3 : 5; }
+
 // ---------------------------------------------------------------------------
 // x forward: stage input, M = Ms m_s, packed real FFT of length px = 2L.
 // R consecutive rows per block; shared memory zs[n][line], line = 3 r + comp.
 // ---------------------------------------------------------------------------
 template <int L>
-__global__ void __launch_bounds__(512) k_xfwd(Plan P, Buffers Bf, StageArgs A) {
+__global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xfwd(Plan P, Buffers Bf, StageArgs A) {
     constexpr int NPT = ColShape<L>::NPT, N1 = ColShape<L>::N1;
     extern __shared__ float2 sm[];
     const int b = A.inst0 + blockIdx.y;
@@ -43,15 +50,19 @@ __global__ void __launch_bounds__(512) k_xfwd(Plan P, Buffers Bf, StageArgs A) {
     const int ld = xpass_ld(P.R);
     const long long base = (long long)b * P.N + (long long)row0 * nx;
     float2* zs = sm;
-    for (int i = threadIdx.x; i < L * ld; i += blockDim.x) zs[i] = make_float2(0.f, 0.f);
+    float2* stw = sm + L * ld;                 // exp(-2 pi i e / px), e < px
+    const int tws = P.twn / P.px;
+    for (int e = threadIdx.x; e < P.px; e += blockDim.x) stw[e] = __ldg(Bf.tw + e * tws);
+    // rows nx/2.. of the packed line are zero padding (rows below are all written)
+    for (int i = (nx >> 1) * ld + threadIdx.x; i < L * ld; i += blockDim.x) zs[i] = make_float2(0.f, 0.f);
     __syncthreads();
 
     const float4* m0 = Bf.m[st.mcur] + base;
     StageInput si;
     si.init(Bf, A, st, base);
     for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) {
-        float4 v = __ldg(m0 + i);
-        si.apply(v, i);
+        float4 v = m0[i];
+        si.apply(Bf, v, i);
         const int r = (int)fdiv((unsigned)i, P.fd_nx), x = i - r * nx;
         float2* zr = zs + (x >> 1) * ld + 3 * r;
         float Mx = v.w * v.x, My = v.w * v.y, Mz = v.w * v.z;
@@ -65,7 +76,7 @@ __global__ void __launch_bounds__(512) k_xfwd(Plan P, Buffers Bf, StageArgs A) {
         float2 v[NPT];
 #pragma unroll
         for (int n2 = 0; n2 < NPT; n2++) v[n2] = zs[(j + N1 * n2) * ld + line];
-        col_fft<L, false>(v, zs, ld, line, j, Bf.tw, P.twn);
+        col_fft<L, false, true>(v, zs, ld, line, j, stw, P.px);
 #pragma unroll
         for (int i = 0; i < NPT; i++) zs[col_out_row<L>(j, i) * ld + line] = v[i];
     }
@@ -74,7 +85,6 @@ __global__ void __launch_bounds__(512) k_xfwd(Plan P, Buffers Bf, StageArgs A) {
     // X[k] = E[k] + W^k O[k], E = (Z[k] + conj Z[L-k]) / 2, O = -i (Z[k] - conj Z[L-k]) / 2
     const int TX = P.TX, lt = P.lt;
     const long long tstride = (long long)P.ny * 3 * TX;
-    const int twstep = P.twn / P.px;
     const int W3 = P.NT * 3 * TX;
     for (int r = 0; r < nr; r++) {
         const int row = row0 + r;
@@ -92,7 +102,7 @@ __global__ void __launch_bounds__(512) k_xfwd(Plan P, Buffers Bf, StageArgs A) {
                 float2 Zc = conjf2(zs[(k == 0 ? 0 : L - k) * ld + line]);
                 float2 E = make_float2(0.5f * (Zk.x + Zc.x), 0.5f * (Zk.y + Zc.y));
                 float2 D = make_float2(0.5f * (Zk.x - Zc.x), 0.5f * (Zk.y - Zc.y));
-                float2 wD = cmul(twiddle(Bf.tw, k * twstep, false), D);
+                float2 wD = cmul(stw[k], D);
                 X = make_float2(E.x + wD.y, E.y - wD.x);
             }
             out[t * tstride + ctx] = X;
@@ -105,7 +115,7 @@ __global__ void __launch_bounds__(512) k_xfwd(Plan P, Buffers Bf, StageArgs A) {
 // Shared memory: xs[k][line] (k <= L, line = 3 r + comp), then m rows.
 // ---------------------------------------------------------------------------
 template <int L>
-__global__ void __launch_bounds__(512) k_xinv(Plan P, Material mat, Buffers Bf, StageArgs A) {
+__global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Plan P, Material mat, Buffers Bf, StageArgs A) {
     constexpr int NPT = ColShape<L>::NPT, N1 = ColShape<L>::N1;
     extern __shared__ float2 sm[];
     __shared__ double s_red[32];
@@ -146,7 +156,7 @@ __global__ void __launch_bounds__(512) k_xinv(Plan P, Material mat, Buffers Bf, 
             xs[k * ld + 3 * r + c] = in[t * tstride + c * TX + tx];
         }
     }
-    for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) mrow[i] = __ldg(msrc + base + i);
+    for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) mrow[i] = msrc[base + i];
     if (threadIdx.x == 0) s_gamma = stage_gamma(A, ip, st, mat);
     __syncthreads();
     // Z[k] = (X[k] + conj X[L-k]) + i e^{+2 pi i k / px} (X[k] - conj X[L-k]), in place by pairs
@@ -183,7 +193,7 @@ __global__ void __launch_bounds__(512) k_xinv(Plan P, Material mat, Buffers Bf, 
 
     const bool want_demag = A.terms & 1, want_exch = A.terms & 2;
     CellUpdate cu;
-    cu.init(mat, Bf, A, st, ip, (float)s_gamma, cb);
+    cu.init(Bf, A, st, ip, (float)s_gamma, cb);
     const long long pl = (long long)nx * P.ny;
     double xacc = 0.0;
     float emax = 0.f;
@@ -224,7 +234,7 @@ __global__ void __launch_bounds__(512) k_xinv(Plan P, Material mat, Buffers Bf, 
             float inv = 1.f / Ms;
             Bx += hx * inv; By += hy * inv; Bz += hz * inv;
         }
-        cu.run(i, m, Bx, By, Bz, xacc, emax, bad);
+        cu.run(mat, Bf, i, m, Bx, By, Bz, xacc, emax, bad);
     }
     if (A.field_only) return;
     stage_epilogue(P, mat, Bf, A, b, blockIdx.x, P.nblk, xacc, emax, bad, s_red, s_redf, &s_last);
@@ -318,7 +328,9 @@ int rows_per_block(int L, int nrows) {
 
 static int xthreads(const Plan& P) { return 3 * P.R * col_threads_per_column(P.L); }
 
-size_t xfwd_smem(const Plan& P) { return (size_t)P.L * xpass_ld(P.R) * sizeof(float2); }
+// shared memory of the x passes: x forward: the packed lines and the
+// px-entry twiddle table; x inverse: the half-spectrum lines and the m rows
+size_t xfwd_smem(const Plan& P) { return ((size_t)P.L * xpass_ld(P.R) + P.px) * sizeof(float2); }
 
 size_t xinv_smem(const Plan& P) {
     size_t n2 = (size_t)(P.L + 1) * xpass_ld(P.R);

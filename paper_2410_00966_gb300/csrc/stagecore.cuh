@@ -209,47 +209,42 @@ static void upload_tableaux() {
 // evaluated (Eq. llg integrated by RK4 / Dormand-Prince).  At the last
 // Dormand-Prince stage the 5th-order solution is formed, renormalised and
 // stored as the candidate, with the partial error dt sum_j e_j k_j.
+// Weights are indexed by compile-time stage numbers only (registers, no
+// stack), and the k buffers are read through the kernel's parameter block.
 struct StageInput {
-    const float4* kp[MAX_STAGES - 1];
     float kw[MAX_STAGES - 1], ke[MAX_STAGES - 1];
-    int nk;
+    const float4* k0;    // buffer of stage 1 (DP45: first-same-as-last slot)
+    long long base;
     bool form, dp_last;
-    float4* out;     // where m_s is written (stage > 0)
+    float4* out;         // where m_s is written (stage > 0)
     float4* e6;
 
-    // Pointers are offset by `base` (the block's first cell); apply() takes
-    // the cell index relative to it.
-    __device__ __forceinline__ void init(const Buffers& Bf, const StageArgs& A, const InstState& st, long long base) {
+    // apply() takes the cell index relative to `base` (the block's first cell).
+    __device__ __forceinline__ void init(const Buffers& Bf, const StageArgs& A, const InstState& st, long long base_) {
         const int s = A.stage;
         const float dt = (float)st.dt;
+        base = base_;
         form = !A.field_only && s > 0;
         dp_last = A.kind == KIND_DP45 && s == 6 && !A.field_only;
-        nk = 0;
 #pragma unroll
-        for (int q = 0; q < MAX_STAGES - 1; q++) { kp[q] = Bf.k[0]; kw[q] = 0.f; ke[q] = 0.f; }
-        if (form) {
-            for (int j = 0; j < s; j++) {
-                float w = dp_last ? c_bf[1][j] : c_af[A.kind][s][j];
-                float e = dp_last ? c_ef[j] : 0.f;
-                if (w == 0.f && e == 0.f) continue;
-                kp[nk] = Bf.k[A.kind == KIND_DP45 ? k_slot(st, j) : j] + base;
-                kw[nk] = dt * w;
-                ke[nk] = dt * e;
-                nk++;
-            }
+        for (int j = 0; j < MAX_STAGES - 1; j++) {
+            const bool on = form && j < s;
+            kw[j] = on ? dt * (dp_last ? c_bf[1][j] : c_af[A.kind][s][j]) : 0.f;
+            ke[j] = on && dp_last ? dt * c_ef[j] : 0.f;
         }
+        k0 = (A.kind == KIND_DP45 ? Bf.k[st.k1slot] : Bf.k[0]) + base;
         out = (dp_last ? Bf.m[st.mcur ^ 1] : Bf.ms) + base;
         e6 = Bf.e6 + base;
     }
 
     // v = m0[i] on entry; m_s on return (written to out, and e6 at the last DP stage)
-    __device__ __forceinline__ void apply(float4& v, int i) const {
+    __device__ __forceinline__ void apply(const Buffers& Bf, float4& v, int i) const {
         if (!form) return;
         float ax = 0.f, ay = 0.f, az = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
 #pragma unroll
         for (int q = 0; q < MAX_STAGES - 1; q++) {
-            if (q < nk) {
-                float4 kj = __ldg(kp[q] + i);
+            if (kw[q] != 0.f || ke[q] != 0.f) {
+                const float4 kj = q == 0 ? k0[i] : Bf.k[q][base + i];
                 ax += kw[q] * kj.x; ay += kw[q] * kj.y; az += kw[q] * kj.z;
                 ex += ke[q] * kj.x; ey += ke[q] * kj.y; ez += ke[q] * kj.z;
             }
@@ -268,19 +263,17 @@ struct StageInput {
 // Everything a stage needs per cell once demag and exchange are known:
 // anisotropy, Zeeman and cavity fields, the LLG torque (Eq. llg), the RK
 // bookkeeping of this stage, and the cell's share of the coupling sum and of
-// the DP45 error.
+// the DP45 error.  Material constants and buffer pointers are read from the
+// kernel's parameter block at each use.
 struct CellUpdate {
-    const Material* mat;
-    const Buffers* Bf;
     float G, bs, dt, bex, bey, bez;
     bool cav_on, want_anis, want_zee, want_cav, field_only;
     int K, s, mode;
     long long cb;
     float4* kout;
 
-    __device__ __forceinline__ void init(const Material& m_, const Buffers& B_, const StageArgs& A,
-                                         const InstState& st, const InstParams& ip, float Gamma, long long cb_) {
-        mat = &m_; Bf = &B_;
+    __device__ __forceinline__ void init(const Buffers& Bf, const StageArgs& A, const InstState& st,
+                                         const InstParams& ip, float Gamma, long long cb_) {
         G = Gamma;
         bs = (float)ip.brms_scale;
         dt = (float)st.dt;
@@ -291,36 +284,36 @@ struct CellUpdate {
         K = A.kind; s = A.stage; mode = A.mode;
         cb = cb_;
         const int k1slot = st.k1slot;
-        kout = K == KIND_RK4 ? (s < 3 ? B_.k[s] : nullptr)
-                             : (s < 6 ? B_.k[s == 0 ? k1slot : s] : B_.k[k1slot == 0 ? 6 : 0]);
+        kout = K == KIND_RK4 ? (s < 3 ? Bf.k[s] : nullptr)
+                             : (s < 6 ? Bf.k[s == 0 ? k1slot : s] : Bf.k[k1slot == 0 ? 6 : 0]);
     }
 
     // (Bx, By, Bz) holds demag + exchange on entry
-    __device__ __forceinline__ void run(long long i, float4 m, float Bx, float By, float Bz, double& xacc, float& emax,
-                                        bool& bad) const {
+    __device__ __forceinline__ void run(const Material& mat, const Buffers& Bf, long long i, float4 m, float Bx,
+                                        float By, float Bz, double& xacc, float& emax, bool& bad) const {
         const float Ms = m.w;
         float px_ = 0.f, py_ = 0.f, pz_ = 0.f;
         if (Ms > 0.f) {
             if (want_anis) {
-                float mu = m.x * mat->u[0] + m.y * mat->u[1] + m.z * mat->u[2];
-                float f = mat->two_ku / Ms * mu;
-                Bx += f * mat->u[0]; By += f * mat->u[1]; Bz += f * mat->u[2];
+                float mu = m.x * mat.u[0] + m.y * mat.u[1] + m.z * mat.u[2];
+                float f = mat.two_ku / Ms * mu;
+                Bx += f * mat.u[0]; By += f * mat.u[1]; Bz += f * mat.u[2];
             }
             if (want_zee) { Bx += bex; By += bey; Bz += bez; }
             if (cav_on) {
-                if (Bf->prof) { float4 p = __ldg(Bf->prof + (i - cb)); px_ = bs * p.x; py_ = bs * p.y; pz_ = bs * p.z; }
+                if (Bf.prof) { float4 p = __ldg(Bf.prof + (i - cb)); px_ = bs * p.x; py_ = bs * p.y; pz_ = bs * p.z; }
                 else { py_ = bs; }
                 if (want_cav) { Bx += G * px_; By += G * py_; Bz += G * pz_; }
             }
         }
         if (field_only) {
-            Bf->fout[i - cb] = make_float4(Bx, By, Bz, 0.f);
+            Bf.fout[i - cb] = make_float4(Bx, By, Bz, 0.f);
             return;
         }
         float cx = m.y * Bz - m.z * By, cy = m.z * Bx - m.x * Bz, cz = m.x * By - m.y * Bx;
         float dx = m.y * cz - m.z * cy, dy = m.z * cx - m.x * cz, dz = m.x * cy - m.y * cx;
-        float4 kk = make_float4(mat->pre * (cx + mat->alpha * dx), mat->pre * (cy + mat->alpha * dy),
-                                mat->pre * (cz + mat->alpha * dz), 0.f);
+        float4 kk = make_float4(mat.pre * (cx + mat.alpha * dx), mat.pre * (cy + mat.alpha * dy),
+                                mat.pre * (cz + mat.alpha * dz), 0.f);
         if (!(Ms > 0.f)) kk = make_float4(0.f, 0.f, 0.f, 0.f);
         if (!isfinite(kk.x) || !isfinite(kk.y) || !isfinite(kk.z)) bad = true;
         float4 mx = m;   // m used for the coupling sum of this launch
@@ -328,8 +321,8 @@ struct CellUpdate {
             if (s < 3) {
                 kout[i] = kk;
             } else {
-                float4 m0 = Bf->m[0][i];
-                float4 k0 = __ldg(Bf->k[0] + i), k1 = __ldg(Bf->k[1] + i), k2 = __ldg(Bf->k[2] + i);
+                float4 m0 = Bf.m[0][i];
+                float4 k0 = Bf.k[0][i], k1 = Bf.k[1][i], k2 = Bf.k[2][i];
                 float h = dt * (1.f / 6.f);
                 float4 mn;
                 mn.x = m0.x + h * (k0.x + 2.f * k1.x + 2.f * k2.x + kk.x);
@@ -339,13 +332,13 @@ struct CellUpdate {
                 float inv = (Ms > 0.f && r2 > 0.f) ? rsqrtf(r2) : 0.f;
                 mn.x *= inv; mn.y *= inv; mn.z *= inv;
                 mn.w = m0.w;
-                Bf->m[0][i] = mn;
+                Bf.m[0][i] = mn;
                 if (mode == CAV_P) mx = mn;
             }
         } else {
             kout[i] = kk;
             if (s == 6) {
-                float4 e = __ldg(Bf->e6 + i);
+                float4 e = Bf.e6[i];
                 float c7 = c_ef[6] * dt;
                 float exx = e.x + c7 * kk.x, eyy = e.y + c7 * kk.y, ezz = e.z + c7 * kk.z;
                 emax = fmaxf(emax, sqrtf(exx * exx + eyy * eyy + ezz * ezz));
