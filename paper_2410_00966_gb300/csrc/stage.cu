@@ -144,6 +144,15 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
     else if (K == KIND_DP45 && s == 6) msrc = Bf.m[st.mcur ^ 1];
     else msrc = Bf.ms;
 
+    // the z neighbours of this block's rows are read in the cell loop: ask L2
+    // for them now (only when the whole range lies inside the instance)
+    if (threadIdx.x == 0 && P.nz > 1 && (A.terms & 2)) {
+        const long long pl_ = (long long)nx * P.ny;
+        const unsigned bytes = (unsigned)(nr * nx * sizeof(float4));
+        if (row0 >= P.ny) prefetch_l2(msrc + base - pl_, bytes);
+        if (row0 + nr - 1 + P.ny < P.nrows) prefetch_l2(msrc + base + pl_, bytes);
+    }
+
     // half-spectrum rows X[0..L] of the three components of every row
     const long long tstride = (long long)P.ny * 3 * TX;
     for (int r = 0; r < nr; r++) {
@@ -151,13 +160,14 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
         const int z = (int)fdiv((unsigned)row, P.fd_ny), y = row - z * P.ny;
         const float2* in = Bf.spec + (((long long)b * P.nz + z) * P.NT * P.ny + y) * 3 * TX;
         for (int idx = threadIdx.x; idx < 3 * (L + 1); idx += blockDim.x) {
-            const int c = (int)fdiv((unsigned)idx, P.fd_L1), k = idx - c * (L + 1);
+            const int c = idx / (L + 1), k = idx - c * (L + 1);
             const int t = k >> lt, tx = k & (TX - 1);
-            xs[k * ld + 3 * r + c] = in[t * tstride + c * TX + tx];
+            cp_async8(xs + k * ld + 3 * r + c, in + t * tstride + c * TX + tx);
         }
     }
-    for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) mrow[i] = msrc[base + i];
+    for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) cp_async16(mrow + i, msrc + base + i);
     if (threadIdx.x == 0) s_gamma = stage_gamma(A, ip, st, mat);
+    cp_async_wait_all();
     __syncthreads();
     // Z[k] = (X[k] + conj X[L-k]) + i e^{+2 pi i k / px} (X[k] - conj X[L-k]), in place by pairs
     const int twstep = P.twn / P.px;
