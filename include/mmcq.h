@@ -192,6 +192,33 @@ int mmcq_get_cavity(mmcq_t* h, int inst, mmcq_cavity* out);
  * *n receives the total count).  Used to replay adaptive runs. */
 int mmcq_get_dt_history(mmcq_t* h, int inst, double* out, int64_t max, int64_t* n);
 
+/* ---- excitation and spectra (Appendix C) --------------------------------
+ * mmcq_set_drive: the excitation of the paper's example script, added to the
+ *   external field of one instance or all (inst = -1):
+ *     B_ext,i(t) += amp * B_rms,i * sinc(omega_cut * (t - t0)),  sinc(0) = 1,
+ *   with B_rms,i the instance's coupling map (mmcq_set_cavity; it stays in
+ *   use after mmcq_disable_cavity), t the simulation time at each Runge-Kutta
+ *   stage, omega_cut in rad/s.  amp = 0 turns it off.  Part of the Zeeman term
+ *   of mmcq_eval_field.
+ * mmcq_set_recording: every > 0 records (t, <mx>, <my>, <mz>) of every
+ *   instance after every `every`-th accepted step, <m> the mean of m over the
+ *   magnetised cells (FP64 sums); 0 stops.  Capacity 65536 samples per
+ *   instance (then MMCQ_ERR_STATE from the read-out).  First use allocates
+ *   32 bytes x 65536 per instance.
+ * mmcq_get_mavg_history: copies up to max samples of one instance into out
+ *   (host, caller owned, max x 4 doubles: t, <mx>, <my>, <mz>); *n = samples.
+ * mmcq_spectrum: on the device, the Fourier transform of one component
+ *   (comp 0..2) of an instance's recorded <m>:
+ *     S(w) = sum_n c_n (y_n - ybar) exp(-i w t_n),
+ *   c_n the trapezoid weights of the sample times (any spacing), ybar their
+ *   time average, at the nw angular frequencies omega (host, rad/s); out
+ *   (host, 2 nw doubles) receives Re, Im.  MMCQ_ERR_STATE if recording was
+ *   never on. */
+int mmcq_set_drive(mmcq_t* h, int inst, double amp, double omega_cut, double t0);
+int mmcq_set_recording(mmcq_t* h, int every);
+int mmcq_get_mavg_history(mmcq_t* h, int inst, double* out, int64_t max, int64_t* n);
+int mmcq_spectrum(mmcq_t* h, int inst, int comp, const double* omega, int nw, double* out);
+
 /* ---- checkpoint / resume -----------------------------------------------
  * A snapshot holds everything that evolves in time or was set per instance:
  * for every instance the accepted m, the first Dormand-Prince stage kept for

@@ -15,6 +15,9 @@ the paper passages they follow:
 * ``Oracle.step``: RK4 / Dormand-Prince on (m, alpha) (E-mode, Sec. 2.2 and
   Appendix A) or on m with the S_n, C_n accumulators (P-mode, Sec. 3.1,
   Eq. Sdiscrete, Cdiscrete, gammadiscretefinal).
+* ``Oracle.set_drive`` / ``Oracle.mavg_history`` / ``spectrum``: Appendix C
+  excitation (amp * B_rms * sinc(omega_cut t) added to B_ext), the spatially
+  averaged m, and its numerical Fourier transform.
 """
 from __future__ import annotations
 
@@ -95,6 +98,11 @@ def _load():
         "or_cavity_X": (d, [p, dp]),
         "or_demag_at": (None, [p, dp, ctypes.POINTER(ctypes.c_long), l, dp]),
         "or_energy": (None, [p, dp]),
+        "or_set_drive": (None, [p, d, d, d]),
+        "or_drive_factor": (d, [p, d]),
+        "or_set_recording": (None, [p, i]),
+        "or_mavg_history": (l, [p, dp, l]),
+        "or_spectrum": (None, [dp, dp, l, dp, l, dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -285,8 +293,38 @@ class Oracle:
                               c.size, _dp(out))
         return out
 
+    def set_drive(self, amp, omega_cut, t0=0.0):
+        """Appendix C excitation: B_ext += amp * B_rms,i * sinc(omega_cut (t - t0)); amp = 0 turns it off."""
+        self._lib.or_set_drive(self._h, amp, omega_cut, t0)
+
+    def drive_factor(self, t) -> float:
+        return self._lib.or_drive_factor(self._h, t)
+
+    def set_recording(self, on=True):
+        self._lib.or_set_recording(self._h, int(bool(on)))
+
+    def mavg_history(self) -> np.ndarray:
+        """(n, 4): t, <mx>, <my>, <mz> after each accepted step while recording."""
+        n = self._lib.or_mavg_history(self._h, None, 0)
+        out = np.zeros((n, 4))
+        if n:
+            self._lib.or_mavg_history(self._h, _dp(out), n)
+        return out
+
     def energy(self) -> dict:
         out = np.zeros(7)
         self._lib.or_energy(self._h, _dp(out))
         return dict(zip(["zeeman", "demag", "exchange", "anis", "coupling", "photon", "total"],
                         out.tolist()))
+
+
+def spectrum(t, y, omega) -> np.ndarray:
+    """Trapezoid-weighted Fourier transform of samples y(t_n) at angular
+    frequencies omega, after removing the time average (complex array)."""
+    lib = _load()
+    t = _f64(t)
+    y = _f64(y)
+    w = _f64(omega)
+    out = np.zeros(2 * w.size)
+    lib.or_spectrum(_dp(t), _dp(y), t.size, _dp(w), w.size, _dp(out))
+    return out[0::2] + 1j * out[1::2]

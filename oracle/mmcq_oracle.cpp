@@ -27,6 +27,9 @@
 //     Mumax3's demag kernel; this is the reading used by both sides).
 //   * Integrators: classic RK4 and Dormand-Prince 5(4) (the paper uses
 //     Mumax3's unmodified ODE solver, Sec. 3.1).
+//   * Appendix C: the excitation amp * B_rms * sinc(omega_cut t) added to
+//     B_ext, the spatially averaged m after each accepted step, and the
+//     numerical Fourier transform of that average (response spectra).
 //
 // Parity of this oracle against the real Mumax3-cQED program is unpinned
 // (no program output is available); each function is pinned instead by the
@@ -252,6 +255,12 @@ struct oracle {
     cplx a;        // E-mode photon amplitude alpha
     double S, C;   // P-mode accumulators (include the cell volume V_c)
     double t, tcav;
+    // excitation of Appendix C: B_ext += amp B_rms,i sinc(omega_cut (t - t0))
+    int drv_on;
+    double drv_amp, drv_wcut, drv_t0;
+    // spatially averaged m after each accepted step: (t, <mx>, <my>, <mz>)
+    int record;
+    std::vector<double> mavg;
     // integrator
     int kind; double tol, dt_next;
     long n_acc, n_rej;
@@ -394,7 +403,7 @@ static double gamma_P(const oracle* o, double tc) {
 
 // Total effective field B_eff' = B_ext + B_demag + B_exch + B_anis + B_rms*Gamma
 // (Sec. 2.1 term list and Eq. bcav).
-static void total_field(const oracle* o, const double* m, double Gamma, double* B) {
+static void total_field(const oracle* o, const double* m, double Gamma, double* B, double drive = 0.0) {
     std::vector<double> t1(3 * o->n), t2(3 * o->n);
     demag_field(o, m, B);
     exchange_field(o, m, t1.data());
@@ -403,8 +412,18 @@ static void total_field(const oracle* o, const double* m, double Gamma, double* 
         for (int c = 0; c < 3; c++) {
             double b = B[3 * i + c] + t1[3 * i + c] + t2[3 * i + c] + o->bext[c];
             if (o->cav_on) b += o->brms[3 * i + c] * Gamma;
+            if (o->ms[i] > 0) b += drive * o->brms[3 * i + c];
             B[3 * i + c] = b;
         }
+}
+
+// The excitation of Appendix C (the example script adds amp B_rms sin(w t)/(w t)
+// to B_ext): the factor amp sinc(omega_cut (t - t0)) at simulation time t, with
+// sinc(0) = 1.
+static double drive_factor(const oracle* o, double t) {
+    if (!o->drv_on) return 0.0;
+    double x = o->drv_wcut * (t - o->drv_t0);
+    return o->drv_amp * (x == 0.0 ? 1.0 : std::sin(x) / x);
 }
 
 // LLG torque, Eq. (llg): dm/dt = -gamma/(1+alpha^2) [m x B + alpha m x (m x B)].
@@ -426,11 +445,11 @@ static void llg_rhs(const oracle* o, const double* m, const double* B, double* d
 // with omega_c -> omega_c - i kappa; the spin operator is S = -Ms m V_c/gamma,
 // Sec. 2.1).  P-mode: Gamma from the accumulators, alpha not integrated.
 static void rhs(const oracle* o, const double* m, cplx a, double tc, double* dm, cplx* da,
-                double* Xout) {
+                double* Xout, double ts = 0.0) {
     double Gamma = 0;
     if (o->cav_on) Gamma = (o->cav_mode == OR_CAV_E) ? 2.0 * a.real() : gamma_P(o, tc);
     std::vector<double> B(3 * o->n);
-    total_field(o, m, Gamma, B.data());
+    total_field(o, m, Gamma, B.data(), drive_factor(o, ts));
     llg_rhs(o, m, B.data(), dm);
     double X = o->cav_on ? cavity_X(o, m) : 0.0;
     if (Xout) *Xout = X;
@@ -460,6 +479,18 @@ static void after_accept(oracle* o, double dt) {
     o->tcav += dt;
     o->n_acc++;
     o->dt_hist.push_back(dt);
+    if (o->record) {
+        // <m> over the magnetised cells of the accepted, renormalised state
+        double sm[3] = {0, 0, 0};
+        long nm = 0;
+        for (long i = 0; i < o->n; i++) {
+            if (o->ms[i] <= 0) continue;
+            nm++;
+            for (int c = 0; c < 3; c++) sm[c] += o->m[3 * i + c];
+        }
+        o->mavg.push_back(o->t);
+        for (int c = 0; c < 3; c++) o->mavg.push_back(nm ? sm[c] / nm : 0.0);
+    }
     if (o->cav_on && o->cav_mode == OR_CAV_P) {
         double X = cavity_X(o, o->m.data());
         double tc = o->tcav;
@@ -484,7 +515,7 @@ static void step_rk4(oracle* o, double dt) {
             for (long q = 0; q < n3; q++) tmp[q] = o->m[q] + c[s] * dt * k[s - 1][q];
             as = o->a + c[s] * dt * ka[s - 1];
         }
-        rhs(o, tmp.data(), as, o->tcav + c[s] * dt, k[s].data(), &ka[s], nullptr);
+        rhs(o, tmp.data(), as, o->tcav + c[s] * dt, k[s].data(), &ka[s], nullptr, o->t + c[s] * dt);
     }
     for (long q = 0; q < n3; q++)
         o->m[q] += dt / 6.0 * (k[0][q] + 2.0 * k[1][q] + 2.0 * k[2][q] + k[3][q]);
@@ -537,7 +568,7 @@ static int step_dp45(oracle* o, double dt, int force, double* err_out) {
             for (int j = 0; j < 6; j++) as += dt * DP_B5[j] * ka[j];
             a5 = as;
         }
-        rhs(o, tmp.data(), as, o->tcav + DP_C[s] * dt, k[s].data(), &ka[s], nullptr);
+        rhs(o, tmp.data(), as, o->tcav + DP_C[s] * dt, k[s].data(), &ka[s], nullptr, o->t + DP_C[s] * dt);
     }
     double err = 0;
     for (long i = 0; i < o->n; i++) {
@@ -614,6 +645,8 @@ oracle* or_create(int nx, int ny, int nz, double dx, double dy, double dz, doubl
     o->brms.assign(3 * o->n, 0.0);
     o->cav_mode = OR_CAV_E;
     o->a = 0; o->S = o->C = 0; o->t = o->tcav = 0;
+    o->drv_on = 0; o->drv_amp = o->drv_wcut = o->drv_t0 = 0;
+    o->record = 0;
     o->kind = OR_RK4; o->tol = 1e-6; o->dt_next = 0;
     o->n_acc = o->n_rej = 0;
     o->demag = demag;
@@ -768,7 +801,55 @@ void or_set_alpha(oracle* o, double re, double im) { o->a = cplx(re, im); }
 void or_demag(const oracle* o, const double* m, double* B) { demag_field(o, m, B); }
 void or_exchange(const oracle* o, const double* m, double* B) { exchange_field(o, m, B); }
 void or_anis(const oracle* o, const double* m, double* B) { anis_field(o, m, B); }
-void or_field(const oracle* o, const double* m, double Gamma, double* B) { total_field(o, m, Gamma, B); }
+// Total field at the current simulation time (the drive, if on, at o->t).
+void or_field(const oracle* o, const double* m, double Gamma, double* B) {
+    total_field(o, m, Gamma, B, drive_factor(o, o->t));
+}
+
+// Appendix C excitation: B_ext += amp B_rms,i sinc(omega_cut (t - t0)); amp = 0 turns it off.
+void or_set_drive(oracle* o, double amp, double wcut, double t0) {
+    o->drv_on = amp != 0.0;
+    o->drv_amp = amp; o->drv_wcut = wcut; o->drv_t0 = t0;
+}
+double or_drive_factor(const oracle* o, double t) { return drive_factor(o, t); }
+
+// Record <m> over the magnetised cells after every accepted step.
+void or_set_recording(oracle* o, int on) { o->record = on != 0; }
+long or_mavg_history(const oracle* o, double* out, long max) {
+    long n = (long)(o->mavg.size() / 4);
+    long c = n < max ? n : max;
+    if (out && c > 0) std::memcpy(out, o->mavg.data(), sizeof(double) * 4 * c);
+    return n;
+}
+
+// Numerical Fourier transform of a sampled signal y(t_n) (Appendix C: the
+// broadband response is the Fourier transform of the spatially averaged m):
+//   S(w) = sum_n c_n (y_n - ybar) exp(-i w t_n),
+// trapezoid weights c_1 = (t_2 - t_1)/2, c_n = (t_{n+1} - t_{n-1})/2,
+// c_N = (t_N - t_{N-1})/2 (any sample spacing), and ybar = sum c_n y_n / sum c_n,
+// the time average.  out[2k], out[2k+1] = Re, Im S(w_k).
+void or_spectrum(const double* t, const double* y, long n, const double* w, long nw, double* out) {
+    std::vector<double> c(n > 0 ? n : 1, 0.0);
+    if (n >= 2) {
+        c[0] = 0.5 * (t[1] - t[0]);
+        c[n - 1] = 0.5 * (t[n - 1] - t[n - 2]);
+        for (long q = 1; q + 1 < n; q++) c[q] = 0.5 * (t[q + 1] - t[q - 1]);
+    }
+    double cs = 0, cy = 0;
+    for (long q = 0; q < n; q++) { cs += c[q]; cy += c[q] * y[q]; }
+    double ybar = cs > 0 ? cy / cs : 0.0;
+#pragma omp parallel for schedule(static)
+    for (long k = 0; k < nw; k++) {
+        double re = 0, im = 0;
+        for (long q = 0; q < n; q++) {
+            double v = c[q] * (y[q] - ybar);
+            re += v * std::cos(w[k] * t[q]);
+            im -= v * std::sin(w[k] * t[q]);
+        }
+        out[2 * k] = re;
+        out[2 * k + 1] = im;
+    }
+}
 void or_rhs(const oracle* o, const double* m, double are, double aim, double tc, double* dm,
             double* da) {
     cplx d;

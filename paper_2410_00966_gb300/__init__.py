@@ -92,6 +92,10 @@ PROTOTYPES = {
     "mmcq_get_cavity": (ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(mmcq_cavity)]),
     "mmcq_get_dt_history": (ctypes.c_int, [_H, ctypes.c_int, _DP, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "mmcq_eval_field": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, _FP, ctypes.c_int]),
+    "mmcq_set_drive": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+    "mmcq_set_recording": (ctypes.c_int, [_H, ctypes.c_int]),
+    "mmcq_get_mavg_history": (ctypes.c_int, [_H, ctypes.c_int, _DP, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    "mmcq_spectrum": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, _DP, ctypes.c_int, _DP]),
     "mmcq_get_state": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "mmcq_group_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(_H), ctypes.c_int,
                                          ctypes.c_int]),
@@ -312,6 +316,31 @@ class Sim:
 
     def launch_count(self) -> int:
         return int(self._lib.mmcq_launch_count(self._h))
+
+    def set_drive(self, amp, omega_cut, t0=0.0, inst=-1):
+        """B_ext += amp * B_rms,i * sinc(omega_cut (t - t0)) (the paper's Appendix C excitation)."""
+        self._ck(self._lib.mmcq_set_drive(self._h, inst, float(amp), float(omega_cut), float(t0)))
+
+    def set_recording(self, every=1):
+        """Record (t, <m>) after every `every`-th accepted step (0 stops)."""
+        self._ck(self._lib.mmcq_set_recording(self._h, int(every)))
+
+    def mavg_history(self, inst=0) -> np.ndarray:
+        n = ctypes.c_int64()
+        self._ck(self._lib.mmcq_get_mavg_history(self._h, inst, None, 0, ctypes.byref(n)))
+        out = np.zeros((n.value, 4))
+        if n.value:
+            self._ck(self._lib.mmcq_get_mavg_history(self._h, inst, out.ctypes.data_as(_DP), n.value,
+                                                     ctypes.byref(n)))
+        return out
+
+    def spectrum(self, omega, comp=0, inst=0) -> np.ndarray:
+        """Fourier transform (device) of the recorded <m_comp>(t) at angular frequencies omega."""
+        w = np.ascontiguousarray(np.asarray(omega, dtype=np.float64))
+        out = np.zeros(2 * w.size)
+        self._ck(self._lib.mmcq_spectrum(self._h, inst, int(comp), w.ctypes.data_as(_DP), w.size,
+                                         out.ctypes.data_as(_DP)))
+        return out[0::2] + 1j * out[1::2]
 
     def get_state(self) -> bytes:
         """Snapshot of every instance (checkpoint), as bytes."""

@@ -30,6 +30,7 @@ cudaError_t launch_apply_ms(float4*, const float*, long long, int, cudaStream_t)
 cudaError_t launch_get_field(const float4*, float*, long long, cudaStream_t);
 cudaError_t launch_coupling_sum(const Buffers&, long long, double, int, int, double*, cudaStream_t);
 cudaError_t launch_set_dt(InstState*, int, double, cudaStream_t);
+cudaError_t launch_spectrum(const double*, long long, int, const double*, int, double*, cudaStream_t);
 cudaError_t build_demag_kernel(const Plan&, double, double, double, double, float*, double2*, cudaStream_t);
 }  // namespace mq
 
@@ -61,6 +62,9 @@ struct mmcq {
     double setup_ms = 0;
     std::string err;
     bool k1_dirty = true;   // some instance may need its first DP45 stage recomputed
+    int record = 0;         // record <m> every `record` accepted steps (0: off)
+    double* spec_buf = nullptr;   // device scratch of mmcq_spectrum (frequencies + result)
+    int spec_cap = 0;             // frequencies it holds
     // measurement
     int64_t launches = 0;
     bool profiling = false;
@@ -141,9 +145,13 @@ double ms_sum(mmcq_t* h) {
 
 void refresh_scales(mmcq_t* h) {
     double sm = ms_sum(h);
-    for (int b = 0; b < h->P.B; b++)
+    long long nmag = 0;
+    for (float v : h->ms_host) nmag += v > 0;
+    for (int b = 0; b < h->P.B; b++) {
         if (h->g_mode[b])
             h->ip[b].brms_scale = sm > 0 ? h->g[b] * std::sqrt(2.0 * h->hbar / (h->gamma * h->mat.vc * sm)) : 0.0;
+        h->ip[b].inv_nmag = nmag > 0 ? 1.0 / (double)nmag : 0.0;
+    }
 }
 
 void reset_alpha(const InstParams& ip, InstState& s) {
@@ -245,6 +253,7 @@ int enqueue_steps(mmcq_t* h, int64_t n) {
     A.field_only = 0;
     A.inst0 = 0;
     A.tol = (float)h->tol;
+    A.record = h->record;
     const int B = h->P.B;
     for (int64_t it = 0; it < n; it++) {
         if (h->kind == KIND_RK4) {
@@ -356,6 +365,8 @@ int mmcq_create(mmcq_t** out, const mmcq_grid* g, double Ms, double Aex, double 
     Bf.ip = (InstParams*)A(sizeof(InstParams) * P.B);
     Bf.st = (InstState*)A(sizeof(InstState) * P.B);
     Bf.xpart = (double*)A(sizeof(double) * (long long)P.B * P.nblk);
+    Bf.mpart = (double*)A(sizeof(double) * 3LL * P.B * P.nblk);
+    Bf.mhist = nullptr;   // allocated by mmcq_set_recording
     Bf.epart = (float*)A(sizeof(float) * (long long)P.B * P.nblk);
     Bf.counter = (unsigned*)A(sizeof(unsigned) * P.B);
     Bf.hcap = 1 << 16;
@@ -396,6 +407,7 @@ int mmcq_create(mmcq_t** out, const mmcq_grid* g, double Ms, double Aex, double 
     h->ip.assign(P.B, InstParams{});
     h->g.assign(P.B, 0.0);
     h->g_mode.assign(P.B, 0);
+    refresh_scales(h);
     std::vector<InstState> st(P.B);
     for (auto& s : st) {
         std::memset(&s, 0, sizeof(s));
@@ -726,6 +738,70 @@ int mmcq_profile_read(mmcq_t* h, mmcq_kernel_stat* out, int max, int* n) {
 
 int64_t mmcq_launch_count(const mmcq_t* h) { return h ? h->launches : -1; }
 
+// ---- excitation and spectra (Appendix C) --------------------------------------
+int mmcq_set_drive(mmcq_t* h, int inst, double amp, double omega_cut, double t0) {
+    if (!h || !valid_inst(h, inst, true) || !std::isfinite(amp) || !std::isfinite(omega_cut) ||
+        !std::isfinite(t0))
+        return MMCQ_ERR_ARG;
+    for (int b = 0; b < h->P.B; b++)
+        if (inst < 0 || b == inst) {
+            h->ip[b].drv_on = amp != 0.0;
+            h->ip[b].drv_amp = amp;
+            h->ip[b].drv_wcut = omega_cut;
+            h->ip[b].drv_t0 = t0;
+        }
+    return upload_params(h);
+}
+
+int mmcq_set_recording(mmcq_t* h, int every) {
+    if (!h || every < 0) return MMCQ_ERR_ARG;
+    if (every > 0 && !h->Bf.mhist) {
+        h->Bf.mhist = (double*)dev_alloc(h, sizeof(double) * 4LL * h->P.B * h->Bf.hcap);
+        if (!h->Bf.mhist) return fail(h, MMCQ_ERR_CUDA, "device allocation failed");
+    }
+    h->record = every;
+    return MMCQ_OK;
+}
+
+int mmcq_get_mavg_history(mmcq_t* h, int inst, double* out, int64_t max, int64_t* n) {
+    if (!h || !valid_inst(h, inst, false) || max < 0 || (max > 0 && !out)) return MMCQ_ERR_ARG;
+    int r = check_flags(h);
+    InstState s;
+    CK(h, cudaMemcpy(&s, h->Bf.st + inst, sizeof(InstState), cudaMemcpyDeviceToHost));
+    if (n) *n = s.nmh;
+    long long c = s.nmh < h->Bf.hcap ? s.nmh : h->Bf.hcap;
+    if (c > max) c = max;
+    if (c > 0 && h->Bf.mhist)
+        CK(h, cudaMemcpy(out, h->Bf.mhist + 4LL * inst * h->Bf.hcap, sizeof(double) * 4 * c,
+                         cudaMemcpyDeviceToHost));
+    if (s.nmh > h->Bf.hcap && r == MMCQ_OK) return fail(h, MMCQ_ERR_STATE, "m-average history overflowed its capacity");
+    return r;
+}
+
+int mmcq_spectrum(mmcq_t* h, int inst, int comp, const double* omega, int nw, double* out) {
+    if (!h || !valid_inst(h, inst, false) || comp < 0 || comp > 2 || nw < 0 || (nw > 0 && (!omega || !out)))
+        return MMCQ_ERR_ARG;
+    if (nw == 0) return MMCQ_OK;
+    int r = check_flags(h);
+    if (r) return r;
+    if (!h->Bf.mhist) return fail(h, MMCQ_ERR_STATE, "recording was never enabled");
+    InstState s;
+    CK(h, cudaMemcpy(&s, h->Bf.st + inst, sizeof(InstState), cudaMemcpyDeviceToHost));
+    const long long ns = s.nmh < h->Bf.hcap ? s.nmh : h->Bf.hcap;
+    if (nw > h->spec_cap) {
+        h->spec_buf = (double*)dev_alloc(h, sizeof(double) * 3LL * nw);
+        if (!h->spec_buf) { h->spec_cap = 0; return fail(h, MMCQ_ERR_CUDA, "device allocation failed"); }
+        h->spec_cap = nw;
+    }
+    double* dw = h->spec_buf;
+    double* dout = h->spec_buf + nw;
+    CK(h, cudaMemcpyAsync(dw, omega, sizeof(double) * nw, cudaMemcpyHostToDevice, h->stream));
+    CK(h, launch_spectrum(h->Bf.mhist + 4LL * inst * h->Bf.hcap, ns, comp, dw, nw, dout, h->stream));
+    CK(h, cudaMemcpyAsync(out, dout, sizeof(double) * 2 * nw, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return MMCQ_OK;
+}
+
 // ---- checkpoint / resume ---------------------------------------------------
 // Snapshot: SnapHeader, then per instance (B of each, in this order)
 // InstState, InstParams, g (double), g_mode (int32), then m of every instance
@@ -832,7 +908,7 @@ struct mmcq_group {
     cudaEvent_t fork = nullptr, done = nullptr;
     std::vector<cudaEvent_t> join, in;
     cudaGraphExec_t exec = nullptr;
-    std::vector<int> cap_kind, cap_mode;
+    std::vector<int> cap_kind, cap_mode, cap_record;
     std::vector<double> cap_tol;
     std::vector<int64_t> cap_launches;      // kernel launches per replay, per handle
     int64_t replays = 0;
@@ -857,7 +933,9 @@ bool group_stale(const mmcq_group_t* g) {
     if (!g->exec) return true;
     for (size_t i = 0; i < g->hs.size(); i++) {
         const mmcq_t* h = g->hs[i];
-        if (h->kind != g->cap_kind[i] || h->mode != g->cap_mode[i] || h->tol != g->cap_tol[i]) return true;
+        if (h->kind != g->cap_kind[i] || h->mode != g->cap_mode[i] || h->tol != g->cap_tol[i] ||
+            h->record != g->cap_record[i])
+            return true;
     }
     return false;
 }
@@ -894,6 +972,7 @@ int group_capture(mmcq_group_t* g) {
         g->cap_kind[i] = g->hs[i]->kind;
         g->cap_mode[i] = g->hs[i]->mode;
         g->cap_tol[i] = g->hs[i]->tol;
+        g->cap_record[i] = g->hs[i]->record;
     }
     if (r != MMCQ_OK) {
         if (graph) cudaGraphDestroy(graph);
@@ -933,6 +1012,7 @@ int mmcq_group_create(mmcq_group_t** out, mmcq_t* const* handles, int n, int chu
     g->cap_kind.assign(n, -1);
     g->cap_mode.assign(n, -1);
     g->cap_tol.assign(n, -1.0);
+    g->cap_record.assign(n, -1);
     g->cap_launches.assign(n, 0);
     bool ok = cudaSetDevice(g->device) == cudaSuccess &&
               cudaStreamCreateWithFlags(&g->origin, cudaStreamNonBlocking) == cudaSuccess &&
@@ -965,6 +1045,7 @@ int mmcq_group_step(mmcq_group_t* g, int64_t n, double dt) {
         if (h->kind == KIND_DP45 && h->mode == CAV_E && h->k1_dirty) {
             StageArgs A{};
             A.kind = h->kind; A.mode = h->mode; A.terms = MMCQ_TERM_ALL; A.tol = (float)h->tol; A.stage = 0;
+            A.record = h->record;
             int r = run_stage(h, A, h->P.B);
             if (r) return gfail(g, r, "first stage launch failed");
             h->k1_dirty = false;

@@ -66,8 +66,10 @@ struct InstParams {
     double bext[3];
     double wc, kappa, x0, p0;
     double brms_scale;   // B_rms,i = brms_scale * profile_i
+    double drv_amp, drv_wcut, drv_t0;   // B_ext += drv_amp B_rms,i sinc(drv_wcut (t - drv_t0))
+    double inv_nmag;     // 1 / number of magnetised cells (spatial average of m)
     int cav_on;
-    int pad_;
+    int drv_on;
 };
 
 // Per-instance integrator and cavity state (owned by the device).
@@ -80,6 +82,7 @@ struct InstState {
     double X;               // last reduced coupling sum (includes V_c)
     double err;             // last error estimate (DP45)
     long long nacc, nrej, nhist;
+    long long nmh;          // recorded spatial averages of m
     int mcur;               // which m buffer holds the accepted state
     int k1slot;             // DP45: k buffer holding stage 1 (FSAL)
     int have_k1;            // DP45: stage 1 valid for the current state
@@ -103,6 +106,8 @@ struct Buffers {
     unsigned* counter;  // [B] blocks finished in the current kernel
     double* hist;     // [B][hcap] accepted step lengths
     int hcap;
+    double* mpart;    // [B][nrows-blocks][3] FP64 partial sums of m (recording only)
+    double* mhist;    // [B][hcap][4] t, <mx>, <my>, <mz> after accepted steps (recording only)
     int* flags;
     const float2* tw; // [twn] exp(-2 pi i k / twn)
     float4* fout;     // [N] field output of eval_field
@@ -117,6 +122,7 @@ struct StageArgs {
     int field_only;  // eval_field: write the field, no state change
     int inst0;     // first instance of this launch (eval_field: one instance)
     float tol;
+    int record;    // record <m> every `record` accepted steps (0: off)
 };
 
 }  // namespace mq

@@ -121,6 +121,7 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
     __shared__ double s_red[32];
     __shared__ float s_redf[32];
     __shared__ double s_gamma;
+    __shared__ float s_drive;
     __shared__ int s_last;
     const int b = A.inst0 + blockIdx.y;
     const InstState& st = Bf.st[b];
@@ -166,7 +167,10 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
         }
     }
     for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) cp_async16(mrow + i, msrc + base + i);
-    if (threadIdx.x == 0) s_gamma = stage_gamma(A, ip, st, mat);
+    if (threadIdx.x == 0) {
+        s_gamma = stage_gamma(A, ip, st, mat);
+        s_drive = (float)drive_factor(A, ip, st);
+    }
     cp_async_wait_all();
     __syncthreads();
     // Z[k] = (X[k] + conj X[L-k]) + i e^{+2 pi i k / px} (X[k] - conj X[L-k]), in place by pairs
@@ -203,9 +207,10 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
 
     const bool want_demag = A.terms & 1, want_exch = A.terms & 2;
     CellUpdate cu;
-    cu.init(Bf, A, st, ip, (float)s_gamma, cb);
+    cu.init(Bf, A, st, ip, (float)s_gamma, s_drive, cb);
     const long long pl = (long long)nx * P.ny;
     double xacc = 0.0;
+    double macc[3] = {0.0, 0.0, 0.0};
     float emax = 0.f;
     bool bad = false;
     for (int ii = threadIdx.x; ii < nr * nx; ii += blockDim.x) {
@@ -244,10 +249,10 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
             float inv = 1.f / Ms;
             Bx += hx * inv; By += hy * inv; Bz += hz * inv;
         }
-        cu.run(mat, Bf, i, m, Bx, By, Bz, xacc, emax, bad);
+        cu.run(mat, Bf, i, m, Bx, By, Bz, xacc, macc, emax, bad);
     }
     if (A.field_only) return;
-    stage_epilogue(P, mat, Bf, A, b, blockIdx.x, P.nblk, xacc, emax, bad, s_red, s_redf, &s_last);
+    stage_epilogue(P, mat, Bf, A, b, blockIdx.x, P.nblk, xacc, emax, bad, s_red, s_redf, &s_last, cu.rec, macc);
 }
 
 // ---------------------------------------------------------------------------
@@ -318,6 +323,46 @@ __global__ void k_coupling_sum(const float4* m0, const float4* m1, const InstSta
     if (threadIdx.x == 0) out[blockIdx.x] = ip[b].cav_on ? acc * ip[b].brms_scale * vc : 0.0;
 }
 
+// Trapezoid-weighted Fourier transform of one component of the recorded
+// spatial averages (t_n, <m>_n), n < ns (Appendix C: the broadband response
+// is the numerical Fourier transform of the averaged m):
+// S(w) = sum_n c_n (y_n - ybar) exp(-i w t_n), c_n the trapezoid weights of
+// the sample times, ybar the time average.  One block per frequency (grid
+// stride), FP64, fixed-order reductions.
+__global__ void k_spectrum(const double* mh, long long ns, int comp, const double* w, int nw, double* out) {
+    __shared__ double red[32];
+    auto weight = [&](long long q) {
+        if (ns < 2) return 0.0;
+        const double tl = mh[4 * (q > 0 ? q - 1 : q)], tr = mh[4 * (q + 1 < ns ? q + 1 : q)];
+        return 0.5 * (tr - tl);
+    };
+    double cs = 0.0, cy = 0.0;
+    for (long long q = threadIdx.x; q < ns; q += blockDim.x) {
+        const double c = weight(q);
+        cs += c;
+        cy += c * mh[4 * q + 1 + comp];
+    }
+    cs = block_sum_d(cs, red);
+    cy = block_sum_d(cy, red);
+    __shared__ double s_ybar;
+    if (threadIdx.x == 0) s_ybar = cs > 0.0 ? cy / cs : 0.0;
+    __syncthreads();
+    const double ybar = s_ybar;
+    for (int k = blockIdx.x; k < nw; k += gridDim.x) {
+        double re = 0.0, im = 0.0;
+        for (long long q = threadIdx.x; q < ns; q += blockDim.x) {
+            const double v = weight(q) * (mh[4 * q + 1 + comp] - ybar);
+            double sn, c;
+            sincos(w[k] * mh[4 * q], &sn, &c);
+            re += v * c;
+            im -= v * sn;
+        }
+        re = block_sum_d(re, red);
+        im = block_sum_d(im, red);
+        if (threadIdx.x == 0) { out[2 * k] = re; out[2 * k + 1] = im; }
+    }
+}
+
 __global__ void k_set_dt(InstState* st, int B, double dt) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b < B) st[b].dt = dt;
@@ -376,6 +421,14 @@ cudaError_t launch_xinv(const Plan& P, const Material& mat, const Buffers& Bf, c
 #undef MMCQ_CASE
         default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spectrum(const double* mh, long long ns, int comp, const double* w, int nw, double* out,
+                            cudaStream_t s) {
+    const int blocks = nw < 1024 ? nw : 1024;
+    if (blocks < 1) return cudaSuccess;
+    k_spectrum<<<blocks, 256, 0, s>>>(mh, ns, comp, w, nw, out);
     return cudaGetLastError();
 }
 

@@ -70,7 +70,8 @@ static __device__ double gamma_p(const InstParams& ip, const InstState& s, doubl
 // Eq. eqmotionaclasical with omega_c -> omega_c - i kappa), accumulators
 // (P-mode, Eq. Sdiscrete / Cdiscrete), time, accept / reject and step size.
 static __device__ void finish_stage(const Plan& P, const Material& mat, const StageArgs& A, const InstParams& ip,
-                             InstState& s, double Xsum, float errmax, double* hist, int hcap, int* flags) {
+                             InstState& s, double Xsum, float errmax, double* hist, int hcap, int* flags,
+                             const double* msum = nullptr, double* mhist = nullptr) {
     const double X = Xsum * mat.vc;
     const int k = A.stage;
     const bool ecav = ip.cav_on && A.mode == CAV_E;
@@ -132,6 +133,16 @@ static __device__ void finish_stage(const Plan& P, const Material& mat, const St
         if (s.nhist < hcap) hist[s.nhist] = dt;
         else atomicOr(flags, FLAG_HIST_FULL);
         s.nhist++;
+        if (A.record > 0 && msum && mhist && s.nacc % A.record == 0) {
+            if (s.nmh < hcap) {
+                double* e = mhist + 4 * s.nmh;
+                e[0] = s.t;
+                for (int c = 0; c < 3; c++) e[1 + c] = msum[c] * ip.inv_nmag;
+            } else {
+                atomicOr(flags, FLAG_HIST_FULL);
+            }
+            s.nmh++;
+        }
         if (pcav) {
             double e = exp(ip.kappa * s.tcav), sn, cs;
             sincos(ip.wc * s.tcav, &sn, &cs);
@@ -266,15 +277,16 @@ struct StageInput {
 // the DP45 error.  Material constants and buffer pointers are read from the
 // kernel's parameter block at each use.
 struct CellUpdate {
-    float G, bs, dt, bex, bey, bez;
-    bool cav_on, want_anis, want_zee, want_cav, field_only;
+    float G, bs, dt, bex, bey, bez, D;
+    bool cav_on, want_anis, want_zee, want_cav, field_only, rec;
     int K, s, mode;
     long long cb;
     float4* kout;
 
     __device__ __forceinline__ void init(const Buffers& Bf, const StageArgs& A, const InstState& st,
-                                         const InstParams& ip, float Gamma, long long cb_) {
+                                         const InstParams& ip, float Gamma, float drive, long long cb_) {
         G = Gamma;
+        D = drive;
         bs = (float)ip.brms_scale;
         dt = (float)st.dt;
         bex = (float)ip.bext[0]; bey = (float)ip.bext[1]; bez = (float)ip.bext[2];
@@ -282,6 +294,7 @@ struct CellUpdate {
         want_anis = A.terms & 4; want_zee = A.terms & 8; want_cav = A.terms & 16;
         field_only = A.field_only != 0;
         K = A.kind; s = A.stage; mode = A.mode;
+        rec = A.record > 0 && !field_only && s == (K == KIND_RK4 ? 3 : 6);
         cb = cb_;
         const int k1slot = st.k1slot;
         kout = K == KIND_RK4 ? (s < 3 ? Bf.k[s] : nullptr)
@@ -290,7 +303,8 @@ struct CellUpdate {
 
     // (Bx, By, Bz) holds demag + exchange on entry
     __device__ __forceinline__ void run(const Material& mat, const Buffers& Bf, long long i, float4 m, float Bx,
-                                        float By, float Bz, double& xacc, float& emax, bool& bad) const {
+                                        float By, float Bz, double& xacc, double (&macc)[3], float& emax,
+                                        bool& bad) const {
         const float Ms = m.w;
         float px_ = 0.f, py_ = 0.f, pz_ = 0.f;
         if (Ms > 0.f) {
@@ -300,10 +314,12 @@ struct CellUpdate {
                 Bx += f * mat.u[0]; By += f * mat.u[1]; Bz += f * mat.u[2];
             }
             if (want_zee) { Bx += bex; By += bey; Bz += bez; }
-            if (cav_on) {
+            if (cav_on || D != 0.f) {
                 if (Bf.prof) { float4 p = __ldg(Bf.prof + (i - cb)); px_ = bs * p.x; py_ = bs * p.y; pz_ = bs * p.z; }
                 else { py_ = bs; }
-                if (want_cav) { Bx += G * px_; By += G * py_; Bz += G * pz_; }
+                if (cav_on && want_cav) { Bx += G * px_; By += G * py_; Bz += G * pz_; }
+                // Appendix C excitation, part of the external field
+                if (want_zee) { Bx += D * px_; By += D * py_; Bz += D * pz_; }
             }
         }
         if (field_only) {
@@ -317,6 +333,7 @@ struct CellUpdate {
         if (!(Ms > 0.f)) kk = make_float4(0.f, 0.f, 0.f, 0.f);
         if (!isfinite(kk.x) || !isfinite(kk.y) || !isfinite(kk.z)) bad = true;
         float4 mx = m;   // m used for the coupling sum of this launch
+        float4 mrec = m; // state being accepted (recorded spatial average)
         if (K == KIND_RK4) {
             if (s < 3) {
                 kout[i] = kk;
@@ -334,6 +351,7 @@ struct CellUpdate {
                 mn.w = m0.w;
                 Bf.m[0][i] = mn;
                 if (mode == CAV_P) mx = mn;
+                mrec = mn;
             }
         } else {
             kout[i] = kk;
@@ -347,8 +365,18 @@ struct CellUpdate {
         // per-cell product in FP32, accumulated in FP64 (the sum over cells is
         // the quantity that needs the range; FP64 arithmetic is ~1/64 rate here)
         if (cav_on) xacc += (double)(Ms * (mx.x * px_ + mx.y * py_ + mx.z * pz_));
+        if (rec && Ms > 0.f) { macc[0] += mrec.x; macc[1] += mrec.y; macc[2] += mrec.z; }
     }
 };
+
+// Factor of the Appendix C excitation at this launch's stage time (simulation
+// time t + c_s dt): drv_amp sinc(drv_wcut (t - drv_t0)), sinc(0) = 1.
+static __device__ double drive_factor(const StageArgs& A, const InstParams& ip, const InstState& st) {
+    if (!ip.drv_on) return 0.0;
+    const double ts = st.t + (A.field_only ? 0.0 : c_cd[A.kind][A.stage] * st.dt);
+    const double x = ip.drv_wcut * (ts - ip.drv_t0);
+    return ip.drv_amp * (x == 0.0 ? 1.0 : sin(x) / x);
+}
 
 // Gamma(t) for the stage of this launch (E-mode: 2 Re alpha of the stage;
 // P-mode: Eq. gammadiscretefinal at the stage time).
@@ -364,14 +392,20 @@ static __device__ double stage_gamma(const StageArgs& A, const InstParams& ip, c
 // `nparts` = blocks per instance, `part` = this block's index among them.
 static __device__ void stage_epilogue(const Plan& P, const Material& mat, const Buffers& Bf, const StageArgs& A,
                                       int b, int part, int nparts, double xacc, float emax, bool bad,
-                                      double* s_red, float* s_redf, int* s_last) {
+                                      double* s_red, float* s_redf, int* s_last, bool rec = false,
+                                      const double* macc = nullptr) {
     if (bad) atomicOr(Bf.flags, FLAG_NAN);
     double xb = block_sum_d(xacc, s_red);
     float eb = block_max_f(emax, s_redf);
     const long long pb = (long long)b * nparts;
+    double mb[3] = {0.0, 0.0, 0.0};
+    if (rec)
+        for (int c = 0; c < 3; c++) mb[c] = block_sum_d(macc[c], s_red);
     if (threadIdx.x == 0) {
         Bf.xpart[pb + part] = xb;
         Bf.epart[pb + part] = eb;
+        if (rec)
+            for (int c = 0; c < 3; c++) Bf.mpart[3 * (pb + part) + c] = mb[c];
         __threadfence();
         unsigned prev = atomicAdd(Bf.counter + b, 1u);
         *s_last = prev == (unsigned)(nparts - 1);
@@ -387,9 +421,18 @@ static __device__ void stage_epilogue(const Plan& P, const Material& mat, const 
     }
     xsum = block_sum_d(xsum, s_red);
     em = block_max_f(em, s_redf);
+    double msum[3] = {0.0, 0.0, 0.0};
+    if (rec) {
+        for (int c = 0; c < 3; c++) {
+            double v = 0.0;
+            for (int r = threadIdx.x; r < nparts; r += blockDim.x) v += __ldcg(Bf.mpart + 3 * (pb + r) + c);
+            msum[c] = block_sum_d(v, s_red);
+        }
+    }
     if (threadIdx.x == 0) {
         InstState ns = Bf.st[b];
-        finish_stage(P, mat, A, Bf.ip[b], ns, xsum, em, Bf.hist + (long long)b * Bf.hcap, Bf.hcap, Bf.flags);
+        finish_stage(P, mat, A, Bf.ip[b], ns, xsum, em, Bf.hist + (long long)b * Bf.hcap, Bf.hcap, Bf.flags,
+                     rec ? msum : nullptr, rec ? Bf.mhist + 4LL * b * Bf.hcap : nullptr);
         Bf.st[b] = ns;
         Bf.counter[b] = 0u;
     }
