@@ -114,7 +114,10 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xfwd(Pla
 // x inverse + local fields + torque + RK bookkeeping + cavity reduction.
 // Shared memory: xs[k][line] (k <= L, line = 3 r + comp), then m rows.
 // ---------------------------------------------------------------------------
-template <int L>
+// REC: this launch records the spatial average of the state being accepted
+// (the last stage of a step with recording on); a separate instantiation so
+// that the common launches carry no extra accumulators.
+template <int L, bool REC>
 __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Plan P, Material mat, Buffers Bf, StageArgs A) {
     constexpr int NPT = ColShape<L>::NPT, N1 = ColShape<L>::N1;
     extern __shared__ float2 sm[];
@@ -210,7 +213,7 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
     cu.init(Bf, A, st, ip, (float)s_gamma, s_drive, cb);
     const long long pl = (long long)nx * P.ny;
     double xacc = 0.0;
-    double macc[3] = {0.0, 0.0, 0.0};
+    double macc[REC ? 3 : 1] = {};
     float emax = 0.f;
     bool bad = false;
     for (int ii = threadIdx.x; ii < nr * nx; ii += blockDim.x) {
@@ -249,10 +252,10 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
             float inv = 1.f / Ms;
             Bx += hx * inv; By += hy * inv; Bz += hz * inv;
         }
-        cu.run(mat, Bf, i, m, Bx, By, Bz, xacc, macc, emax, bad);
+        cu.run<REC>(mat, Bf, i, m, Bx, By, Bz, xacc, macc, emax, bad);
     }
     if (A.field_only) return;
-    stage_epilogue(P, mat, Bf, A, b, blockIdx.x, P.nblk, xacc, emax, bad, s_red, s_redf, &s_last, cu.rec, macc);
+    stage_epilogue<REC>(P, mat, Bf, A, b, blockIdx.x, P.nblk, xacc, emax, bad, s_red, s_redf, &s_last, macc);
 }
 
 // ---------------------------------------------------------------------------
@@ -415,8 +418,13 @@ cudaError_t launch_xinv(const Plan& P, const Material& mat, const Buffers& Bf, c
     dim3 grid(P.nblk, nb);
     const int th = xthreads(P);
     const size_t sm = xinv_smem(P);
+    const bool rec = A.record > 0 && !A.field_only && A.stage == (A.kind == KIND_RK4 ? 3 : 6);
     switch (P.L) {
-#define MMCQ_CASE(Lv) case Lv: k_xinv<Lv><<<grid, th, sm, s>>>(P, mat, Bf, A); break;
+#define MMCQ_CASE(Lv)                                                      \
+    case Lv:                                                               \
+        if (rec) k_xinv<Lv, true><<<grid, th, sm, s>>>(P, mat, Bf, A);    \
+        else k_xinv<Lv, false><<<grid, th, sm, s>>>(P, mat, Bf, A);       \
+        break;
         MMCQ_XCASES(MMCQ_CASE)
 #undef MMCQ_CASE
         default: return cudaErrorInvalidValue;
@@ -469,7 +477,10 @@ cudaError_t set_smem_limits() {
 #define MMCQ_CASE(Lv)                                                                                         \
     if ((e = cudaFuncSetAttribute(k_xfwd<Lv>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess) \
         return e;                                                                                             \
-    if ((e = cudaFuncSetAttribute(k_xinv<Lv>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess) \
+    if ((e = cudaFuncSetAttribute(k_xinv<Lv, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) !=        \
+        cudaSuccess)                                                                                               \
+        return e;                                                                                                  \
+    if ((e = cudaFuncSetAttribute(k_xinv<Lv, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess) \
         return e;
     MMCQ_XCASES(MMCQ_CASE)
 #undef MMCQ_CASE

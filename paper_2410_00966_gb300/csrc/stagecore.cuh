@@ -278,7 +278,7 @@ struct StageInput {
 // kernel's parameter block at each use.
 struct CellUpdate {
     float G, bs, dt, bex, bey, bez, D;
-    bool cav_on, want_anis, want_zee, want_cav, field_only, rec;
+    bool cav_on, want_anis, want_zee, want_cav, field_only;
     int K, s, mode;
     long long cb;
     float4* kout;
@@ -294,7 +294,6 @@ struct CellUpdate {
         want_anis = A.terms & 4; want_zee = A.terms & 8; want_cav = A.terms & 16;
         field_only = A.field_only != 0;
         K = A.kind; s = A.stage; mode = A.mode;
-        rec = A.record > 0 && !field_only && s == (K == KIND_RK4 ? 3 : 6);
         cb = cb_;
         const int k1slot = st.k1slot;
         kout = K == KIND_RK4 ? (s < 3 ? Bf.k[s] : nullptr)
@@ -302,8 +301,9 @@ struct CellUpdate {
     }
 
     // (Bx, By, Bz) holds demag + exchange on entry
+    template <bool REC>
     __device__ __forceinline__ void run(const Material& mat, const Buffers& Bf, long long i, float4 m, float Bx,
-                                        float By, float Bz, double& xacc, double (&macc)[3], float& emax,
+                                        float By, float Bz, double& xacc, double (&macc)[REC ? 3 : 1], float& emax,
                                         bool& bad) const {
         const float Ms = m.w;
         float px_ = 0.f, py_ = 0.f, pz_ = 0.f;
@@ -365,7 +365,9 @@ struct CellUpdate {
         // per-cell product in FP32, accumulated in FP64 (the sum over cells is
         // the quantity that needs the range; FP64 arithmetic is ~1/64 rate here)
         if (cav_on) xacc += (double)(Ms * (mx.x * px_ + mx.y * py_ + mx.z * pz_));
-        if (rec && Ms > 0.f) { macc[0] += mrec.x; macc[1] += mrec.y; macc[2] += mrec.z; }
+        if constexpr (REC) {
+            if (Ms > 0.f) { macc[0] += mrec.x; macc[1] += mrec.y; macc[2] += mrec.z; }
+        }
     }
 };
 
@@ -390,10 +392,11 @@ static __device__ double stage_gamma(const StageArgs& A, const InstParams& ip, c
 // Block partials of X and of the DP45 error; the last block of the instance
 // to arrive reduces all partials in a fixed order and runs finish_stage.
 // `nparts` = blocks per instance, `part` = this block's index among them.
+template <bool REC>
 static __device__ void stage_epilogue(const Plan& P, const Material& mat, const Buffers& Bf, const StageArgs& A,
                                       int b, int part, int nparts, double xacc, float emax, bool bad,
-                                      double* s_red, float* s_redf, int* s_last, bool rec = false,
-                                      const double* macc = nullptr) {
+                                      double* s_red, float* s_redf, int* s_last, const double* macc) {
+    constexpr bool rec = REC;
     if (bad) atomicOr(Bf.flags, FLAG_NAN);
     double xb = block_sum_d(xacc, s_red);
     float eb = block_max_f(emax, s_redf);
