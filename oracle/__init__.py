@@ -99,6 +99,15 @@ def _load():
         "or_demag_at": (None, [p, dp, ctypes.POINTER(ctypes.c_long), l, dp]),
         "or_energy": (None, [p, dp]),
         "or_set_drive": (None, [p, d, d, d]),
+        "or_set_cavity_mode": (None, [p, i, d, d, d, dp, i]),
+        "or_set_cavity_init_mode": (None, [p, i, d, d]),
+        "or_get_cavity_mode": (None, [p, i, dp]),
+        "or_get_brms_mode": (None, [p, i, dp]),
+        "or_set_alpha_mode": (None, [p, i, d, d]),
+        "or_field_modes": (None, [p, dp, dp, dp]),
+        "or_rhs_modes": (None, [p, dp, dp, d, dp, dp]),
+        "or_cavity_X_mode": (d, [p, dp, i]),
+        "or_max_modes": (i, []),
         "or_drive_factor": (d, [p, d]),
         "or_set_recording": (None, [p, i]),
         "or_mavg_history": (l, [p, dp, l]),
@@ -293,6 +302,53 @@ class Oracle:
                               c.size, _dp(out))
         return out
 
+    # ---- cavity modes (mode 0 is the single mode set by set_cavity) ----------
+    def set_cavity_mode(self, k, omega_c, kappa, g=0.0, profile=None, profile_is_brms=False):
+        prof = None if profile is None else _f64(profile, 3 * self.n)
+        self._lib.or_set_cavity_mode(self._h, k, omega_c, kappa, g, None if prof is None else _dp(prof),
+                                     int(bool(profile_is_brms)))
+
+    def set_cavity_init_mode(self, k, x0, p0):
+        self._lib.or_set_cavity_init_mode(self._h, k, x0, p0)
+
+    def cavity_mode(self, k) -> dict:
+        out = np.zeros(12)
+        self._lib.or_get_cavity_mode(self._h, k, _dp(out))
+        keys = ["t", "t_cav", "re_alpha", "im_alpha", "n_photon", "Gamma", "S", "C", "X", "dt",
+                "accepted", "rejected"]
+        return dict(zip(keys, out.tolist()))
+
+    def get_brms_mode(self, k) -> np.ndarray:
+        out = np.zeros((self.n, 3))
+        self._lib.or_get_brms_mode(self._h, k, _dp(out))
+        return out
+
+    def set_alpha_mode(self, k, re, im):
+        self._lib.or_set_alpha_mode(self._h, k, re, im)
+
+    def field_modes(self, m, Gammas):
+        mm = _f64(m, 3 * self.n)
+        G = np.zeros(max_modes())
+        G[:len(Gammas)] = Gammas
+        out = np.zeros((self.n, 3))
+        self._lib.or_field_modes(self._h, _dp(mm), _dp(G), _dp(out))
+        return out
+
+    def rhs_modes(self, m, alphas, t_cav=0.0):
+        """dm/dt and d alpha_k/dt with every mode's amplitude given (list of complex)."""
+        mm = _f64(m, 3 * self.n)
+        K = max_modes()
+        a = np.zeros(2 * K)
+        for k, v in enumerate(alphas):
+            a[2 * k], a[2 * k + 1] = v.real, v.imag
+        dm = np.zeros((self.n, 3))
+        da = np.zeros(2 * K)
+        self._lib.or_rhs_modes(self._h, _dp(mm), _dp(a), t_cav, _dp(dm), _dp(da))
+        return dm, da[0::2] + 1j * da[1::2]
+
+    def cavity_X_mode(self, m, k):
+        return self._lib.or_cavity_X_mode(self._h, _dp(_f64(m, 3 * self.n)), k)
+
     def set_drive(self, amp, omega_cut, t0=0.0):
         """Appendix C excitation: B_ext += amp * B_rms,i * sinc(omega_cut (t - t0)); amp = 0 turns it off."""
         self._lib.or_set_drive(self._h, amp, omega_cut, t0)
@@ -328,3 +384,8 @@ def spectrum(t, y, omega) -> np.ndarray:
     out = np.zeros(2 * w.size)
     lib.or_spectrum(_dp(t), _dp(y), t.size, _dp(w), w.size, _dp(out))
     return out[0::2] + 1j * out[1::2]
+
+
+def max_modes() -> int:
+    """Cavity modes the oracle holds (mode 0 is the paper's single mode)."""
+    return _load().or_max_modes()

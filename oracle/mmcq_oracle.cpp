@@ -237,6 +237,11 @@ static int pow2_at_least(int n) {
 enum { OR_DEMAG_NONE = 0, OR_DEMAG_DIRECT = 1, OR_DEMAG_FFT = 2 };
 enum { OR_RK4 = 0, OR_DP45 = 1 };
 enum { OR_CAV_E = 0, OR_CAV_P = 1 };
+// Cavity modes: mode 0 is the paper's single mode (Sec. 2.2); the paper notes
+// that more modes follow the same equations, each with its own B_rms map
+// (Sec. 4, multimode remark).  Mode k has its own omega_c, kappa, x0, p0,
+// alpha and S, C; the cavity time t_cav is shared.
+static const int OR_MAX_MODES = 4;
 
 struct oracle {
     int nx, ny, nz;
@@ -247,13 +252,13 @@ struct oracle {
     std::vector<double> ms;    // [n]
     std::vector<double> m;     // [n*3]
     double bext[3];
-    // cavity (Sec. 2.2 / 3.1)
-    int cav_on;
-    double wc, kappa, x0, p0;
-    std::vector<double> brms;  // [n*3] in tesla
+    // cavity modes (Sec. 2.2 / 3.1)
+    int cav_on[OR_MAX_MODES];
+    double wc[OR_MAX_MODES], kappa[OR_MAX_MODES], x0[OR_MAX_MODES], p0[OR_MAX_MODES];
+    std::vector<double> brms[OR_MAX_MODES];  // [n*3] in tesla
     int cav_mode;
-    cplx a;        // E-mode photon amplitude alpha
-    double S, C;   // P-mode accumulators (include the cell volume V_c)
+    cplx a[OR_MAX_MODES];                    // E-mode photon amplitudes alpha_k
+    double S[OR_MAX_MODES], C[OR_MAX_MODES]; // P-mode accumulators (include V_c)
     double t, tcav;
     // excitation of Appendix C: B_ext += amp B_rms,i sinc(omega_cut (t - t0))
     int drv_on;
@@ -383,27 +388,33 @@ static void anis_field(const oracle* o, const double* m, double* B) {
     }
 }
 
-// X = V_c sum_i Ms_i m_i . B_rms,i  -- the coupling-weighted magnetisation
-// that drives the cavity (Eq. gammafinal integrand times V_c).
-static double cavity_X(const oracle* o, const double* m) {
+// X_k = V_c sum_i Ms_i m_i . B_rms,k,i  -- the coupling-weighted magnetisation
+// that drives cavity mode k (Eq. gammafinal integrand times V_c).
+static double cavity_X(const oracle* o, const double* m, int k = 0) {
+    const double* b = o->brms[k].data();
     double s = 0;
     for (long i = 0; i < o->n; i++)
-        s += o->ms[i] * (m[3 * i] * o->brms[3 * i] + m[3 * i + 1] * o->brms[3 * i + 1] +
-                         m[3 * i + 2] * o->brms[3 * i + 2]);
+        s += o->ms[i] * (m[3 * i] * b[3 * i] + m[3 * i + 1] * b[3 * i + 1] + m[3 * i + 2] * b[3 * i + 2]);
     return o->vc * s;
 }
 
-// Gamma(t) from the P-mode accumulators, Eq. (gammadiscretefinal), with
+// Gamma_k(t) from the P-mode accumulators, Eq. (gammadiscretefinal), with
 // x0 = 2 Re alpha0, p0 = -2 Im alpha0 and S, C already carrying V_c.
-static double gamma_P(const oracle* o, double tc) {
-    double e = std::exp(-o->kappa * tc);
-    return e * std::cos(o->wc * tc) * (o->x0 - 2.0 * o->S / o->hbar) -
-           e * std::sin(o->wc * tc) * (o->p0 - 2.0 * o->C / o->hbar);
+static double gamma_P(const oracle* o, int k, double tc) {
+    double e = std::exp(-o->kappa[k] * tc);
+    return e * std::cos(o->wc[k] * tc) * (o->x0[k] - 2.0 * o->S[k] / o->hbar) -
+           e * std::sin(o->wc[k] * tc) * (o->p0[k] - 2.0 * o->C[k] / o->hbar);
+}
+
+static bool any_cavity(const oracle* o) {
+    for (int k = 0; k < OR_MAX_MODES; k++)
+        if (o->cav_on[k]) return true;
+    return false;
 }
 
 // Total effective field B_eff' = B_ext + B_demag + B_exch + B_anis + B_rms*Gamma
 // (Sec. 2.1 term list and Eq. bcav).
-static void total_field(const oracle* o, const double* m, double Gamma, double* B, double drive = 0.0) {
+static void total_field(const oracle* o, const double* m, const double* Gamma, double* B, double drive = 0.0) {
     std::vector<double> t1(3 * o->n), t2(3 * o->n);
     demag_field(o, m, B);
     exchange_field(o, m, t1.data());
@@ -411,15 +422,17 @@ static void total_field(const oracle* o, const double* m, double Gamma, double* 
     for (long i = 0; i < o->n; i++)
         for (int c = 0; c < 3; c++) {
             double b = B[3 * i + c] + t1[3 * i + c] + t2[3 * i + c] + o->bext[c];
-            if (o->cav_on) b += o->brms[3 * i + c] * Gamma;
-            if (o->ms[i] > 0) b += drive * o->brms[3 * i + c];
+            for (int k = 0; k < OR_MAX_MODES; k++)
+                if (o->cav_on[k]) b += o->brms[k][3 * i + c] * Gamma[k];
+            if (o->ms[i] > 0) b += drive * o->brms[0][3 * i + c];
             B[3 * i + c] = b;
         }
 }
 
 // The excitation of Appendix C (the example script adds amp B_rms sin(w t)/(w t)
-// to B_ext): the factor amp sinc(omega_cut (t - t0)) at simulation time t, with
-// sinc(0) = 1.
+// to B_ext, with the B_rms map of the cavity mode): the factor
+// amp sinc(omega_cut (t - t0)) at simulation time t, with sinc(0) = 1; it
+// multiplies the map of mode 0.
 static double drive_factor(const oracle* o, double t) {
     if (!o->drv_on) return 0.0;
     double x = o->drv_wcut * (t - o->drv_t0);
@@ -444,20 +457,24 @@ static void llg_rhs(const oracle* o, const double* m, const double* B, double* d
 // d(alpha)/dt = -(kappa + i omega_c) alpha + i X / hbar (Eq. eqmotionaclasical
 // with omega_c -> omega_c - i kappa; the spin operator is S = -Ms m V_c/gamma,
 // Sec. 2.1).  P-mode: Gamma from the accumulators, alpha not integrated.
-static void rhs(const oracle* o, const double* m, cplx a, double tc, double* dm, cplx* da,
+// a, da: one amplitude per mode (OR_MAX_MODES).
+static void rhs(const oracle* o, const double* m, const cplx* a, double tc, double* dm, cplx* da,
                 double* Xout, double ts = 0.0) {
-    double Gamma = 0;
-    if (o->cav_on) Gamma = (o->cav_mode == OR_CAV_E) ? 2.0 * a.real() : gamma_P(o, tc);
+    double Gamma[OR_MAX_MODES] = {0, 0, 0, 0};
+    for (int k = 0; k < OR_MAX_MODES; k++)
+        if (o->cav_on[k]) Gamma[k] = (o->cav_mode == OR_CAV_E) ? 2.0 * a[k].real() : gamma_P(o, k, tc);
     std::vector<double> B(3 * o->n);
     total_field(o, m, Gamma, B.data(), drive_factor(o, ts));
     llg_rhs(o, m, B.data(), dm);
-    double X = o->cav_on ? cavity_X(o, m) : 0.0;
-    if (Xout) *Xout = X;
-    if (da) {
-        if (o->cav_on && o->cav_mode == OR_CAV_E)
-            *da = -cplx(o->kappa, o->wc) * a + cplx(0.0, X / o->hbar);
-        else
-            *da = 0;
+    for (int k = 0; k < OR_MAX_MODES; k++) {
+        double X = o->cav_on[k] ? cavity_X(o, m, k) : 0.0;
+        if (Xout) Xout[k] = X;
+        if (da) {
+            if (o->cav_on[k] && o->cav_mode == OR_CAV_E)
+                da[k] = -cplx(o->kappa[k], o->wc[k]) * a[k] + cplx(0.0, X / o->hbar);
+            else
+                da[k] = 0;
+        }
     }
 }
 
@@ -491,12 +508,13 @@ static void after_accept(oracle* o, double dt) {
         o->mavg.push_back(o->t);
         for (int c = 0; c < 3; c++) o->mavg.push_back(nm ? sm[c] / nm : 0.0);
     }
-    if (o->cav_on && o->cav_mode == OR_CAV_P) {
-        double X = cavity_X(o, o->m.data());
+    for (int k = 0; k < OR_MAX_MODES; k++) {
+        if (!o->cav_on[k] || o->cav_mode != OR_CAV_P) continue;
+        double X = cavity_X(o, o->m.data(), k);
         double tc = o->tcav;
-        double e = std::exp(o->kappa * tc);
-        o->S += e * std::sin(o->wc * tc) * X * dt;
-        o->C += e * std::cos(o->wc * tc) * X * dt;
+        double e = std::exp(o->kappa[k] * tc);
+        o->S[k] += e * std::sin(o->wc[k] * tc) * X * dt;
+        o->C[k] += e * std::cos(o->wc[k] * tc) * X * dt;
     }
 }
 
@@ -504,22 +522,24 @@ static void after_accept(oracle* o, double dt) {
 static void step_rk4(oracle* o, double dt) {
     long n3 = 3 * o->n;
     std::vector<double> k[4], tmp(n3);
-    cplx ka[4];
+    cplx ka[4][OR_MAX_MODES];
     for (int s = 0; s < 4; s++) k[s].resize(n3);
     const double c[4] = {0.0, 0.5, 0.5, 1.0};
     for (int s = 0; s < 4; s++) {
-        cplx as = o->a;
+        cplx as[OR_MAX_MODES];
+        for (int j = 0; j < OR_MAX_MODES; j++) as[j] = o->a[j];
         if (s == 0) {
             for (long q = 0; q < n3; q++) tmp[q] = o->m[q];
         } else {
             for (long q = 0; q < n3; q++) tmp[q] = o->m[q] + c[s] * dt * k[s - 1][q];
-            as = o->a + c[s] * dt * ka[s - 1];
+            for (int j = 0; j < OR_MAX_MODES; j++) as[j] = o->a[j] + c[s] * dt * ka[s - 1][j];
         }
-        rhs(o, tmp.data(), as, o->tcav + c[s] * dt, k[s].data(), &ka[s], nullptr, o->t + c[s] * dt);
+        rhs(o, tmp.data(), as, o->tcav + c[s] * dt, k[s].data(), ka[s], nullptr, o->t + c[s] * dt);
     }
     for (long q = 0; q < n3; q++)
         o->m[q] += dt / 6.0 * (k[0][q] + 2.0 * k[1][q] + 2.0 * k[2][q] + k[3][q]);
-    o->a += dt / 6.0 * (ka[0] + 2.0 * ka[1] + 2.0 * ka[2] + ka[3]);
+    for (int j = 0; j < OR_MAX_MODES; j++)
+        o->a[j] += dt / 6.0 * (ka[0][j] + 2.0 * ka[1][j] + 2.0 * ka[2][j] + ka[3][j]);
     normalise(o, o->m.data());
     after_accept(o, dt);
 }
@@ -545,18 +565,21 @@ static const double DP_B4[7] = {5179.0 / 57600, 0, 7571.0 / 16695, 393.0 / 640,
 static int step_dp45(oracle* o, double dt, int force, double* err_out) {
     long n3 = 3 * o->n;
     std::vector<double> k[7], tmp(n3), m5(n3), m4(n3);
-    cplx ka[7];
+    cplx ka[7][OR_MAX_MODES];
     for (int s = 0; s < 7; s++) k[s].resize(n3);
-    cplx a5 = o->a;
+    cplx a5[OR_MAX_MODES];
+    for (int j = 0; j < OR_MAX_MODES; j++) a5[j] = o->a[j];
     for (int s = 0; s < 7; s++) {
-        cplx as = o->a;
+        cplx as[OR_MAX_MODES];
+        for (int j = 0; j < OR_MAX_MODES; j++) as[j] = o->a[j];
         if (s < 6) {
             for (long q = 0; q < n3; q++) {
                 double v = o->m[q];
                 for (int j = 0; j < s; j++) v += dt * DP_A[s][j] * k[j][q];
                 tmp[q] = v;
             }
-            for (int j = 0; j < s; j++) as += dt * DP_A[s][j] * ka[j];
+            for (int j = 0; j < s; j++)
+                for (int q = 0; q < OR_MAX_MODES; q++) as[q] += dt * DP_A[s][j] * ka[j][q];
         } else {
             for (long q = 0; q < n3; q++) {
                 double v = o->m[q];
@@ -565,10 +588,11 @@ static int step_dp45(oracle* o, double dt, int force, double* err_out) {
                 tmp[q] = v;
             }
             normalise(o, tmp.data());
-            for (int j = 0; j < 6; j++) as += dt * DP_B5[j] * ka[j];
-            a5 = as;
+            for (int j = 0; j < 6; j++)
+                for (int q = 0; q < OR_MAX_MODES; q++) as[q] += dt * DP_B5[j] * ka[j][q];
+            for (int q = 0; q < OR_MAX_MODES; q++) a5[q] = as[q];
         }
-        rhs(o, tmp.data(), as, o->tcav + DP_C[s] * dt, k[s].data(), &ka[s], nullptr, o->t + DP_C[s] * dt);
+        rhs(o, tmp.data(), as, o->tcav + DP_C[s] * dt, k[s].data(), ka[s], nullptr, o->t + DP_C[s] * dt);
     }
     double err = 0;
     for (long i = 0; i < o->n; i++) {
@@ -587,7 +611,7 @@ static int step_dp45(oracle* o, double dt, int force, double* err_out) {
         std::vector<double> mn = m5;
         normalise(o, mn.data());
         o->m = mn;
-        o->a = a5;
+        for (int q = 0; q < OR_MAX_MODES; q++) o->a[q] = a5[q];
         after_accept(o, dt);
     } else {
         o->n_rej++;
@@ -641,10 +665,13 @@ oracle* or_create(int nx, int ny, int nz, double dx, double dy, double dz, doubl
     o->m.assign(3 * o->n, 0.0);
     for (long i = 0; i < o->n; i++) o->m[3 * i] = 1.0;
     o->bext[0] = o->bext[1] = o->bext[2] = 0;
-    o->cav_on = 0; o->wc = o->kappa = o->x0 = o->p0 = 0;
-    o->brms.assign(3 * o->n, 0.0);
+    for (int k = 0; k < OR_MAX_MODES; k++) {
+        o->cav_on[k] = 0; o->wc[k] = o->kappa[k] = o->x0[k] = o->p0[k] = 0;
+        o->brms[k].assign(3 * o->n, 0.0);
+        o->a[k] = 0; o->S[k] = o->C[k] = 0;
+    }
     o->cav_mode = OR_CAV_E;
-    o->a = 0; o->S = o->C = 0; o->t = o->tcav = 0;
+    o->t = o->tcav = 0;
     o->drv_on = 0; o->drv_amp = o->drv_wcut = o->drv_t0 = 0;
     o->record = 0;
     o->kind = OR_RK4; o->tol = 1e-6; o->dt_next = 0;
@@ -701,16 +728,28 @@ void or_set_m(oracle* o, const double* m) {
 void or_get_m(const oracle* o, double* m) { std::memcpy(m, o->m.data(), sizeof(double) * 3 * o->n); }
 void or_set_bias(oracle* o, const double* B) { for (int c = 0; c < 3; c++) o->bext[c] = B[c]; }
 
-// Cavity set-up (Sec. 3.2 built-ins B_rms, Wc, Kappa).  With profile_is_brms
-// the profile is B_rms in tesla.  Otherwise B_rms,i = s * profile_i with
-// s = g sqrt(2 hbar / (gamma V_c sum_i Ms_i)), the macrospin relation
-// g = B_rms sqrt(gamma Ms V / (2 hbar)) obtained by matching the linearised
-// equations of motion to the normal-phase polariton formula
-// (Eq. dickepolaritons with the Dicke mapping of Sec. 4).  A null profile
-// means a uniform unit vector along +y.
-void or_set_cavity(oracle* o, double wc, double kappa, double g, const double* profile,
-                   int profile_is_brms) {
-    o->cav_on = 1; o->wc = wc; o->kappa = kappa;
+// Every mode starts from alpha_k(0) = (x0_k - i p0_k)/2 with empty
+// accumulators at t_cav = 0 (ResetMemoryTerm, Sec. 3.2).
+static void reset_memory(oracle* o) {
+    o->tcav = 0;
+    for (int k = 0; k < OR_MAX_MODES; k++) {
+        o->S[k] = o->C[k] = 0;
+        o->a[k] = cplx(0.5 * o->x0[k], -0.5 * o->p0[k]);
+    }
+}
+
+// Cavity mode k set-up (Sec. 3.2 built-ins B_rms, Wc, Kappa; mode 0 is the
+// paper's single mode).  With profile_is_brms the profile is B_rms in tesla.
+// Otherwise B_rms,i = s * profile_i with s = g sqrt(2 hbar / (gamma V_c sum_i Ms_i)),
+// the macrospin relation g = B_rms sqrt(gamma Ms V / (2 hbar)) obtained by
+// matching the linearised equations of motion to the normal-phase polariton
+// formula (Eq. dickepolaritons with the Dicke mapping of Sec. 4).  A null
+// profile means a uniform unit vector along +y.  Configuring a mode restarts
+// the cavity memory of every mode.
+void or_set_cavity_mode(oracle* o, int k, double wc, double kappa, double g, const double* profile,
+                        int profile_is_brms) {
+    if (k < 0 || k >= OR_MAX_MODES) return;
+    o->cav_on[k] = 1; o->wc[k] = wc; o->kappa[k] = kappa;
     double s = 1.0;
     if (!profile_is_brms) {
         double sm = 0;
@@ -720,23 +759,28 @@ void or_set_cavity(oracle* o, double wc, double kappa, double g, const double* p
     for (long i = 0; i < o->n; i++)
         for (int c = 0; c < 3; c++) {
             double p = profile ? profile[3 * i + c] : (c == 1 ? 1.0 : 0.0);
-            o->brms[3 * i + c] = s * p;
+            o->brms[k][3 * i + c] = s * p;
         }
-    o->tcav = 0; o->S = o->C = 0;
-    o->a = cplx(0.5 * o->x0, -0.5 * o->p0);
+    reset_memory(o);
 }
-void or_get_brms(const oracle* o, double* out) { std::memcpy(out, o->brms.data(), sizeof(double) * 3 * o->n); }
+void or_set_cavity(oracle* o, double wc, double kappa, double g, const double* profile, int profile_is_brms) {
+    or_set_cavity_mode(o, 0, wc, kappa, g, profile, profile_is_brms);
+}
+void or_get_brms_mode(const oracle* o, int k, double* out) {
+    std::memcpy(out, o->brms[k].data(), sizeof(double) * 3 * o->n);
+}
+void or_get_brms(const oracle* o, double* out) { or_get_brms_mode(o, 0, out); }
 // x0 = 2 Re alpha0, p0 = -2 Im alpha0 (Sec. 3.2 built-ins X0, P0).
-void or_set_cavity_init(oracle* o, double x0, double p0) {
-    o->x0 = x0; o->p0 = p0;
-    o->a = cplx(0.5 * x0, -0.5 * p0);
+void or_set_cavity_init_mode(oracle* o, int k, double x0, double p0) {
+    o->x0[k] = x0; o->p0[k] = p0;
+    o->a[k] = cplx(0.5 * x0, -0.5 * p0);
 }
+void or_set_cavity_init(oracle* o, double x0, double p0) { or_set_cavity_init_mode(o, 0, x0, p0); }
 // ResetMemoryTerm(): the current state becomes the cavity's t = 0.
-void or_reset_cavity(oracle* o) {
-    o->tcav = 0; o->S = o->C = 0;
-    o->a = cplx(0.5 * o->x0, -0.5 * o->p0);
+void or_reset_cavity(oracle* o) { reset_memory(o); }
+void or_disable_cavity(oracle* o) {
+    for (int k = 0; k < OR_MAX_MODES; k++) o->cav_on[k] = 0;
 }
-void or_disable_cavity(oracle* o) { o->cav_on = 0; }
 void or_set_integrator(oracle* o, int kind, double tol, int mode) {
     o->kind = kind; o->tol = tol; o->cav_mode = mode;
 }
@@ -777,32 +821,40 @@ long or_dt_history(const oracle* o, double* out, long max) {
 }
 
 // out = {t, t_cav, Re alpha, Im alpha, |alpha|^2, Gamma, S, C, X, dt_next,
-//        n_accepted, n_rejected}.  In P-mode alpha is reconstructed from the
-// accumulators: alpha(t) = e^{-(kappa + i omega_c) t}[alpha0 - S/hbar + i C/hbar]
+//        n_accepted, n_rejected} of mode k.  In P-mode alpha is reconstructed
+// from the accumulators: alpha(t) = e^{-(kappa + i omega_c) t}[alpha0 - S/hbar + i C/hbar]
 // (Sec. 2.2, a-posteriori photon amplitude).
-void or_get_cavity(const oracle* o, double* out) {
-    double X = o->cav_on ? cavity_X(o, o->m.data()) : 0.0;
-    cplx a = o->a;
+void or_get_cavity_mode(const oracle* o, int k, double* out) {
+    double X = o->cav_on[k] ? cavity_X(o, o->m.data(), k) : 0.0;
+    cplx a = o->a[k];
     double G = 2.0 * a.real();
-    if (o->cav_on && o->cav_mode == OR_CAV_P) {
-        cplx a0(0.5 * o->x0, -0.5 * o->p0);
-        a = std::exp(-cplx(o->kappa, o->wc) * o->tcav) * (a0 + cplx(-o->S / o->hbar, o->C / o->hbar));
-        G = gamma_P(o, o->tcav);
+    if (o->cav_on[k] && o->cav_mode == OR_CAV_P) {
+        cplx a0(0.5 * o->x0[k], -0.5 * o->p0[k]);
+        a = std::exp(-cplx(o->kappa[k], o->wc[k]) * o->tcav) * (a0 + cplx(-o->S[k] / o->hbar, o->C[k] / o->hbar));
+        G = gamma_P(o, k, o->tcav);
     }
-    out[6] = o->S; out[7] = o->C;
+    out[6] = o->S[k]; out[7] = o->C[k];
     out[0] = o->t; out[1] = o->tcav; out[2] = a.real(); out[3] = a.imag(); out[4] = std::norm(a);
-    out[5] = o->cav_on ? G : 0.0; out[8] = X; out[9] = o->dt_next;
+    out[5] = o->cav_on[k] ? G : 0.0; out[8] = X; out[9] = o->dt_next;
     out[10] = (double)o->n_acc; out[11] = (double)o->n_rej;
 }
+void or_get_cavity(const oracle* o, double* out) { or_get_cavity_mode(o, 0, out); }
 
-void or_set_alpha(oracle* o, double re, double im) { o->a = cplx(re, im); }
+void or_set_alpha(oracle* o, double re, double im) { o->a[0] = cplx(re, im); }
+void or_set_alpha_mode(oracle* o, int k, double re, double im) { o->a[k] = cplx(re, im); }
 
 // ---- single evaluations for pins and sampled parity --------------------------
 void or_demag(const oracle* o, const double* m, double* B) { demag_field(o, m, B); }
 void or_exchange(const oracle* o, const double* m, double* B) { exchange_field(o, m, B); }
 void or_anis(const oracle* o, const double* m, double* B) { anis_field(o, m, B); }
-// Total field at the current simulation time (the drive, if on, at o->t).
+// Total field at the current simulation time (the drive, if on, at o->t),
+// with Gamma for mode 0 and no field from the other modes.
 void or_field(const oracle* o, const double* m, double Gamma, double* B) {
+    double G[OR_MAX_MODES] = {Gamma, 0, 0, 0};
+    total_field(o, m, G, B, drive_factor(o, o->t));
+}
+// Same with one Gamma per mode.
+void or_field_modes(const oracle* o, const double* m, const double* Gamma, double* B) {
     total_field(o, m, Gamma, B, drive_factor(o, o->t));
 }
 
@@ -852,11 +904,20 @@ void or_spectrum(const double* t, const double* y, long n, const double* w, long
 }
 void or_rhs(const oracle* o, const double* m, double are, double aim, double tc, double* dm,
             double* da) {
-    cplx d;
-    rhs(o, m, cplx(are, aim), tc, dm, &d, nullptr);
-    da[0] = d.real(); da[1] = d.imag();
+    cplx a[OR_MAX_MODES] = {cplx(are, aim), 0, 0, 0}, d[OR_MAX_MODES];
+    rhs(o, m, a, tc, dm, d, nullptr);
+    da[0] = d[0].real(); da[1] = d[0].imag();
 }
-double or_cavity_X(const oracle* o, const double* m) { return cavity_X(o, m); }
+// Right-hand side with every mode's amplitude: a, da = OR_MAX_MODES (re, im) pairs.
+void or_rhs_modes(const oracle* o, const double* m, const double* a, double tc, double* dm, double* da) {
+    cplx aa[OR_MAX_MODES], d[OR_MAX_MODES];
+    for (int k = 0; k < OR_MAX_MODES; k++) aa[k] = cplx(a[2 * k], a[2 * k + 1]);
+    rhs(o, m, aa, tc, dm, d, nullptr);
+    for (int k = 0; k < OR_MAX_MODES; k++) { da[2 * k] = d[k].real(); da[2 * k + 1] = d[k].imag(); }
+}
+double or_cavity_X(const oracle* o, const double* m) { return cavity_X(o, m, 0); }
+double or_cavity_X_mode(const oracle* o, const double* m, int k) { return cavity_X(o, m, k); }
+int or_max_modes(void) { return OR_MAX_MODES; }
 
 // Demag field at a list of cells by the direct sum, with the tensor evaluated
 // on the fly (no table): usable on grids far too large for the O(N^2) table.
@@ -884,8 +945,9 @@ void or_demag_at(const oracle* o, const double* m, const long* cells, long nc, d
 }
 
 // Energy terms (J): {Zeeman, demag, exchange, anisotropy, cavity coupling,
-// photon, total}.  The cavity pair is -X * 2Re(alpha) and hbar omega_c |alpha|^2,
-// from the Hamiltonian Eq. (startH) with S = -Ms m V_c / gamma.
+// photon, total}.  The cavity pair is -X_k * 2Re(alpha_k) and
+// hbar omega_c,k |alpha_k|^2 summed over the modes, from the Hamiltonian
+// Eq. (startH) with S = -Ms m V_c / gamma.
 void or_energy(const oracle* o, double* out) {
     long n = o->n;
     std::vector<double> Bd(3 * n), Bx(3 * n);
@@ -904,10 +966,11 @@ void or_energy(const oracle* o, double* out) {
         }
     }
     double ec = 0, ep = 0;
-    if (o->cav_on) {
-        double X = cavity_X(o, o->m.data());
-        ec = -X * 2.0 * o->a.real();
-        ep = o->hbar * o->wc * std::norm(o->a);
+    for (int k = 0; k < OR_MAX_MODES; k++) {
+        if (!o->cav_on[k]) continue;
+        double X = cavity_X(o, o->m.data(), k);
+        ec -= X * 2.0 * o->a[k].real();
+        ep += o->hbar * o->wc[k] * std::norm(o->a[k]);
     }
     out[0] = ez; out[1] = ed; out[2] = ex; out[3] = ea; out[4] = ec; out[5] = ep;
     out[6] = ez + ed + ex + ea + ec + ep;
