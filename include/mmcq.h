@@ -155,10 +155,21 @@ int mmcq_get_m(mmcq_t* h, int inst, float* out, int where);
  * (CavityFeatureStatus = 1 in the paper's terms). */
 int mmcq_set_cavity(mmcq_t* h, int inst, double omega_c, double kappa, double g, const float* profile,
                     int profile_is_brms);
+/* Cavity mode `mode` (0 .. 3) of one instance or all: the same arguments as
+ * mmcq_set_cavity, which sets mode 0.  Every enabled mode k adds
+ * B_rms,k Gamma_k to the field and follows its own amplitude equation driven
+ * by X_k = V_c sum_i Ms_i m_i . B_rms,k,i (the paper keeps one mode and notes
+ * that more modes follow the same equations, Sec. 4).  Each mode has its own
+ * profile map, shared by the instances.  Configuring any mode restarts the
+ * cavity memory of every mode of the selected instances (t_cav = 0,
+ * S = C = 0, alpha_k = alpha_k(0)).  MMCQ_ERR_ARG for a mode outside 0..3. */
+int mmcq_set_cavity_mode(mmcq_t* h, int inst, int mode, double omega_c, double kappa, double g,
+                         const float* profile, int profile_is_brms);
 /* x0 = 2 Re alpha0, p0 = -2 Im alpha0 (Sec. 3.2 built-ins X0, P0; the paper's
  * wording after Eq. gammadiscretefinal is read with alpha0). Resets alpha. */
 int mmcq_set_cavity_init(mmcq_t* h, int inst, double x0, double p0);
-/* ResetMemoryTerm() (Sec. 3.2): t_cav := 0, S = C = 0, alpha := alpha0. */
+int mmcq_set_cavity_init_mode(mmcq_t* h, int inst, int mode, double x0, double p0);
+/* ResetMemoryTerm() (Sec. 3.2): t_cav := 0, S = C = 0, alpha := alpha0, every mode. */
 int mmcq_reset_cavity(mmcq_t* h, int inst);
 int mmcq_disable_cavity(mmcq_t* h, int inst);
 
@@ -187,6 +198,8 @@ int mmcq_sync(mmcq_t* h);
  * in P-mode alpha is rebuilt from S and C).  inst = -1 fills out[0..batch-1]
  * for every instance in one call; otherwise out is one struct. */
 int mmcq_get_cavity(mmcq_t* h, int inst, mmcq_cavity* out);
+/* The same read-out for cavity mode `mode` (mmcq_get_cavity reads mode 0). */
+int mmcq_get_cavity_mode(mmcq_t* h, int inst, int mode, mmcq_cavity* out);
 
 /* Accepted step lengths of one instance in order (at most max are copied;
  * *n receives the total count).  Used to replay adaptive runs. */

@@ -83,6 +83,10 @@ PROTOTYPES = {
     "mmcq_set_cavity": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, _FP,
                                        ctypes.c_int]),
     "mmcq_set_cavity_init": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
+    "mmcq_set_cavity_mode": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_double, _FP, ctypes.c_int]),
+    "mmcq_set_cavity_init_mode": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
+    "mmcq_get_cavity_mode": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, ctypes.POINTER(mmcq_cavity)]),
     "mmcq_reset_cavity": (ctypes.c_int, [_H, ctypes.c_int]),
     "mmcq_disable_cavity": (ctypes.c_int, [_H, ctypes.c_int]),
     "mmcq_set_integrator": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_double, ctypes.c_int]),
@@ -258,6 +262,9 @@ class Sim:
         return out
 
     def set_cavity(self, omega_c, kappa, g=0.0, profile=None, profile_is_brms=False, inst=-1):
+        self.set_cavity_mode(0, omega_c, kappa, g, profile, profile_is_brms, inst)
+
+    def set_cavity_mode(self, mode, omega_c, kappa, g=0.0, profile=None, profile_is_brms=False, inst=-1):
         keep = None
         p = None
         if profile is not None:
@@ -265,10 +272,14 @@ class Sim:
             if keep.size != 3 * self.n:
                 raise ValueError("profile must have N x 3 values")
             p = ctypes.c_void_p(keep.ctypes.data)
-        self._ck(self._lib.mmcq_set_cavity(self._h, inst, omega_c, kappa, g, p, int(bool(profile_is_brms))))
+        self._ck(self._lib.mmcq_set_cavity_mode(self._h, inst, int(mode), omega_c, kappa, g, p,
+                                                int(bool(profile_is_brms))))
 
     def set_cavity_init(self, x0, p0, inst=-1):
         self._ck(self._lib.mmcq_set_cavity_init(self._h, inst, x0, p0))
+
+    def set_cavity_init_mode(self, mode, x0, p0, inst=-1):
+        self._ck(self._lib.mmcq_set_cavity_init_mode(self._h, inst, int(mode), x0, p0))
 
     def reset_cavity(self, inst=-1):
         self._ck(self._lib.mmcq_reset_cavity(self._h, inst))
@@ -288,11 +299,11 @@ class Sim:
     def sync(self):
         self._ck(self._lib.mmcq_sync(self._h))
 
-    def cavity(self, inst=0):
+    def cavity(self, inst=0, mode=0):
         """Read-out of one instance (dict), or of all instances (list of dicts) for inst = -1."""
         n = self.batch if inst == -1 else 1
         c = (mmcq_cavity * n)()
-        self._ck(self._lib.mmcq_get_cavity(self._h, inst, c))
+        self._ck(self._lib.mmcq_get_cavity_mode(self._h, inst, int(mode), c))
         res = [{k: getattr(c[i], k) for k, _ in mmcq_cavity._fields_} for i in range(n)]
         return res if inst == -1 else res[0]
 

@@ -28,7 +28,7 @@ cudaError_t launch_set_m(float4*, const float*, const float*, long long, int, in
 cudaError_t launch_get_m(const float4*, float*, long long, cudaStream_t);
 cudaError_t launch_apply_ms(float4*, const float*, long long, int, cudaStream_t);
 cudaError_t launch_get_field(const float4*, float*, long long, cudaStream_t);
-cudaError_t launch_coupling_sum(const Buffers&, long long, double, int, int, double*, cudaStream_t);
+cudaError_t launch_coupling_sum(const Buffers&, long long, double, int, int, int, double*, cudaStream_t);
 cudaError_t launch_set_dt(InstState*, int, double, cudaStream_t);
 cudaError_t launch_spectrum(const double*, long long, int, const double*, int, double*, cudaStream_t);
 cudaError_t build_demag_kernel(const Plan&, double, double, double, double, float*, double2*, cudaStream_t);
@@ -51,8 +51,9 @@ struct mmcq {
     double tol = 1e-6;
     int mode = CAV_E;
     std::vector<InstParams> ip;
-    std::vector<double> g;          // coupling strength per instance (profile_is_brms = 0)
-    std::vector<int> g_mode;        // 1: scale from g, 0: profile is B_rms
+    std::vector<double> g;          // [B][MAX_MODES] coupling strength (profile_is_brms = 0)
+    std::vector<int> g_mode;        // [B][MAX_MODES] 1: scale from g, 0: profile is B_rms
+    int nmodes = 1;                 // cavity modes in use: highest configured mode + 1
     std::vector<float> ms_host;
     float* ms_dev = nullptr;
     float* stage3 = nullptr;
@@ -148,16 +149,37 @@ void refresh_scales(mmcq_t* h) {
     long long nmag = 0;
     for (float v : h->ms_host) nmag += v > 0;
     for (int b = 0; b < h->P.B; b++) {
-        if (h->g_mode[b])
-            h->ip[b].brms_scale = sm > 0 ? h->g[b] * std::sqrt(2.0 * h->hbar / (h->gamma * h->mat.vc * sm)) : 0.0;
+        for (int k = 0; k < MAX_MODES; k++)
+            if (h->g_mode[b * MAX_MODES + k])
+                h->ip[b].brms_scale[k] =
+                    sm > 0 ? h->g[b * MAX_MODES + k] * std::sqrt(2.0 * h->hbar / (h->gamma * h->mat.vc * sm)) : 0.0;
         h->ip[b].inv_nmag = nmag > 0 ? 1.0 / (double)nmag : 0.0;
     }
 }
 
-void reset_alpha(const InstParams& ip, InstState& s) {
-    s.a_re = s.as_re = 0.5 * ip.x0;
-    s.a_im = s.as_im = -0.5 * ip.p0;
+// Every mode back to alpha_k(0) = (x0_k - i p0_k)/2 with empty accumulators at
+// t_cav = 0 (ResetMemoryTerm).
+void reset_memory(const InstParams& ip, InstState& s) {
+    s.tcav = 0;
+    for (int k = 0; k < MAX_MODES; k++) {
+        s.S[k] = s.C[k] = 0;
+        s.a_re[k] = s.as_re[k] = 0.5 * ip.x0[k];
+        s.a_im[k] = s.as_im[k] = -0.5 * ip.p0[k];
+    }
     s.have_k1 = 0;
+}
+
+StageArgs step_args(const mmcq_t* h) {
+    StageArgs A{};
+    A.kind = h->kind;
+    A.mode = h->mode;
+    A.terms = MMCQ_TERM_ALL;
+    A.field_only = 0;
+    A.inst0 = 0;
+    A.tol = (float)h->tol;
+    A.record = h->record;
+    A.nmodes = h->nmodes;
+    return A;
 }
 
 // Algorithmic (compulsory) bytes of one launch of class cls for nb instances.
@@ -189,7 +211,8 @@ double launch_bytes(const mmcq_t* h, int cls, const StageArgs& A, int nb) {
             else if (A.kind == KIND_RK4 && s == 3) cells += 16.0 * 5;  // m0, k1..k3 in, m out
             else if (A.kind == KIND_DP45 && s == 6) cells += 32.0;     // e6 in, k out
             else cells += 16.0;                          // k out
-            if (h->Bf.prof) cells += 16.0;
+            for (int k = 0; k < h->nmodes; k++)
+                if (h->Bf.prof[k]) cells += 16.0;
             per = spec + N * cells;
             break;
         }
@@ -246,14 +269,7 @@ int check_flags(mmcq_t* h) {
 
 // n steps (RK4) or attempts (DP45) of every instance, enqueued on h->stream.
 int enqueue_steps(mmcq_t* h, int64_t n) {
-    StageArgs A{};
-    A.kind = h->kind;
-    A.mode = h->mode;
-    A.terms = MMCQ_TERM_ALL;
-    A.field_only = 0;
-    A.inst0 = 0;
-    A.tol = (float)h->tol;
-    A.record = h->record;
+    StageArgs A = step_args(h);
     const int B = h->P.B;
     for (int64_t it = 0; it < n; it++) {
         if (h->kind == KIND_RK4) {
@@ -361,10 +377,10 @@ int mmcq_create(mmcq_t** out, const mmcq_grid* g, double Ms, double Aex, double 
     Bf.spec = (float2*)A(sizeof(float2) * spec_n);
     if (P.nz > 1) Bf.spec2 = (float2*)A(sizeof(float2) * (long long)P.B * P.nz * P.NT * P.py * 3 * P.TX);
     Bf.kern = (float*)A(sizeof(float) * 6LL * P.hzk * P.hyk * P.NT * P.TX);
-    Bf.prof = nullptr;
+    for (int k = 0; k < MAX_MODES; k++) Bf.prof[k] = nullptr;
     Bf.ip = (InstParams*)A(sizeof(InstParams) * P.B);
     Bf.st = (InstState*)A(sizeof(InstState) * P.B);
-    Bf.xpart = (double*)A(sizeof(double) * (long long)P.B * P.nblk);
+    Bf.xpart = (double*)A(sizeof(double) * MAX_MODES * (long long)P.B * P.nblk);
     Bf.mpart = (double*)A(sizeof(double) * 3LL * P.B * P.nblk);
     Bf.mhist = nullptr;   // allocated by mmcq_set_recording
     Bf.epart = (float*)A(sizeof(float) * (long long)P.B * P.nblk);
@@ -405,8 +421,8 @@ int mmcq_create(mmcq_t** out, const mmcq_grid* g, double Ms, double Aex, double 
     // initial state
     h->ms_host.assign(P.N, (float)Ms);
     h->ip.assign(P.B, InstParams{});
-    h->g.assign(P.B, 0.0);
-    h->g_mode.assign(P.B, 0);
+    h->g.assign((size_t)P.B * MAX_MODES, 0.0);
+    h->g_mode.assign((size_t)P.B * MAX_MODES, 0);
     refresh_scales(h);
     std::vector<InstState> st(P.B);
     for (auto& s : st) {
@@ -516,63 +532,75 @@ int mmcq_get_m(mmcq_t* h, int inst, float* out, int where) {
     return r;
 }
 
-int mmcq_set_cavity(mmcq_t* h, int inst, double omega_c, double kappa, double g, const float* profile,
-                    int profile_is_brms) {
-    if (!h || !valid_inst(h, inst, true) || !std::isfinite(omega_c) || !std::isfinite(kappa) || !std::isfinite(g))
+int mmcq_set_cavity_mode(mmcq_t* h, int inst, int mode, double omega_c, double kappa, double g,
+                         const float* profile, int profile_is_brms) {
+    if (!h || !valid_inst(h, inst, true) || mode < 0 || mode >= MAX_MODES || !std::isfinite(omega_c) ||
+        !std::isfinite(kappa) || !std::isfinite(g))
         return MMCQ_ERR_ARG;
     const long long N = h->P.N;
     if (profile) {
-        if (!h->Bf.prof) {
-            h->Bf.prof = (float4*)dev_alloc(h, sizeof(float4) * N);
-            if (!h->Bf.prof) return fail(h, MMCQ_ERR_CUDA, "profile allocation failed");
+        if (!h->Bf.prof[mode]) {
+            h->Bf.prof[mode] = (float4*)dev_alloc(h, sizeof(float4) * N);
+            if (!h->Bf.prof[mode]) return fail(h, MMCQ_ERR_CUDA, "profile allocation failed");
         }
         std::vector<float4> p(N);
         for (long long i = 0; i < N; i++) p[i] = make_float4(profile[3 * i], profile[3 * i + 1], profile[3 * i + 2], 0.f);
         CK(h, cudaStreamSynchronize(h->stream));
-        CK(h, cudaMemcpy(h->Bf.prof, p.data(), sizeof(float4) * N, cudaMemcpyHostToDevice));
+        CK(h, cudaMemcpy(h->Bf.prof[mode], p.data(), sizeof(float4) * N, cudaMemcpyHostToDevice));
     }
     for (int b = 0; b < h->P.B; b++) {
         if (inst >= 0 && b != inst) continue;
-        h->ip[b].wc = omega_c;
-        h->ip[b].kappa = kappa;
-        h->ip[b].cav_on = 1;
-        h->g[b] = g;
-        h->g_mode[b] = profile_is_brms ? 0 : 1;
-        if (profile_is_brms) h->ip[b].brms_scale = 1.0;
+        h->ip[b].wc[mode] = omega_c;
+        h->ip[b].kappa[mode] = kappa;
+        h->ip[b].cav_on[mode] = 1;
+        h->g[b * MAX_MODES + mode] = g;
+        h->g_mode[b * MAX_MODES + mode] = profile_is_brms ? 0 : 1;
+        if (profile_is_brms) h->ip[b].brms_scale[mode] = 1.0;
     }
+    if (mode + 1 > h->nmodes) h->nmodes = mode + 1;
     refresh_scales(h);
     int r = upload_params(h);
     if (r) return r;
     std::vector<InstParams> ip = h->ip;
+    return edit_state(h, inst, [&](InstState& s, int b) { reset_memory(ip[b], s); });
+}
+
+int mmcq_set_cavity(mmcq_t* h, int inst, double omega_c, double kappa, double g, const float* profile,
+                    int profile_is_brms) {
+    return mmcq_set_cavity_mode(h, inst, 0, omega_c, kappa, g, profile, profile_is_brms);
+}
+
+int mmcq_set_cavity_init_mode(mmcq_t* h, int inst, int mode, double x0, double p0) {
+    if (!h || !valid_inst(h, inst, true) || mode < 0 || mode >= MAX_MODES || !std::isfinite(x0) ||
+        !std::isfinite(p0))
+        return MMCQ_ERR_ARG;
+    for (int b = 0; b < h->P.B; b++)
+        if (inst < 0 || b == inst) { h->ip[b].x0[mode] = x0; h->ip[b].p0[mode] = p0; }
+    int r = upload_params(h);
+    if (r) return r;
+    std::vector<InstParams> ip = h->ip;
     return edit_state(h, inst, [&](InstState& s, int b) {
-        s.tcav = 0; s.S = 0; s.C = 0;
-        reset_alpha(ip[b], s);
+        s.a_re[mode] = s.as_re[mode] = 0.5 * ip[b].x0[mode];
+        s.a_im[mode] = s.as_im[mode] = -0.5 * ip[b].p0[mode];
+        s.have_k1 = 0;
     });
 }
 
 int mmcq_set_cavity_init(mmcq_t* h, int inst, double x0, double p0) {
-    if (!h || !valid_inst(h, inst, true) || !std::isfinite(x0) || !std::isfinite(p0)) return MMCQ_ERR_ARG;
-    for (int b = 0; b < h->P.B; b++)
-        if (inst < 0 || b == inst) { h->ip[b].x0 = x0; h->ip[b].p0 = p0; }
-    int r = upload_params(h);
-    if (r) return r;
-    std::vector<InstParams> ip = h->ip;
-    return edit_state(h, inst, [&](InstState& s, int b) { reset_alpha(ip[b], s); });
+    return mmcq_set_cavity_init_mode(h, inst, 0, x0, p0);
 }
 
 int mmcq_reset_cavity(mmcq_t* h, int inst) {
     if (!h || !valid_inst(h, inst, true)) return MMCQ_ERR_ARG;
     std::vector<InstParams> ip = h->ip;
-    return edit_state(h, inst, [&](InstState& s, int b) {
-        s.tcav = 0; s.S = 0; s.C = 0;
-        reset_alpha(ip[b], s);
-    });
+    return edit_state(h, inst, [&](InstState& s, int b) { reset_memory(ip[b], s); });
 }
 
 int mmcq_disable_cavity(mmcq_t* h, int inst) {
     if (!h || !valid_inst(h, inst, true)) return MMCQ_ERR_ARG;
     for (int b = 0; b < h->P.B; b++)
-        if (inst < 0 || b == inst) h->ip[b].cav_on = 0;
+        if (inst < 0 || b == inst)
+            for (int k = 0; k < MAX_MODES; k++) h->ip[b].cav_on[k] = 0;
     int r = upload_params(h);
     if (r) return r;
     return edit_state(h, inst, [](InstState& s, int) { s.have_k1 = 0; });
@@ -599,8 +627,10 @@ int mmcq_set_integrator(mmcq_t* h, int kind, double tol, int cavity_mode) {
         s.mcur = 0;
         s.have_k1 = 0;
         s.k1slot = 0;
-        s.as_re = s.a_re;
-        s.as_im = s.a_im;
+        for (int k = 0; k < MAX_MODES; k++) {
+            s.as_re[k] = s.a_re[k];
+            s.as_im[k] = s.a_im[k];
+        }
     });
 }
 
@@ -626,28 +656,29 @@ int mmcq_sync(mmcq_t* h) {
     return check_flags(h);
 }
 
-int mmcq_get_cavity(mmcq_t* h, int inst, mmcq_cavity* out) {
-    if (!h || !out || !valid_inst(h, inst, true)) return MMCQ_ERR_ARG;
+int mmcq_get_cavity_mode(mmcq_t* h, int inst, int mode, mmcq_cavity* out) {
+    if (!h || !out || !valid_inst(h, inst, true) || mode < 0 || mode >= MAX_MODES) return MMCQ_ERR_ARG;
     int r = check_flags(h);
     const int b0 = inst < 0 ? 0 : inst, nb = inst < 0 ? h->P.B : 1;
+    const int k = mode;
     std::vector<InstState> st(nb);
     std::vector<double> X(nb, 0.0);
     CK(h, cudaMemcpy(st.data(), h->Bf.st + b0, sizeof(InstState) * nb, cudaMemcpyDeviceToHost));
-    CK(h, launch_coupling_sum(h->Bf, h->P.N, h->mat.vc, b0, nb, h->dscratch, h->stream));
+    CK(h, launch_coupling_sum(h->Bf, h->P.N, h->mat.vc, b0, nb, k, h->dscratch, h->stream));
     CK(h, cudaMemcpyAsync(X.data(), h->dscratch, sizeof(double) * nb, cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     for (int q = 0; q < nb; q++) {
         const InstState& s = st[q];
         const InstParams& ip = h->ip[b0 + q];
-        std::complex<double> a(s.a_re, s.a_im);
-        double G = ip.cav_on ? 2.0 * s.a_re : 0.0;
-        if (ip.cav_on && h->mode == CAV_P) {
-            std::complex<double> a0(0.5 * ip.x0, -0.5 * ip.p0);
-            a = std::exp(-std::complex<double>(ip.kappa, ip.wc) * s.tcav) *
-                (a0 + std::complex<double>(-s.S / h->hbar, s.C / h->hbar));
-            double e = std::exp(-ip.kappa * s.tcav);
-            G = e * std::cos(ip.wc * s.tcav) * (ip.x0 - 2.0 * s.S / h->hbar) -
-                e * std::sin(ip.wc * s.tcav) * (ip.p0 - 2.0 * s.C / h->hbar);
+        std::complex<double> a(s.a_re[k], s.a_im[k]);
+        double G = ip.cav_on[k] ? 2.0 * s.a_re[k] : 0.0;
+        if (ip.cav_on[k] && h->mode == CAV_P) {
+            std::complex<double> a0(0.5 * ip.x0[k], -0.5 * ip.p0[k]);
+            a = std::exp(-std::complex<double>(ip.kappa[k], ip.wc[k]) * s.tcav) *
+                (a0 + std::complex<double>(-s.S[k] / h->hbar, s.C[k] / h->hbar));
+            double e = std::exp(-ip.kappa[k] * s.tcav);
+            G = e * std::cos(ip.wc[k] * s.tcav) * (ip.x0[k] - 2.0 * s.S[k] / h->hbar) -
+                e * std::sin(ip.wc[k] * s.tcav) * (ip.p0[k] - 2.0 * s.C[k] / h->hbar);
         }
         mmcq_cavity& o = out[q];
         o.t = s.t;
@@ -656,8 +687,8 @@ int mmcq_get_cavity(mmcq_t* h, int inst, mmcq_cavity* out) {
         o.im_alpha = a.imag();
         o.n_photon = std::norm(a);
         o.Gamma = G;
-        o.S = s.S;
-        o.C = s.C;
+        o.S = s.S[k];
+        o.C = s.C[k];
         o.X = X[q];
         o.dt = s.dt;
         o.accepted = s.nacc;
@@ -665,6 +696,8 @@ int mmcq_get_cavity(mmcq_t* h, int inst, mmcq_cavity* out) {
     }
     return r;
 }
+
+int mmcq_get_cavity(mmcq_t* h, int inst, mmcq_cavity* out) { return mmcq_get_cavity_mode(h, inst, 0, out); }
 
 int mmcq_get_dt_history(mmcq_t* h, int inst, double* out, int64_t max, int64_t* n) {
     if (!h || !valid_inst(h, inst, false) || max < 0 || (max > 0 && !out)) return MMCQ_ERR_ARG;
@@ -684,9 +717,8 @@ int mmcq_eval_field(mmcq_t* h, int inst, int terms, float* out, int where) {
     if (!h || !out || !valid_inst(h, inst, false) || (where != MMCQ_HOST && where != MMCQ_DEVICE) ||
         terms < 0 || terms > MMCQ_TERM_ALL)
         return MMCQ_ERR_ARG;
-    StageArgs A{};
-    A.kind = h->kind; A.mode = h->mode; A.terms = terms; A.field_only = 1; A.inst0 = inst; A.stage = 0;
-    A.tol = (float)h->tol;
+    StageArgs A = step_args(h);
+    A.terms = terms; A.field_only = 1; A.inst0 = inst; A.stage = 0; A.record = 0;
     int r = run_stage(h, A, 1);
     if (r) return r;
     const long long N = h->P.N;
@@ -803,9 +835,9 @@ int mmcq_spectrum(mmcq_t* h, int inst, int comp, const double* omega, int nw, do
 }
 
 // ---- checkpoint / resume ---------------------------------------------------
-// Snapshot: SnapHeader, then per instance (B of each, in this order)
-// InstState, InstParams, g (double), g_mode (int32), then m of every instance
-// (B x N float4) and the kept first DP45 stage (B x N float4).
+// Snapshot: SnapHeader, then B InstState, B InstParams, B x MAX_MODES g
+// (double), B x MAX_MODES g_mode (int32), then m of every instance (B x N
+// float4) and the kept first DP45 stage (B x N float4).
 namespace {
 struct SnapHeader {
     char magic[8];
@@ -817,7 +849,7 @@ const char SNAP_MAGIC[8] = {'M', 'M', 'C', 'Q', 'S', 'N', 'A', 'P'};
 
 int64_t snap_size(const mmcq_t* h) {
     const int64_t B = h->P.B;
-    return (int64_t)sizeof(SnapHeader) + B * (int64_t)(sizeof(InstState) + sizeof(InstParams) + 8 + 4) +
+    return (int64_t)sizeof(SnapHeader) + B * (int64_t)(sizeof(InstState) + sizeof(InstParams) + 12 * MAX_MODES) +
            2 * B * h->P.N * (int64_t)sizeof(float4);
 }
 }  // namespace
@@ -836,15 +868,15 @@ int mmcq_get_state(mmcq_t* h, void* buf, int64_t cap, int64_t* size) {
     char* p = static_cast<char*>(buf);
     SnapHeader hd{};
     std::memcpy(hd.magic, SNAP_MAGIC, 8);
-    hd.version = 1;
+    hd.version = 2;
     hd.nx = h->P.nx; hd.ny = h->P.ny; hd.nz = h->P.nz; hd.B = B;
     hd.kind = h->kind; hd.mode = h->mode; hd.tol = h->tol;
     hd.N = N; hd.st_bytes = sizeof(InstState); hd.ip_bytes = sizeof(InstParams);
     std::memcpy(p, &hd, sizeof(hd)); p += sizeof(hd);
     std::memcpy(p, st.data(), sizeof(InstState) * B); p += sizeof(InstState) * B;
     std::memcpy(p, h->ip.data(), sizeof(InstParams) * B); p += sizeof(InstParams) * B;
-    std::memcpy(p, h->g.data(), sizeof(double) * B); p += sizeof(double) * B;
-    for (int b = 0; b < B; b++) { int32_t v = h->g_mode[b]; std::memcpy(p, &v, 4); p += 4; }
+    std::memcpy(p, h->g.data(), sizeof(double) * B * MAX_MODES); p += sizeof(double) * B * MAX_MODES;
+    for (int q = 0; q < B * MAX_MODES; q++) { int32_t v = h->g_mode[q]; std::memcpy(p, &v, 4); p += 4; }
     const size_t row = sizeof(float4) * N;
     for (int b = 0; b < B; b++, p += row)
         CK(h, cudaMemcpy(p, h->Bf.m[st[b].mcur] + (long long)b * N, row, cudaMemcpyDeviceToHost));
@@ -860,7 +892,7 @@ int mmcq_set_state(mmcq_t* h, const void* buf, int64_t size) {
     std::memcpy(&hd, p, sizeof(hd)); p += sizeof(hd);
     const int B = h->P.B;
     const long long N = h->P.N;
-    if (std::memcmp(hd.magic, SNAP_MAGIC, 8) != 0 || hd.version != 1)
+    if (std::memcmp(hd.magic, SNAP_MAGIC, 8) != 0 || hd.version != 2)
         return fail(h, MMCQ_ERR_ARG, "not an mmcq snapshot");
     if (hd.nx != h->P.nx || hd.ny != h->P.ny || hd.nz != h->P.nz || hd.B != B || hd.N != N ||
         hd.st_bytes != (int64_t)sizeof(InstState) || hd.ip_bytes != (int64_t)sizeof(InstParams))
@@ -875,10 +907,10 @@ int mmcq_set_state(mmcq_t* h, const void* buf, int64_t size) {
             return fail(h, MMCQ_ERR_ARG, "snapshot state fields invalid");
     std::vector<InstParams> ip(B);
     std::memcpy(ip.data(), p, sizeof(InstParams) * B); p += sizeof(InstParams) * B;
-    std::vector<double> g(B);
-    std::memcpy(g.data(), p, sizeof(double) * B); p += sizeof(double) * B;
-    std::vector<int> gm(B);
-    for (int b = 0; b < B; b++) { int32_t v; std::memcpy(&v, p, 4); p += 4; gm[b] = v; }
+    std::vector<double> g((size_t)B * MAX_MODES);
+    std::memcpy(g.data(), p, sizeof(double) * B * MAX_MODES); p += sizeof(double) * B * MAX_MODES;
+    std::vector<int> gm((size_t)B * MAX_MODES);
+    for (int q = 0; q < B * MAX_MODES; q++) { int32_t v; std::memcpy(&v, p, 4); p += 4; gm[q] = v; }
     CK(h, cudaStreamSynchronize(h->stream));
     const size_t row = sizeof(float4) * N;
     for (int b = 0; b < B; b++, p += row)
@@ -890,6 +922,9 @@ int mmcq_set_state(mmcq_t* h, const void* buf, int64_t size) {
     h->ip = ip;
     h->g = g;
     h->g_mode = gm;
+    for (const InstParams& q : ip)
+        for (int k = 0; k < MAX_MODES; k++)
+            if (q.cav_on[k] && k + 1 > h->nmodes) h->nmodes = k + 1;
     h->kind = hd.kind;
     h->mode = hd.mode;
     h->tol = hd.tol;
@@ -908,7 +943,7 @@ struct mmcq_group {
     cudaEvent_t fork = nullptr, done = nullptr;
     std::vector<cudaEvent_t> join, in;
     cudaGraphExec_t exec = nullptr;
-    std::vector<int> cap_kind, cap_mode, cap_record;
+    std::vector<int> cap_kind, cap_mode, cap_record, cap_nmodes;
     std::vector<double> cap_tol;
     std::vector<int64_t> cap_launches;      // kernel launches per replay, per handle
     int64_t replays = 0;
@@ -934,7 +969,7 @@ bool group_stale(const mmcq_group_t* g) {
     for (size_t i = 0; i < g->hs.size(); i++) {
         const mmcq_t* h = g->hs[i];
         if (h->kind != g->cap_kind[i] || h->mode != g->cap_mode[i] || h->tol != g->cap_tol[i] ||
-            h->record != g->cap_record[i])
+            h->record != g->cap_record[i] || h->nmodes != g->cap_nmodes[i])
             return true;
     }
     return false;
@@ -973,6 +1008,7 @@ int group_capture(mmcq_group_t* g) {
         g->cap_mode[i] = g->hs[i]->mode;
         g->cap_tol[i] = g->hs[i]->tol;
         g->cap_record[i] = g->hs[i]->record;
+        g->cap_nmodes[i] = g->hs[i]->nmodes;
     }
     if (r != MMCQ_OK) {
         if (graph) cudaGraphDestroy(graph);
@@ -1013,6 +1049,7 @@ int mmcq_group_create(mmcq_group_t** out, mmcq_t* const* handles, int n, int chu
     g->cap_mode.assign(n, -1);
     g->cap_tol.assign(n, -1.0);
     g->cap_record.assign(n, -1);
+    g->cap_nmodes.assign(n, -1);
     g->cap_launches.assign(n, 0);
     bool ok = cudaSetDevice(g->device) == cudaSuccess &&
               cudaStreamCreateWithFlags(&g->origin, cudaStreamNonBlocking) == cudaSuccess &&
@@ -1043,9 +1080,8 @@ int mmcq_group_step(mmcq_group_t* g, int64_t n, double dt) {
         // the first DP45 stage after a host-side change runs before the graph
         // (the captured attempts reuse it, first-same-as-last)
         if (h->kind == KIND_DP45 && h->mode == CAV_E && h->k1_dirty) {
-            StageArgs A{};
-            A.kind = h->kind; A.mode = h->mode; A.terms = MMCQ_TERM_ALL; A.tol = (float)h->tol; A.stage = 0;
-            A.record = h->record;
+            StageArgs A = step_args(h);
+            A.stage = 0;
             int r = run_stage(h, A, h->P.B);
             if (r) return gfail(g, r, "first stage launch failed");
             h->k1_dirty = false;

@@ -7,6 +7,7 @@
 namespace mq {
 
 constexpr int MAX_STAGES = 7;
+constexpr int MAX_MODES = 4;      // cavity modes (mode 0: the paper's single mode)
 constexpr int MAX_SLOTS = 4;      // 4-value FFT slots held per thread per stage
 constexpr int MAX_THREADS = 1024;
 constexpr int XINV_THREADS = 768;  // register budget of the torque kernel (85 per thread)
@@ -64,22 +65,23 @@ struct Material {
 // Per-instance parameters (set from the host).
 struct InstParams {
     double bext[3];
-    double wc, kappa, x0, p0;
-    double brms_scale;   // B_rms,i = brms_scale * profile_i
-    double drv_amp, drv_wcut, drv_t0;   // B_ext += drv_amp B_rms,i sinc(drv_wcut (t - drv_t0))
+    double wc[MAX_MODES], kappa[MAX_MODES], x0[MAX_MODES], p0[MAX_MODES];
+    double brms_scale[MAX_MODES];   // B_rms,k,i = brms_scale[k] * profile_k,i
+    double drv_amp, drv_wcut, drv_t0;   // B_ext += drv_amp B_rms,0,i sinc(drv_wcut (t - drv_t0))
     double inv_nmag;     // 1 / number of magnetised cells (spatial average of m)
-    int cav_on;
+    int cav_on[MAX_MODES];
     int drv_on;
+    int pad_;
 };
 
 // Per-instance integrator and cavity state (owned by the device).
 struct InstState {
     double t, tcav, dt, t_end;
-    double a_re, a_im;      // alpha at the start of the step (E-mode)
-    double as_re, as_im;    // alpha of the stage about to be evaluated (E-mode)
-    double S, C;            // P-mode accumulators
-    double ka_re[MAX_STAGES], ka_im[MAX_STAGES];
-    double X;               // last reduced coupling sum (includes V_c)
+    double a_re[MAX_MODES], a_im[MAX_MODES];     // alpha_k at the start of the step (E-mode)
+    double as_re[MAX_MODES], as_im[MAX_MODES];   // alpha_k of the stage about to be evaluated (E-mode)
+    double S[MAX_MODES], C[MAX_MODES];           // P-mode accumulators
+    double ka_re[MAX_MODES][MAX_STAGES], ka_im[MAX_MODES][MAX_STAGES];
+    double X[MAX_MODES];    // last reduced coupling sums (include V_c)
     double err;             // last error estimate (DP45)
     long long nacc, nrej, nhist;
     long long nmh;          // recorded spatial averages of m
@@ -98,10 +100,10 @@ struct Buffers {
     float2* spec;     // [B][nz][NT][ny][3][TX] x-half-spectrum
     float2* spec2;    // [B][nz][NT][py][3][TX] after the y transform (3-D only)
     float* kern;      // [hzk][hyk][NT*TX][6] demag kernel (real, scaled)
-    float4* prof;     // [N] coupling-profile shape (or null: uniform +y)
+    float4* prof[MAX_MODES];  // [N] coupling-profile shape of each mode (or null: uniform +y)
     InstParams* ip;
     InstState* st;
-    double* xpart;    // [B][nrows] FP64 partial coupling sums
+    double* xpart;    // [MAX_MODES][B][x-pass blocks] FP64 partial coupling sums
     float* epart;     // [B][nrows] partial error maxima
     unsigned* counter;  // [B] blocks finished in the current kernel
     double* hist;     // [B][hcap] accepted step lengths
@@ -123,6 +125,7 @@ struct StageArgs {
     int inst0;     // first instance of this launch (eval_field: one instance)
     float tol;
     int record;    // record <m> every `record` accepted steps (0: off)
+    int nmodes;    // cavity modes in use (highest enabled mode + 1)
 };
 
 }  // namespace mq

@@ -6,7 +6,7 @@
 //            along x, written to a tiled half-spectrum.
 //   k_col  : (col.cu) FFT along y (and z) of tiles of kx columns, the
 //            pointwise product with the symmetric demag kernel, inverse FFT.
-//   k_xinv : complex-to-real inverse FFT along x giving B_demag, then per cell
+//   k_xinv : (xinv.cu) complex-to-real inverse FFT along x giving B_demag, then per cell
 //            exchange + anisotropy + Zeeman + cavity B_rms Gamma (Sec. 2.1
 //            field terms, Eq. bcav), the LLG torque (Eq. llg), the RK
 //            bookkeeping, and FP64 block partials of the coupling sum
@@ -19,19 +19,9 @@
 #include "fftreg.cuh"
 #include "kern_common.cuh"
 #include "stagecore.cuh"
+#include "xpass.cuh"
 
 namespace mq {
-
-// Shared-memory pitch of the x passes: 3 R lines rounded up to an odd count,
-// so that consecutive cells (stride one pitch) fall in different banks.
-__host__ __device__ __forceinline__ int xpass_ld(int R) { return (3 * R) | 1; }
-
-// Threads of an x-pass block: 3 R lines x N1 threads per line with R = 64 / N1
-// rows (fewer when the grid has fewer rows), so never more than 192.
-constexpr int XPASS_THREADS = 192;
-// Resident blocks asked of the compiler: 5 (64 registers) while a thread
-// holds 16 points of the x transform, 3 when it holds 32 (L >= 512).
-constexpr int xpass_min_blocks(int L) { return L >= 512 ? 3 : 5; }
 
 // ---------------------------------------------------------------------------
 // x forward: stage input, M = Ms m_s, packed real FFT of length px = 2L.
@@ -111,154 +101,6 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xfwd(Pla
 }
 
 // ---------------------------------------------------------------------------
-// x inverse + local fields + torque + RK bookkeeping + cavity reduction.
-// Shared memory: xs[k][line] (k <= L, line = 3 r + comp), then m rows.
-// ---------------------------------------------------------------------------
-// REC: this launch records the spatial average of the state being accepted
-// (the last stage of a step with recording on); a separate instantiation so
-// that the common launches carry no extra accumulators.
-template <int L, bool REC>
-__global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Plan P, Material mat, Buffers Bf, StageArgs A) {
-    constexpr int NPT = ColShape<L>::NPT, N1 = ColShape<L>::N1;
-    extern __shared__ float2 sm[];
-    __shared__ double s_red[32];
-    __shared__ float s_redf[32];
-    __shared__ double s_gamma;
-    __shared__ float s_drive;
-    __shared__ int s_last;
-    const int b = A.inst0 + blockIdx.y;
-    const InstState& st = Bf.st[b];
-    if (stage_skips(st, A)) return;
-    const InstParams& ip = Bf.ip[b];
-    const int TX = P.TX, nx = P.nx, lt = P.lt;
-    const int row0 = blockIdx.x * P.R;
-    const int nr = min(P.R, P.nrows - row0);
-    const int ld = xpass_ld(P.R);
-    const long long cb = (long long)b * P.N;
-    const long long base = cb + (long long)row0 * nx;
-    const int s = A.stage;
-    const int K = A.kind;
-    float2* xs = sm;                                   // [L + 1][ld]
-    const int xs_n = (L + 1) * ld + (((L + 1) * ld) & 1);
-    float4* mrow = reinterpret_cast<float4*>(sm + xs_n);  // [row][nx]
-
-    // which buffer holds the stage input m_s
-    const float4* msrc;
-    if (A.field_only || s == 0) msrc = Bf.m[st.mcur];
-    else if (K == KIND_DP45 && s == 6) msrc = Bf.m[st.mcur ^ 1];
-    else msrc = Bf.ms;
-
-    // the z neighbours of this block's rows are read in the cell loop: ask L2
-    // for them now (only when the whole range lies inside the instance)
-    if (threadIdx.x == 0 && P.nz > 1 && (A.terms & 2)) {
-        const long long pl_ = (long long)nx * P.ny;
-        const unsigned bytes = (unsigned)(nr * nx * sizeof(float4));
-        if (row0 >= P.ny) prefetch_l2(msrc + base - pl_, bytes);
-        if (row0 + nr - 1 + P.ny < P.nrows) prefetch_l2(msrc + base + pl_, bytes);
-    }
-
-    // half-spectrum rows X[0..L] of the three components of every row
-    const long long tstride = (long long)P.ny * 3 * TX;
-    for (int r = 0; r < nr; r++) {
-        const int row = row0 + r;
-        const int z = (int)fdiv((unsigned)row, P.fd_ny), y = row - z * P.ny;
-        const float2* in = Bf.spec + (((long long)b * P.nz + z) * P.NT * P.ny + y) * 3 * TX;
-        for (int idx = threadIdx.x; idx < 3 * (L + 1); idx += blockDim.x) {
-            const int c = idx / (L + 1), k = idx - c * (L + 1);
-            const int t = k >> lt, tx = k & (TX - 1);
-            cp_async8(xs + k * ld + 3 * r + c, in + t * tstride + c * TX + tx);
-        }
-    }
-    for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) cp_async16(mrow + i, msrc + base + i);
-    if (threadIdx.x == 0) {
-        s_gamma = stage_gamma(A, ip, st, mat);
-        s_drive = (float)drive_factor(A, ip, st);
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    // Z[k] = (X[k] + conj X[L-k]) + i e^{+2 pi i k / px} (X[k] - conj X[L-k]), in place by pairs
-    const int twstep = P.twn / P.px;
-    constexpr int HALF = L / 2 + 1;
-    for (int idx = threadIdx.x; idx < 3 * nr * HALF; idx += blockDim.x) {
-        const int line = idx / HALF, k = idx - line * HALF;
-        const int kk = L - k;
-        float2 a = xs[k * ld + line], bq = xs[kk * ld + line];
-        float2 ca = conjf2(bq);
-        float2 sum = cadd(a, ca), dif = csub(a, ca);
-        float2 wd = cmul(twiddle(Bf.tw, k * twstep, true), dif);
-        float2 zk = make_float2(sum.x - wd.y, sum.y + wd.x);   // sum + i wd
-        if (k != 0 && kk != k) {
-            float2 cb2 = conjf2(a);
-            float2 sum2 = cadd(bq, cb2), dif2 = csub(bq, cb2);
-            float2 wd2 = cmul(twiddle(Bf.tw, kk * twstep, true), dif2);
-            xs[kk * ld + line] = make_float2(sum2.x - wd2.y, sum2.y + wd2.x);
-        }
-        xs[k * ld + line] = zk;
-    }
-    __syncthreads();
-    {
-        const int nl = 3 * P.R;
-        const int line = threadIdx.x % nl, j = threadIdx.x / nl;
-        float2 v[NPT];
-#pragma unroll
-        for (int n2 = 0; n2 < NPT; n2++) v[n2] = xs[(j + N1 * n2) * ld + line];
-        col_fft<L, true>(v, xs, ld, line, j, Bf.tw, P.twn);
-#pragma unroll
-        for (int i = 0; i < NPT; i++) xs[col_out_row<L>(j, i) * ld + line] = v[i];
-    }
-    __syncthreads();
-
-    const bool want_demag = A.terms & 1, want_exch = A.terms & 2;
-    CellUpdate cu;
-    cu.init(Bf, A, st, ip, (float)s_gamma, s_drive, cb);
-    const long long pl = (long long)nx * P.ny;
-    double xacc = 0.0;
-    double macc[REC ? 3 : 1] = {};
-    float emax = 0.f;
-    bool bad = false;
-    for (int ii = threadIdx.x; ii < nr * nx; ii += blockDim.x) {
-        const int r = (int)fdiv((unsigned)ii, P.fd_nx), x = ii - r * nx;
-        const int row = row0 + r;
-        const int z = (int)fdiv((unsigned)row, P.fd_ny), y = row - z * P.ny;
-        const long long i = base + ii;
-        float4 m = mrow[ii];
-        const float Ms = m.w;
-        float Bx = 0.f, By = 0.f, Bz = 0.f;
-        if (want_demag) {
-            const float2* zr = xs + (x >> 1) * ld + 3 * r;
-            float2 zx = zr[0], zy = zr[1], zz = zr[2];
-            if (x & 1) { Bx = zx.y; By = zy.y; Bz = zz.y; }
-            else { Bx = zx.x; By = zy.x; Bz = zz.x; }
-        }
-        if (Ms > 0.f && want_exch) {
-            float hx = 0.f, hy = 0.f, hz = 0.f;
-            float4 q;
-#define MMCQ_NB(Q, C)                                                                   \
-    q = (Q);                                                                            \
-    if (q.w > 0.f) { hx += (C) * (q.x - m.x); hy += (C) * (q.y - m.y); hz += (C) * (q.z - m.z); }
-            if (x > 0) { MMCQ_NB(mrow[ii - 1], mat.exch[0]) }
-            if (x + 1 < nx) { MMCQ_NB(mrow[ii + 1], mat.exch[0]) }
-            if (y > 0) {
-                if (r > 0) { MMCQ_NB(mrow[ii - nx], mat.exch[1]) }
-                else { MMCQ_NB(__ldg(msrc + i - nx), mat.exch[1]) }
-            }
-            if (y + 1 < P.ny) {
-                if (r + 1 < nr) { MMCQ_NB(mrow[ii + nx], mat.exch[1]) }
-                else { MMCQ_NB(__ldg(msrc + i + nx), mat.exch[1]) }
-            }
-            if (z > 0) { MMCQ_NB(__ldg(msrc + i - pl), mat.exch[2]) }
-            if (z + 1 < P.nz) { MMCQ_NB(__ldg(msrc + i + pl), mat.exch[2]) }
-#undef MMCQ_NB
-            float inv = 1.f / Ms;
-            Bx += hx * inv; By += hy * inv; Bz += hz * inv;
-        }
-        cu.run<REC>(mat, Bf, i, m, Bx, By, Bz, xacc, macc, emax, bad);
-    }
-    if (A.field_only) return;
-    stage_epilogue<REC>(P, mat, Bf, A, b, blockIdx.x, P.nblk, xacc, emax, bad, s_red, s_redf, &s_last, macc);
-}
-
-// ---------------------------------------------------------------------------
 // small helpers
 // ---------------------------------------------------------------------------
 
@@ -311,7 +153,7 @@ __global__ void k_get_field(const float4* f, float* dst, long long N) {
 // X = V_c sum Ms m . B_rms of each instance at its accepted state (read-out
 // only): one block per instance, fixed-order reduction.
 __global__ void k_coupling_sum(const float4* m0, const float4* m1, const InstState* st, const InstParams* ip,
-                               const float4* prof, long long N, double vc, int b0, double* out) {
+                               const float4* prof, long long N, double vc, int b0, int k, double* out) {
     __shared__ double red[32];
     const int b = b0 + blockIdx.x;
     const float4* m = (st[b].mcur ? m1 : m0) + (long long)b * N;
@@ -323,7 +165,7 @@ __global__ void k_coupling_sum(const float4* m0, const float4* m1, const InstSta
         acc += (double)v.w * (v.x * px + v.y * py + v.z * pz);
     }
     acc = block_sum_d(acc, red);
-    if (threadIdx.x == 0) out[blockIdx.x] = ip[b].cav_on ? acc * ip[b].brms_scale * vc : 0.0;
+    if (threadIdx.x == 0) out[blockIdx.x] = ip[b].cav_on[k] ? acc * ip[b].brms_scale[k] * vc : 0.0;
 }
 
 // Trapezoid-weighted Fourier transform of one component of the recorded
@@ -384,7 +226,6 @@ int rows_per_block(int L, int nrows) {
     return R;
 }
 
-static int xthreads(const Plan& P) { return 3 * P.R * col_threads_per_column(P.L); }
 
 // shared memory of the x passes: x forward: the packed lines and the
 // px-entry twiddle table; x inverse: the half-spectrum lines and the m rows
@@ -398,7 +239,6 @@ size_t xinv_smem(const Plan& P) {
 
 bool x_fits(const Plan& P) { return P.L <= 1024 && xthreads(P) <= 512 && xinv_smem(P) <= 200 * 1024; }
 
-#define MMCQ_XCASES(F) F(1) F(2) F(4) F(8) F(16) F(32) F(64) F(128) F(256) F(512) F(1024)
 
 cudaError_t launch_xfwd(const Plan& P, const Buffers& Bf, const StageArgs& A, int nb, cudaStream_t s) {
     dim3 grid(P.nblk, nb);
@@ -406,25 +246,6 @@ cudaError_t launch_xfwd(const Plan& P, const Buffers& Bf, const StageArgs& A, in
     const size_t sm = xfwd_smem(P);
     switch (P.L) {
 #define MMCQ_CASE(Lv) case Lv: k_xfwd<Lv><<<grid, th, sm, s>>>(P, Bf, A); break;
-        MMCQ_XCASES(MMCQ_CASE)
-#undef MMCQ_CASE
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_xinv(const Plan& P, const Material& mat, const Buffers& Bf, const StageArgs& A, int nb,
-                        cudaStream_t s) {
-    dim3 grid(P.nblk, nb);
-    const int th = xthreads(P);
-    const size_t sm = xinv_smem(P);
-    const bool rec = A.record > 0 && !A.field_only && A.stage == (A.kind == KIND_RK4 ? 3 : 6);
-    switch (P.L) {
-#define MMCQ_CASE(Lv)                                                      \
-    case Lv:                                                               \
-        if (rec) k_xinv<Lv, true><<<grid, th, sm, s>>>(P, mat, Bf, A);    \
-        else k_xinv<Lv, false><<<grid, th, sm, s>>>(P, mat, Bf, A);       \
-        break;
         MMCQ_XCASES(MMCQ_CASE)
 #undef MMCQ_CASE
         default: return cudaErrorInvalidValue;
@@ -457,9 +278,9 @@ cudaError_t launch_get_field(const float4* f, float* dst, long long N, cudaStrea
     k_get_field<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(f, dst, N);
     return cudaGetLastError();
 }
-cudaError_t launch_coupling_sum(const Buffers& Bf, long long N, double vc, int b0, int nb, double* out,
+cudaError_t launch_coupling_sum(const Buffers& Bf, long long N, double vc, int b0, int nb, int k, double* out,
                                 cudaStream_t s) {
-    k_coupling_sum<<<nb, 1024, 0, s>>>(Bf.m[0], Bf.m[1], Bf.st, Bf.ip, Bf.prof, N, vc, b0, out);
+    k_coupling_sum<<<nb, 1024, 0, s>>>(Bf.m[0], Bf.m[1], Bf.st, Bf.ip, Bf.prof[k], N, vc, b0, k, out);
     return cudaGetLastError();
 }
 cudaError_t launch_set_dt(InstState* st, int B, double dt, cudaStream_t s) {
@@ -468,6 +289,7 @@ cudaError_t launch_set_dt(InstState* st, int B, double dt, cudaStream_t s) {
 }
 
 cudaError_t col_init();
+cudaError_t xinv_init();
 
 cudaError_t set_smem_limits() {
     cudaError_t e;
@@ -476,14 +298,10 @@ cudaError_t set_smem_limits() {
     const int lim = 200 * 1024;
 #define MMCQ_CASE(Lv)                                                                                         \
     if ((e = cudaFuncSetAttribute(k_xfwd<Lv>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess) \
-        return e;                                                                                             \
-    if ((e = cudaFuncSetAttribute(k_xinv<Lv, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) !=        \
-        cudaSuccess)                                                                                               \
-        return e;                                                                                                  \
-    if ((e = cudaFuncSetAttribute(k_xinv<Lv, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess) \
         return e;
     MMCQ_XCASES(MMCQ_CASE)
 #undef MMCQ_CASE
+    if ((e = xinv_init()) != cudaSuccess) return e;
     return col_init();
 }
 

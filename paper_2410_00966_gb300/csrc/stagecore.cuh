@@ -57,47 +57,51 @@ static __device__ float block_max_f(float v, float* red) {
     return r;
 }
 
-// Gamma(t) from the P-mode accumulators, Eq. (gammadiscretefinal).
-static __device__ double gamma_p(const InstParams& ip, const InstState& s, double tc, double hbar) {
-    double e = exp(-ip.kappa * tc);
+// Gamma_k(t) from the P-mode accumulators, Eq. (gammadiscretefinal).
+static __device__ double gamma_p(const InstParams& ip, const InstState& s, int k, double tc, double hbar) {
+    double e = exp(-ip.kappa[k] * tc);
     double sn, cs;
-    sincos(ip.wc * tc, &sn, &cs);
-    return e * cs * (ip.x0 - 2.0 * s.S / hbar) - e * sn * (ip.p0 - 2.0 * s.C / hbar);
+    sincos(ip.wc[k] * tc, &sn, &cs);
+    return e * cs * (ip.x0[k] - 2.0 * s.S[k] / hbar) - e * sn * (ip.p0[k] - 2.0 * s.C[k] / hbar);
 }
 
 // FP64 scalar work after the last block of an instance has finished a stage:
-// cavity amplitude (E-mode: d alpha/dt = -(kappa + i omega_c) alpha + i X / hbar,
-// Eq. eqmotionaclasical with omega_c -> omega_c - i kappa), accumulators
-// (P-mode, Eq. Sdiscrete / Cdiscrete), time, accept / reject and step size.
+// for every cavity mode k the amplitude (E-mode: d alpha_k/dt =
+// -(kappa_k + i omega_k) alpha_k + i X_k / hbar, Eq. eqmotionaclasical with
+// omega_c -> omega_c - i kappa) or the accumulators (P-mode, Eq. Sdiscrete /
+// Cdiscrete); then time, accept / reject and step size.  Xsum[k] holds the
+// coupling sums without V_c.
 static __device__ void finish_stage(const Plan& P, const Material& mat, const StageArgs& A, const InstParams& ip,
-                             InstState& s, double Xsum, float errmax, double* hist, int hcap, int* flags,
+                             InstState& s, const double* Xsum, float errmax, double* hist, int hcap, int* flags,
                              const double* msum = nullptr, double* mhist = nullptr) {
-    const double X = Xsum * mat.vc;
     const int k = A.stage;
-    const bool ecav = ip.cav_on && A.mode == CAV_E;
-    const bool pcav = ip.cav_on && A.mode == CAV_P;
     const int K = A.kind;
+    const int nm = A.nmodes;
     const double dt = s.dt;
-    s.X = X;
-    if (ecav) {
-        // derivative of alpha at this stage
-        s.ka_re[k] = -ip.kappa * s.as_re + ip.wc * s.as_im;
-        s.ka_im[k] = -ip.kappa * s.as_im - ip.wc * s.as_re + X / mat.hbar;
+    for (int q = 0; q < nm; q++) {
+        const double X = Xsum[q] * mat.vc;
+        s.X[q] = X;
+        if (ip.cav_on[q] && A.mode == CAV_E) {
+            // derivative of alpha_q at this stage
+            s.ka_re[q][k] = -ip.kappa[q] * s.as_re[q] + ip.wc[q] * s.as_im[q];
+            s.ka_im[q][k] = -ip.kappa[q] * s.as_im[q] - ip.wc[q] * s.as_re[q] + X / mat.hbar;
+        }
     }
     const int nst = K == KIND_RK4 ? 4 : 7;
     const bool last = k == nst - 1;
     if (!last) {
-        if (ecav) {
-            // alpha of the next stage (DP45 stage 7 takes the 5th-order weights)
-            const bool to_b = (K == KIND_DP45 && k + 1 == 6);
-            double re = s.a_re, im = s.a_im;
+        // alpha of the next stage (DP45 stage 7 takes the 5th-order weights)
+        const bool to_b = (K == KIND_DP45 && k + 1 == 6);
+        for (int q = 0; q < nm; q++) {
+            if (!ip.cav_on[q] || A.mode != CAV_E) continue;
+            double re = s.a_re[q], im = s.a_im[q];
             for (int j = 0; j <= k; j++) {
                 double w = to_b ? c_bd[1][j] : c_ad[K][k + 1][j];
-                re += dt * w * s.ka_re[j];
-                im += dt * w * s.ka_im[j];
+                re += dt * w * s.ka_re[q][j];
+                im += dt * w * s.ka_im[q][j];
             }
-            s.as_re = re;
-            s.as_im = im;
+            s.as_re[q] = re;
+            s.as_im[q] = im;
         }
         if (K == KIND_DP45 && k == 0) s.have_k1 = 1;
         return;
@@ -110,20 +114,22 @@ static __device__ void finish_stage(const Plan& P, const Material& mat, const St
     }
     if (accept) {
         if (K == KIND_RK4) {
-            if (ecav) {
-                double re = s.a_re, im = s.a_im;
+            for (int q = 0; q < nm; q++) {
+                if (!ip.cav_on[q] || A.mode != CAV_E) continue;
+                double re = s.a_re[q], im = s.a_im[q];
                 for (int j = 0; j < 4; j++) {
-                    re += dt * c_bd[0][j] * s.ka_re[j];
-                    im += dt * c_bd[0][j] * s.ka_im[j];
+                    re += dt * c_bd[0][j] * s.ka_re[q][j];
+                    im += dt * c_bd[0][j] * s.ka_im[q][j];
                 }
-                s.a_re = re; s.a_im = im;
+                s.a_re[q] = re; s.a_im[q] = im;
             }
         } else {
             s.mcur ^= 1;
             s.k1slot = s.k1slot == 0 ? 6 : 0;
-            if (ecav) {
-                s.a_re = s.as_re; s.a_im = s.as_im;   // alpha5
-                s.ka_re[0] = s.ka_re[6]; s.ka_im[0] = s.ka_im[6];
+            for (int q = 0; q < nm; q++) {
+                if (!ip.cav_on[q] || A.mode != CAV_E) continue;
+                s.a_re[q] = s.as_re[q]; s.a_im[q] = s.as_im[q];   // alpha5
+                s.ka_re[q][0] = s.ka_re[q][6]; s.ka_im[q][0] = s.ka_im[q][6];
             }
             if (A.mode == CAV_P) s.have_k1 = 0;   // Gamma at t_n changes with S_n, C_n
         }
@@ -143,11 +149,14 @@ static __device__ void finish_stage(const Plan& P, const Material& mat, const St
             }
             s.nmh++;
         }
-        if (pcav) {
-            double e = exp(ip.kappa * s.tcav), sn, cs;
-            sincos(ip.wc * s.tcav, &sn, &cs);
-            s.S += e * sn * X * dt;
-            s.C += e * cs * X * dt;
+        if (A.mode == CAV_P) {
+            for (int q = 0; q < nm; q++) {
+                if (!ip.cav_on[q]) continue;
+                double e = exp(ip.kappa[q] * s.tcav), sn, cs;
+                sincos(ip.wc[q] * s.tcav, &sn, &cs);
+                s.S[q] += e * sn * s.X[q] * dt;
+                s.C[q] += e * cs * s.X[q] * dt;
+            }
         }
     } else {
         s.nrej++;
@@ -166,12 +175,13 @@ static __device__ void finish_stage(const Plan& P, const Material& mat, const St
         if (nd < 1e-20 && !s.done) { atomicOr(flags, FLAG_DT_UNDERFLOW); s.done = 1; }
         s.dt = nd;
     }
-    if (ecav) {
+    for (int q = 0; q < nm; q++) {
+        if (!ip.cav_on[q] || A.mode != CAV_E) continue;
         if (K == KIND_DP45) {
-            s.as_re = s.a_re + s.dt * c_ad[1][1][0] * s.ka_re[0];
-            s.as_im = s.a_im + s.dt * c_ad[1][1][0] * s.ka_im[0];
+            s.as_re[q] = s.a_re[q] + s.dt * c_ad[1][1][0] * s.ka_re[q][0];
+            s.as_im[q] = s.a_im[q] + s.dt * c_ad[1][1][0] * s.ka_im[q][0];
         } else {
-            s.as_re = s.a_re; s.as_im = s.a_im;
+            s.as_re[q] = s.a_re[q]; s.as_im[q] = s.a_im[q];
         }
     }
 }
@@ -272,25 +282,34 @@ struct StageInput {
 };
 
 // Everything a stage needs per cell once demag and exchange are known:
-// anisotropy, Zeeman and cavity fields, the LLG torque (Eq. llg), the RK
-// bookkeeping of this stage, and the cell's share of the coupling sum and of
-// the DP45 error.  Material constants and buffer pointers are read from the
-// kernel's parameter block at each use.
+// anisotropy, Zeeman (with the Appendix C excitation) and cavity fields, the
+// LLG torque (Eq. llg), the RK bookkeeping of this stage, and the cell's
+// share of the coupling sums and of the DP45 error.  NM: cavity modes
+// compiled in (1: the paper's single mode; MAX_MODES: up to A.nmodes).
+// Material constants and buffer pointers are read from the kernel's
+// parameter block at each use.
+template <int NM>
 struct CellUpdate {
-    float G, bs, dt, bex, bey, bez, D;
-    bool cav_on, want_anis, want_zee, want_cav, field_only;
-    int K, s, mode;
+    float G[NM], bs[NM];
+    bool on[NM];
+    float dt, bex, bey, bez, D;
+    bool want_anis, want_zee, want_cav, field_only;
+    int K, s, mode, nm;
     long long cb;
     float4* kout;
 
     __device__ __forceinline__ void init(const Buffers& Bf, const StageArgs& A, const InstState& st,
-                                         const InstParams& ip, float Gamma, float drive, long long cb_) {
-        G = Gamma;
+                                         const InstParams& ip, const double* gam, float drive, long long cb_) {
+        nm = NM == 1 ? 1 : A.nmodes;
+#pragma unroll
+        for (int q = 0; q < NM; q++) {
+            G[q] = (float)gam[q];
+            bs[q] = (float)ip.brms_scale[q];
+            on[q] = q < nm && ip.cav_on[q] != 0;
+        }
         D = drive;
-        bs = (float)ip.brms_scale;
         dt = (float)st.dt;
         bex = (float)ip.bext[0]; bey = (float)ip.bext[1]; bez = (float)ip.bext[2];
-        cav_on = ip.cav_on != 0;
         want_anis = A.terms & 4; want_zee = A.terms & 8; want_cav = A.terms & 16;
         field_only = A.field_only != 0;
         K = A.kind; s = A.stage; mode = A.mode;
@@ -303,10 +322,12 @@ struct CellUpdate {
     // (Bx, By, Bz) holds demag + exchange on entry
     template <bool REC>
     __device__ __forceinline__ void run(const Material& mat, const Buffers& Bf, long long i, float4 m, float Bx,
-                                        float By, float Bz, double& xacc, double (&macc)[REC ? 3 : 1], float& emax,
-                                        bool& bad) const {
+                                        float By, float Bz, double (&xacc)[NM], double (&macc)[REC ? 3 : 1],
+                                        float& emax, bool& bad) const {
         const float Ms = m.w;
-        float px_ = 0.f, py_ = 0.f, pz_ = 0.f;
+        float px_[NM], py_[NM], pz_[NM];
+#pragma unroll
+        for (int q = 0; q < NM; q++) px_[q] = py_[q] = pz_[q] = 0.f;
         if (Ms > 0.f) {
             if (want_anis) {
                 float mu = m.x * mat.u[0] + m.y * mat.u[1] + m.z * mat.u[2];
@@ -314,12 +335,18 @@ struct CellUpdate {
                 Bx += f * mat.u[0]; By += f * mat.u[1]; Bz += f * mat.u[2];
             }
             if (want_zee) { Bx += bex; By += bey; Bz += bez; }
-            if (cav_on || D != 0.f) {
-                if (Bf.prof) { float4 p = __ldg(Bf.prof + (i - cb)); px_ = bs * p.x; py_ = bs * p.y; pz_ = bs * p.z; }
-                else { py_ = bs; }
-                if (cav_on && want_cav) { Bx += G * px_; By += G * py_; Bz += G * pz_; }
-                // Appendix C excitation, part of the external field
-                if (want_zee) { Bx += D * px_; By += D * py_; Bz += D * pz_; }
+#pragma unroll
+            for (int q = 0; q < NM; q++) {
+                // the excitation (Appendix C) uses the map of mode 0
+                if (!(on[q] || (q == 0 && D != 0.f))) continue;
+                if (Bf.prof[q]) {
+                    float4 p = __ldg(Bf.prof[q] + (i - cb));
+                    px_[q] = bs[q] * p.x; py_[q] = bs[q] * p.y; pz_[q] = bs[q] * p.z;
+                } else {
+                    py_[q] = bs[q];
+                }
+                if (on[q] && want_cav) { Bx += G[q] * px_[q]; By += G[q] * py_[q]; Bz += G[q] * pz_[q]; }
+                if (q == 0 && want_zee) { Bx += D * px_[0]; By += D * py_[0]; Bz += D * pz_[0]; }
             }
         }
         if (field_only) {
@@ -332,7 +359,7 @@ struct CellUpdate {
                                 mat.pre * (cz + mat.alpha * dz), 0.f);
         if (!(Ms > 0.f)) kk = make_float4(0.f, 0.f, 0.f, 0.f);
         if (!isfinite(kk.x) || !isfinite(kk.y) || !isfinite(kk.z)) bad = true;
-        float4 mx = m;   // m used for the coupling sum of this launch
+        float4 mx = m;   // m used for the coupling sums of this launch
         float4 mrec = m; // state being accepted (recorded spatial average)
         if (K == KIND_RK4) {
             if (s < 3) {
@@ -362,9 +389,11 @@ struct CellUpdate {
                 emax = fmaxf(emax, sqrtf(exx * exx + eyy * eyy + ezz * ezz));
             }
         }
-        // per-cell product in FP32, accumulated in FP64 (the sum over cells is
+        // per-cell products in FP32, accumulated in FP64 (the sum over cells is
         // the quantity that needs the range; FP64 arithmetic is ~1/64 rate here)
-        if (cav_on) xacc += (double)(Ms * (mx.x * px_ + mx.y * py_ + mx.z * pz_));
+#pragma unroll
+        for (int q = 0; q < NM; q++)
+            if (on[q]) xacc[q] += (double)(Ms * (mx.x * px_[q] + mx.y * py_[q] + mx.z * pz_[q]));
         if constexpr (REC) {
             if (Ms > 0.f) { macc[0] += mrec.x; macc[1] += mrec.y; macc[2] += mrec.z; }
         }
@@ -380,34 +409,39 @@ static __device__ double drive_factor(const StageArgs& A, const InstParams& ip, 
     return ip.drv_amp * (x == 0.0 ? 1.0 : sin(x) / x);
 }
 
-// Gamma(t) for the stage of this launch (E-mode: 2 Re alpha of the stage;
+// Gamma_k(t) for the stage of this launch (E-mode: 2 Re alpha_k of the stage;
 // P-mode: Eq. gammadiscretefinal at the stage time).
 static __device__ double stage_gamma(const StageArgs& A, const InstParams& ip, const InstState& st,
-                                     const Material& mat) {
-    if (!ip.cav_on) return 0.0;
-    if (A.mode == CAV_E) return 2.0 * (A.field_only ? st.a_re : st.as_re);
-    return gamma_p(ip, st, st.tcav + (A.field_only ? 0.0 : c_cd[A.kind][A.stage] * st.dt), mat.hbar);
+                                     const Material& mat, int k) {
+    if (!ip.cav_on[k]) return 0.0;
+    if (A.mode == CAV_E) return 2.0 * (A.field_only ? st.a_re[k] : st.as_re[k]);
+    return gamma_p(ip, st, k, st.tcav + (A.field_only ? 0.0 : c_cd[A.kind][A.stage] * st.dt), mat.hbar);
 }
 
-// Block partials of X and of the DP45 error; the last block of the instance
+// Block partials of X_k and of the DP45 error; the last block of the instance
 // to arrive reduces all partials in a fixed order and runs finish_stage.
 // `nparts` = blocks per instance, `part` = this block's index among them.
-template <bool REC>
+// Partials of mode k live at xpart[(k B + b) nparts + part].
+template <bool REC, int NM>
 static __device__ void stage_epilogue(const Plan& P, const Material& mat, const Buffers& Bf, const StageArgs& A,
-                                      int b, int part, int nparts, double xacc, float emax, bool bad,
+                                      int b, int part, int nparts, const double (&xacc)[NM], float emax, bool bad,
                                       double* s_red, float* s_redf, int* s_last, const double* macc) {
-    constexpr bool rec = REC;
     if (bad) atomicOr(Bf.flags, FLAG_NAN);
-    double xb = block_sum_d(xacc, s_red);
+    const int nm = NM == 1 ? 1 : A.nmodes;
+    double xb[NM];
+#pragma unroll
+    for (int q = 0; q < NM; q++) xb[q] = q < nm ? block_sum_d(xacc[q], s_red) : 0.0;
     float eb = block_max_f(emax, s_redf);
     const long long pb = (long long)b * nparts;
     double mb[3] = {0.0, 0.0, 0.0};
-    if (rec)
+    if (REC)
         for (int c = 0; c < 3; c++) mb[c] = block_sum_d(macc[c], s_red);
     if (threadIdx.x == 0) {
-        Bf.xpart[pb + part] = xb;
+#pragma unroll
+        for (int q = 0; q < NM; q++)
+            if (q < nm) Bf.xpart[((long long)q * P.B + b) * nparts + part] = xb[q];
         Bf.epart[pb + part] = eb;
-        if (rec)
+        if (REC)
             for (int c = 0; c < 3; c++) Bf.mpart[3 * (pb + part) + c] = mb[c];
         __threadfence();
         unsigned prev = atomicAdd(Bf.counter + b, 1u);
@@ -416,16 +450,18 @@ static __device__ void stage_epilogue(const Plan& P, const Material& mat, const 
     __syncthreads();
     if (!*s_last) return;
     __threadfence();
-    double xsum = 0.0;
-    float em = 0.f;
-    for (int r = threadIdx.x; r < nparts; r += blockDim.x) {
-        xsum += __ldcg(Bf.xpart + pb + r);
-        em = fmaxf(em, __ldcg(Bf.epart + pb + r));
+    double xs[MAX_MODES] = {0.0, 0.0, 0.0, 0.0};
+    for (int q = 0; q < nm; q++) {
+        double v = 0.0;
+        const double* xp = Bf.xpart + ((long long)q * P.B + b) * nparts;
+        for (int r = threadIdx.x; r < nparts; r += blockDim.x) v += __ldcg(xp + r);
+        xs[q] = block_sum_d(v, s_red);
     }
-    xsum = block_sum_d(xsum, s_red);
+    float em = 0.f;
+    for (int r = threadIdx.x; r < nparts; r += blockDim.x) em = fmaxf(em, __ldcg(Bf.epart + pb + r));
     em = block_max_f(em, s_redf);
     double msum[3] = {0.0, 0.0, 0.0};
-    if (rec) {
+    if (REC) {
         for (int c = 0; c < 3; c++) {
             double v = 0.0;
             for (int r = threadIdx.x; r < nparts; r += blockDim.x) v += __ldcg(Bf.mpart + 3 * (pb + r) + c);
@@ -434,8 +470,8 @@ static __device__ void stage_epilogue(const Plan& P, const Material& mat, const 
     }
     if (threadIdx.x == 0) {
         InstState ns = Bf.st[b];
-        finish_stage(P, mat, A, Bf.ip[b], ns, xsum, em, Bf.hist + (long long)b * Bf.hcap, Bf.hcap, Bf.flags,
-                     rec ? msum : nullptr, rec ? Bf.mhist + 4LL * b * Bf.hcap : nullptr);
+        finish_stage(P, mat, A, Bf.ip[b], ns, xs, em, Bf.hist + (long long)b * Bf.hcap, Bf.hcap, Bf.flags,
+                     REC ? msum : nullptr, REC ? Bf.mhist + 4LL * b * Bf.hcap : nullptr);
         Bf.st[b] = ns;
         Bf.counter[b] = 0u;
     }

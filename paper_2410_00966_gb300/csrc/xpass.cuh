@@ -1,0 +1,24 @@
+// Shapes shared by the two x passes (stage.cu: x forward, xinv.cu: x inverse).
+#pragma once
+
+#include "common.cuh"
+#include "fftreg.cuh"
+
+namespace mq {
+
+// Shared-memory pitch of the x passes: 3 R lines rounded up to an odd count,
+// so that consecutive cells (stride one pitch) fall in different banks.
+__host__ __device__ __forceinline__ int xpass_ld(int R) { return (3 * R) | 1; }
+
+// Threads of an x-pass block: 3 R lines x N1 threads per line with R = 64 / N1
+// rows (fewer when the grid has fewer rows), so never more than 192.
+constexpr int XPASS_THREADS = 192;
+// Resident blocks asked of the compiler: 5 (64 registers) while a thread
+// holds 16 points of the x transform, 3 when it holds 32 (L >= 512).
+constexpr int xpass_min_blocks(int L) { return L >= 512 ? 3 : 5; }
+
+static inline int xthreads(const Plan& P) { return 3 * P.R * col_threads_per_column(P.L); }
+
+#define MMCQ_XCASES(F) F(1) F(2) F(4) F(8) F(16) F(32) F(64) F(128) F(256) F(512) F(1024)
+
+}  // namespace mq
