@@ -21,7 +21,6 @@ cudaError_t launch_conv_part(const Plan&, const Buffers&, const StageArgs&, int,
 int convolution_launches(const Plan&);
 bool col_fits(const Plan&);
 bool fft_fits(int, int);
-size_t xinv_smem(const Plan&);
 int rows_per_block(int, int);
 bool x_fits(const Plan&);
 cudaError_t launch_set_m(float4*, const float*, const float*, long long, int, int, int*, cudaStream_t);

@@ -227,15 +227,9 @@ int rows_per_block(int L, int nrows) {
 }
 
 
-// shared memory of the x passes: x forward: the packed lines and the
-// px-entry twiddle table; x inverse: the half-spectrum lines and the m rows
+// shared memory of the x forward: the packed lines and the px-entry twiddle table
 size_t xfwd_smem(const Plan& P) { return ((size_t)P.L * xpass_ld(P.R) + P.px) * sizeof(float2); }
 
-size_t xinv_smem(const Plan& P) {
-    size_t n2 = (size_t)(P.L + 1) * xpass_ld(P.R);
-    n2 += n2 & 1;
-    return n2 * sizeof(float2) + (size_t)P.nx * P.R * sizeof(float4);
-}
 
 bool x_fits(const Plan& P) { return P.L <= 1024 && xthreads(P) <= 512 && xinv_smem(P) <= 200 * 1024; }
 

@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
             float inv = 1.f / Ms;
             Bx += hx * inv; By += hy * inv; Bz += hz * inv;
         }
-        cu.run<REC>(mat, Bf, i, m, Bx, By, Bz, xacc, macc, emax, bad);
+        cu.template run<REC>(mat, Bf, i, m, Bx, By, Bz, xacc, macc, emax, bad);
     }
     if (A.field_only) return;
     stage_epilogue<REC, NM>(P, mat, Bf, A, b, blockIdx.x, P.nblk, xacc, emax, bad, s_red, s_redf, &s_last, macc);

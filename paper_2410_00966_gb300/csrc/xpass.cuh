@@ -19,6 +19,13 @@ constexpr int xpass_min_blocks(int L) { return L >= 512 ? 3 : 5; }
 
 static inline int xthreads(const Plan& P) { return 3 * P.R * col_threads_per_column(P.L); }
 
+// Shared memory of the x inverse: the half-spectrum lines and the m rows.
+static inline size_t xinv_smem(const Plan& P) {
+    size_t n2 = (size_t)(P.L + 1) * xpass_ld(P.R);
+    n2 += n2 & 1;
+    return n2 * sizeof(float2) + (size_t)P.nx * P.R * sizeof(float4);
+}
+
 #define MMCQ_XCASES(F) F(1) F(2) F(4) F(8) F(16) F(32) F(64) F(128) F(256) F(512) F(1024)
 
 }  // namespace mq
