@@ -944,6 +944,169 @@ void or_demag_at(const oracle* o, const double* m, const long* cells, long nc, d
     }
 }
 
+// ---- discrete adjoint of the RK4 path (gradients) -------------------------------
+// Vector-Jacobian product of the right-hand side at (m, alpha) of mode 0
+// (E-mode): given cotangents u (of dm/dt, per cell) and nu (of d alpha/dt, as
+// (re, im)), returns the cotangent of m (gm), of alpha (ga) and the parameter
+// cotangents dp = (B_ext x, y, z; eta; omega_c; kappa), eta the scale of the
+// B_rms map (B_rms -> eta B_rms, at eta = 1).  Written from Eq. (llg), the
+// field terms of Sec. 2.1, Eq. (bcav) and the amplitude equation of Sec. 2.2.
+static void rhs_vjp(const oracle* o, const double* m, cplx a, const double* u, const double* nu, double* gm,
+                    double* ga, double* dp) {
+    const long n = o->n;
+    const double G = 2.0 * a.real();
+    double Gam[OR_MAX_MODES] = {G, 0, 0, 0};
+    std::vector<double> B(3 * n), lb(3 * n, 0.0), v(3 * n, 0.0), D(3 * n);
+    total_field(o, m, Gam, B.data(), 0.0);
+    const double pre = -o->gamma / (1.0 + o->alpha * o->alpha), al = o->alpha;
+    const double* br = o->brms[0].data();
+    const double lX = nu[1] / o->hbar;      // cotangent of X (f_i = ... + X / hbar)
+    double X = 0;
+    for (long i = 0; i < n; i++) {
+        if (o->ms[i] <= 0) { for (int c = 0; c < 3; c++) gm[3 * i + c] = 0; continue; }
+        const double* mi = m + 3 * i;
+        const double* bi = &B[3 * i];
+        const double* ui = u + 3 * i;
+        double mb = mi[0] * bi[0] + mi[1] * bi[1] + mi[2] * bi[2];
+        double um = ui[0] * mi[0] + ui[1] * mi[1] + ui[2] * mi[2];
+        double ub = ui[0] * bi[0] + ui[1] * bi[1] + ui[2] * bi[2];
+        double mm = mi[0] * mi[0] + mi[1] * mi[1] + mi[2] * mi[2];
+        double bxu[3] = {bi[1] * ui[2] - bi[2] * ui[1], bi[2] * ui[0] - bi[0] * ui[2], bi[0] * ui[1] - bi[1] * ui[0]};
+        double uxm[3] = {ui[1] * mi[2] - ui[2] * mi[1], ui[2] * mi[0] - ui[0] * mi[2], ui[0] * mi[1] - ui[1] * mi[0]};
+        for (int c = 0; c < 3; c++) {
+            // d/dm of u . [m x B + al m x (m x B)] at fixed B
+            gm[3 * i + c] = pre * (bxu[c] + al * (mb * ui[c] + um * bi[c] - 2.0 * ub * mi[c]));
+            // d/dB of the same
+            lb[3 * i + c] = pre * (uxm[c] + al * (um * mi[c] - mm * ui[c]));
+            // X = V_c sum Ms m . B_rms
+            gm[3 * i + c] += lX * o->vc * o->ms[i] * br[3 * i + c];
+            v[3 * i + c] = lb[3 * i + c] / o->ms[i];
+        }
+        X += o->vc * o->ms[i] * (mi[0] * br[3 * i] + mi[1] * br[3 * i + 1] + mi[2] * br[3 * i + 2]);
+    }
+    // field terms are linear in m: demag (symmetric kernel, B = D(Ms m), so the
+    // transpose is Ms D(lb)); exchange (B_i = c_i sum_j w_ij (m_j - m_i), c = 2A/Ms,
+    // transpose sum_j w_ij (c_j lb_j - c_i lb_i)); anisotropy (symmetric per cell)
+    demag_field(o, v.data(), D.data());       // D(Ms * (lb / Ms)) = D(lb)
+    const double d2[3] = {o->dx * o->dx, o->dy * o->dy, o->dz * o->dz};
+    const int nb6[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+    for (int z = 0; z < o->nz; z++)
+        for (int y = 0; y < o->ny; y++)
+            for (int x = 0; x < o->nx; x++) {
+                long i = cidx(o, x, y, z);
+                if (o->ms[i] <= 0) continue;
+                double ci = 2.0 * o->Aex / o->ms[i];
+                for (int q = 0; q < 6; q++) {
+                    int xn = x + nb6[q][0], yn = y + nb6[q][1], zn = z + nb6[q][2];
+                    if (xn < 0 || yn < 0 || zn < 0 || xn >= o->nx || yn >= o->ny || zn >= o->nz) continue;
+                    long j = cidx(o, xn, yn, zn);
+                    if (o->ms[j] <= 0) continue;
+                    double cj = 2.0 * o->Aex / o->ms[j];
+                    for (int c = 0; c < 3; c++) gm[3 * i + c] += (cj * lb[3 * j + c] - ci * lb[3 * i + c]) / d2[q / 2];
+                }
+                double lu = lb[3 * i] * o->u[0] + lb[3 * i + 1] * o->u[1] + lb[3 * i + 2] * o->u[2];
+                for (int c = 0; c < 3; c++)
+                    gm[3 * i + c] += o->ms[i] * D[3 * i + c] + 2.0 * o->Ku / o->ms[i] * lu * o->u[c];
+            }
+    double pb = 0, sb[3] = {0, 0, 0};
+    for (long i = 0; i < n; i++)
+        for (int c = 0; c < 3; c++) { pb += br[3 * i + c] * lb[3 * i + c]; sb[c] += lb[3 * i + c]; }
+    const double kap = o->kappa[0], w = o->wc[0];
+    // d alpha/dt = -(kappa + i omega) alpha + i X / hbar as a real pair; B_cav = B_rms 2 Re alpha
+    ga[0] = -kap * nu[0] - w * nu[1] + 2.0 * pb;
+    ga[1] = w * nu[0] - kap * nu[1];
+    for (int c = 0; c < 3; c++) dp[c] = sb[c];
+    dp[3] = G * pb + lX * X;
+    dp[4] = nu[0] * a.imag() - nu[1] * a.real();
+    dp[5] = -nu[0] * a.real() - nu[1] * a.imag();
+}
+
+// J = w . <m>(T) + wn |alpha(T)|^2 after nsteps RK4 steps of dt from the current
+// state (E-mode, cavity mode 0 only, no drive), and its gradient by the
+// discrete adjoint of the RK4 map with the per-step renormalisation:
+// grad = dJ/d(B_ext x, y, z; eta; omega_c; kappa) and, if gm0 is given,
+// dJ/dm0 (per cell).  The state is left at step nsteps.  Returns J.
+double or_adjoint_rk4(oracle* o, long nsteps, double dt, const double* wv, double wn, double* grad,
+                      double* gm0) {
+    const long n3 = 3 * o->n;
+    std::vector<std::vector<double>> ms_ck((size_t)nsteps + 1);
+    std::vector<cplx> a_ck((size_t)nsteps + 1);
+    for (long q = 0; q < nsteps; q++) {
+        ms_ck[q] = o->m;
+        a_ck[q] = o->a[0];
+        step_rk4(o, dt);
+    }
+    long nm = 0;
+    double avg[3] = {0, 0, 0};
+    for (long i = 0; i < o->n; i++)
+        if (o->ms[i] > 0) { nm++; for (int c = 0; c < 3; c++) avg[c] += o->m[3 * i + c]; }
+    double J = wn * std::norm(o->a[0]);
+    for (int c = 0; c < 3; c++) J += wv[c] * (nm ? avg[c] / nm : 0.0);
+    // terminal cotangents
+    std::vector<double> lm(n3, 0.0);
+    for (long i = 0; i < o->n; i++)
+        if (o->ms[i] > 0) for (int c = 0; c < 3; c++) lm[3 * i + c] = wv[c] / nm;
+    double la[2] = {2.0 * wn * o->a[0].real(), 2.0 * wn * o->a[0].imag()};
+    for (int c = 0; c < 6; c++) grad[c] = 0;
+    const double cc[4] = {0.0, 0.5, 0.5, 1.0}, bb[4] = {1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6};
+    std::vector<double> Y[4], K[4], lk[4], g(n3), mp(n3), lp(n3);
+    cplx Ya[4], Ka[4];
+    double lka[4][2];
+    for (int s = 0; s < 4; s++) { Y[s].resize(n3); K[s].resize(n3); lk[s].resize(n3); }
+    for (long q = nsteps - 1; q >= 0; q--) {
+        // recompute the stages of step q from its checkpoint
+        const std::vector<double>& m0 = ms_ck[q];
+        const cplx a0 = a_ck[q];
+        for (int s = 0; s < 4; s++) {
+            Ya[s] = a0;
+            for (long e = 0; e < n3; e++) Y[s][e] = m0[e];
+            if (s > 0) {
+                for (long e = 0; e < n3; e++) Y[s][e] += cc[s] * dt * K[s - 1][e];
+                Ya[s] += cc[s] * dt * Ka[s - 1];
+            }
+            cplx aa[OR_MAX_MODES] = {Ya[s], 0, 0, 0}, da[OR_MAX_MODES];
+            rhs(o, Y[s].data(), aa, 0.0, K[s].data(), da, nullptr, 0.0);
+            Ka[s] = da[0];
+        }
+        for (long e = 0; e < n3; e++) mp[e] = m0[e] + dt * (bb[0] * K[0][e] + bb[1] * K[1][e] + bb[2] * K[2][e] + bb[3] * K[3][e]);
+        // renormalisation m = m'/|m'|: cotangent (lm - (lm.mh) mh) / |m'|
+        for (long i = 0; i < o->n; i++) {
+            double r = std::sqrt(mp[3 * i] * mp[3 * i] + mp[3 * i + 1] * mp[3 * i + 1] + mp[3 * i + 2] * mp[3 * i + 2]);
+            if (o->ms[i] <= 0 || r <= 0) { for (int c = 0; c < 3; c++) lp[3 * i + c] = 0; continue; }
+            double h[3] = {mp[3 * i] / r, mp[3 * i + 1] / r, mp[3 * i + 2] / r};
+            double d = lm[3 * i] * h[0] + lm[3 * i + 1] * h[1] + lm[3 * i + 2] * h[2];
+            for (int c = 0; c < 3; c++) lp[3 * i + c] = (lm[3 * i + c] - d * h[c]) / r;
+        }
+        // y' = y + dt sum b_s k_s
+        for (int s = 0; s < 4; s++) {
+            for (long e = 0; e < n3; e++) lk[s][e] = dt * bb[s] * lp[e];
+            lka[s][0] = dt * bb[s] * la[0];
+            lka[s][1] = dt * bb[s] * la[1];
+        }
+        std::vector<double> nl(lp);
+        double nla[2] = {la[0], la[1]};
+        for (int s = 3; s >= 0; s--) {
+            double ga[2], dp[6];
+            rhs_vjp(o, Y[s].data(), Ya[s], lk[s].data(), lka[s], g.data(), ga, dp);
+            for (long e = 0; e < n3; e++) nl[e] += g[e];
+            nla[0] += ga[0];
+            nla[1] += ga[1];
+            if (s > 0) {
+                // Y_s = y + c_s dt k_{s-1}
+                for (long e = 0; e < n3; e++) lk[s - 1][e] += cc[s] * dt * g[e];
+                lka[s - 1][0] += cc[s] * dt * ga[0];
+                lka[s - 1][1] += cc[s] * dt * ga[1];
+            }
+            for (int c = 0; c < 6; c++) grad[c] += dp[c];
+        }
+        lm.swap(nl);
+        la[0] = nla[0];
+        la[1] = nla[1];
+    }
+    if (gm0) std::memcpy(gm0, lm.data(), sizeof(double) * n3);
+    return J;
+}
+
 // Energy terms (J): {Zeeman, demag, exchange, anisotropy, cavity coupling,
 // photon, total}.  The cavity pair is -X_k * 2Re(alpha_k) and
 // hbar omega_c,k |alpha_k|^2 summed over the modes, from the Hamiltonian
