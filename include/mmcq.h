@@ -232,6 +232,23 @@ int mmcq_set_recording(mmcq_t* h, int every);
 int mmcq_get_mavg_history(mmcq_t* h, int inst, double* out, int64_t max, int64_t* n);
 int mmcq_spectrum(mmcq_t* h, int inst, int comp, const double* omega, int nw, double* out);
 
+/* ---- gradients: discrete adjoint of the RK4 path ------------------------
+ * mmcq_adjoint_rk4 runs nsteps RK4 steps of dt from the current state of
+ * every instance (E-mode, cavity mode 0 only, no drive), keeping a
+ * checkpoint of every step on the device (16 B x cells x instances per
+ * step), then sweeps back through the discrete adjoint of each step
+ * (stages recomputed from the checkpoint, the renormalisation included).
+ * Objective per instance b:  J_b = w . <m>(T) + wn |alpha(T)|^2, <m> the mean
+ * over magnetised cells.  J (host, B doubles, may be NULL) receives J_b;
+ * grad (host, B x 6 doubles) receives dJ_b/d(B_ext x, y, z; eta; omega_c;
+ * kappa), eta the scale of the instance's B_rms map at eta = 1 (so
+ * dJ/dg = grad[3] / g when B_rms comes from g).  The demag convolution of
+ * the adjoint field reuses the forward passes (the tensor is symmetric).
+ * The state is left at step nsteps; the integrator setting is restored.
+ * MMCQ_ERR_UNSUPPORTED in P-mode, with more than one mode or with the drive
+ * on; MMCQ_ERR_ARG for nsteps < 1, dt <= 0 or a NULL w / grad. */
+int mmcq_adjoint_rk4(mmcq_t* h, int64_t nsteps, double dt, const double w[3], double wn, double* J, double* grad);
+
 /* ---- checkpoint / resume -----------------------------------------------
  * A snapshot holds everything that evolves in time or was set per instance:
  * for every instance the accepted m, the first Dormand-Prince stage kept for

@@ -100,6 +100,7 @@ PROTOTYPES = {
     "mmcq_set_recording": (ctypes.c_int, [_H, ctypes.c_int]),
     "mmcq_get_mavg_history": (ctypes.c_int, [_H, ctypes.c_int, _DP, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "mmcq_spectrum": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, _DP, ctypes.c_int, _DP]),
+    "mmcq_adjoint_rk4": (ctypes.c_int, [_H, ctypes.c_int64, ctypes.c_double, _DP, ctypes.c_double, _DP, _DP]),
     "mmcq_get_state": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "mmcq_group_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(_H), ctypes.c_int,
                                          ctypes.c_int]),
@@ -352,6 +353,16 @@ class Sim:
         self._ck(self._lib.mmcq_spectrum(self._h, inst, int(comp), w.ctypes.data_as(_DP), w.size,
                                          out.ctypes.data_as(_DP)))
         return out[0::2] + 1j * out[1::2]
+
+    def adjoint_rk4(self, nsteps, dt, w=(0.0, 0.0, 0.0), wn=0.0):
+        """J_b = w . <m>(T) + wn |alpha(T)|^2 after nsteps RK4 steps and its gradient by the
+        discrete adjoint: (J (B,), dJ/d(Bx, By, Bz, eta, omega_c, kappa) (B, 6))."""
+        wv = np.ascontiguousarray(np.asarray(w, dtype=np.float64).reshape(3))
+        J = np.zeros(self.batch)
+        g = np.zeros((self.batch, 6))
+        self._ck(self._lib.mmcq_adjoint_rk4(self._h, int(nsteps), float(dt), wv.ctypes.data_as(_DP), float(wn),
+                                            J.ctypes.data_as(_DP), g.ctypes.data_as(_DP)))
+        return J, g
 
     def get_state(self) -> bytes:
         """Snapshot of every instance (checkpoint), as bytes."""

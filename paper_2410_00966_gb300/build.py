@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libmmcq.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["stage.cu", "xinv.cu", "col.cu", "tensor.cu", "capi.cu", "noalloc.cu"]
+SOURCES = ["stage.cu", "xinv.cu", "col.cu", "tensor.cu", "capi.cu", "noalloc.cu", "adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

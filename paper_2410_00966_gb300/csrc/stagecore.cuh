@@ -295,11 +295,14 @@ struct CellUpdate {
     float dt, bex, bey, bez, D;
     bool want_anis, want_zee, want_cav, field_only;
     int K, s, mode, nm;
-    long long cb;
+    long long cb, fb;    // first cell of this instance; of the launch's first instance (field output)
     float4* kout;
 
+    // fb_: first cell of the launch's first instance; a field evaluation writes
+    // fout[i - fb_], so a launch over several instances fills [instances][N]
     __device__ __forceinline__ void init(const Buffers& Bf, const StageArgs& A, const InstState& st,
-                                         const InstParams& ip, const double* gam, float drive, long long cb_) {
+                                         const InstParams& ip, const double* gam, float drive, long long cb_,
+                                         long long fb_) {
         nm = NM == 1 ? 1 : A.nmodes;
 #pragma unroll
         for (int q = 0; q < NM; q++) {
@@ -314,6 +317,7 @@ struct CellUpdate {
         field_only = A.field_only != 0;
         K = A.kind; s = A.stage; mode = A.mode;
         cb = cb_;
+        fb = fb_;
         const int k1slot = st.k1slot;
         kout = K == KIND_RK4 ? (s < 3 ? Bf.k[s] : nullptr)
                              : (s < 6 ? Bf.k[s == 0 ? k1slot : s] : Bf.k[k1slot == 0 ? 6 : 0]);
@@ -350,7 +354,7 @@ struct CellUpdate {
             }
         }
         if (field_only) {
-            Bf.fout[i - cb] = make_float4(Bx, By, Bz, 0.f);
+            Bf.fout[i - fb] = make_float4(Bx, By, Bz, 0.f);
             return;
         }
         float cx = m.y * Bz - m.z * By, cy = m.z * Bx - m.x * Bz, cz = m.x * By - m.y * Bx;

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
 
     const bool want_demag = A.terms & 1, want_exch = A.terms & 2;
     CellUpdate<NM> cu;
-    cu.init(Bf, A, st, ip, s_gamma, s_drive, cb);
+    cu.init(Bf, A, st, ip, s_gamma, s_drive, cb, (long long)A.inst0 * P.N);
     const long long pl = (long long)nx * P.ny;
     double xacc[NM];
 #pragma unroll
