@@ -282,24 +282,34 @@ __global__ void __launch_bounds__(192, 5) k_zconv2(Plan Pl, Buffers Bf, StageArg
 
     // product at every (kz, g, tx) point of the block: symmetric kernel
     // (xx, yy, zz, xy, xz, yz) at (|kz|, |ky|, kx); xy is odd in ky, xz in kz,
-    // yz in both
+    // yz in both.  The block has 2 W = 6 G TX threads, so a thread keeps its
+    // (g, tx) point and steps kz by 6.
     const int GT = C.G * TX;                      // power of two
     const int lgt = __ffs(GT) - 1;
     const long long zs = (long long)Pl.hyk * Pl.NT * TX * 6;
-    for (int idx = threadIdx.x; idx < P * GT; idx += 2 * W) {
-        const int kz = idx >> lgt, p = idx & (GT - 1);
-        const int gg = p >> lt, xx = p & (TX - 1);
-        const int ky = o0 + gg, kx = t * TX + xx;
-        float2* pm = sm + kz * W + gg * 3 * TX + xx;
-        float2 mx = pm[0], my = pm[TX], mz = pm[2 * TX];
+    const int p = threadIdx.x & (GT - 1);
+    const int gg = p >> lt, xx = p & (TX - 1);
+    const int ky = o0 + gg, kx = t * TX + xx;
+    const bool live = kx < Pl.hx;
+    const bool ny_ = ky > Pl.py / 2;
+    const int kyr = ny_ ? Pl.py - ky : ky;
+    const float sy = ny_ ? -1.f : 1.f;
+    const float* Kb = Bf.kern + ((long long)kyr * Pl.NT * TX + (live ? kx : 0)) * 6;
+    float2* pm0 = sm + gg * 3 * TX + xx;
+    const int kz0 = threadIdx.x >> lgt;           // 0 .. 5
+#pragma unroll
+    for (int it = 0; it < (P + 5) / 6; it++) {
+        const int kz = kz0 + 6 * it;
+        if (kz >= P) break;
+        float2* pm = pm0 + kz * W;
+        const float2 mx = pm[0], my = pm[TX], mz = pm[2 * TX];
         float2 hx = make_float2(0.f, 0.f), hy = hx, hz = hx;
-        if (kx < Pl.hx) {
-            const bool ny_ = ky > Pl.py / 2, nz_ = kz > P / 2;
-            const int kyr = ny_ ? Pl.py - ky : ky, kzr = nz_ ? P - kz : kz;
-            const float2* Kp =
-                reinterpret_cast<const float2*>(Bf.kern + kzr * zs + ((long long)kyr * Pl.NT * TX + kx) * 6);
+        if (live) {
+            const bool nz_ = kz > P / 2;
+            const int kzr = nz_ ? P - kz : kz;
+            const float2* Kp = reinterpret_cast<const float2*>(Kb + kzr * zs);
             const float2 k0 = __ldg(Kp), k1 = __ldg(Kp + 1), k2 = __ldg(Kp + 2);
-            const float sy = ny_ ? -1.f : 1.f, sz = nz_ ? -1.f : 1.f;
+            const float sz = nz_ ? -1.f : 1.f;
             const float Kxx = k0.x, Kyy = k0.y, Kzz = k1.x, Kxy = sy * k1.y, Kxz = sz * k2.x, Kyz = sy * sz * k2.y;
             hx = make_float2(Kxx * mx.x + Kxy * my.x + Kxz * mz.x, Kxx * mx.y + Kxy * my.y + Kxz * mz.y);
             hy = make_float2(Kxy * mx.x + Kyy * my.x + Kyz * mz.x, Kxy * mx.y + Kyy * my.y + Kyz * mz.y);
