@@ -39,6 +39,16 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xfwd(Pla
     const int nr = min(P.R, P.nrows - row0);
     const int ld = xpass_ld(P.R);
     const long long base = (long long)b * P.N + (long long)row0 * nx;
+    const float4* m0 = Bf.m[st.mcur] + base;
+    StageInput si;
+    si.init(Bf, A, st, base);
+    if (threadIdx.x == 0) {
+        // the block's rows of m0 and of every k it combines: in flight while
+        // the shared tables are set up
+        const unsigned bytes = (unsigned)(nr * nx * sizeof(float4));
+        prefetch_l2(m0, bytes);
+        si.prefetch(Bf, bytes);
+    }
     float2* zs = sm;
     float2* stw = sm + L * ld;                 // exp(-2 pi i e / px), e < px
     const int tws = P.twn / P.px;
@@ -47,9 +57,7 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xfwd(Pla
     for (int i = (nx >> 1) * ld + threadIdx.x; i < L * ld; i += blockDim.x) zs[i] = make_float2(0.f, 0.f);
     __syncthreads();
 
-    const float4* m0 = Bf.m[st.mcur] + base;
-    StageInput si;
-    si.init(Bf, A, st, base);
+
     for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) {
         float4 v = m0[i];
         si.apply(Bf, v, i);

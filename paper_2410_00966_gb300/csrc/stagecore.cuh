@@ -258,6 +258,14 @@ struct StageInput {
         e6 = Bf.e6 + base;
     }
 
+    // Ask L2 for the k rows this block will read ([base, base + bytes) of each).
+    __device__ __forceinline__ void prefetch(const Buffers& Bf, unsigned bytes) const {
+        if (!form) return;
+#pragma unroll
+        for (int q = 0; q < MAX_STAGES - 1; q++)
+            if (kw[q] != 0.f || ke[q] != 0.f) prefetch_l2(q == 0 ? k0 : Bf.k[q] + base, bytes);
+    }
+
     // v = m0[i] on entry; m_s on return (written to out, and e6 at the last DP stage)
     __device__ __forceinline__ void apply(const Buffers& Bf, float4& v, int i) const {
         if (!form) return;
