@@ -45,7 +45,8 @@ enum {
     MMCQ_ERR_ARG = -1,         /* invalid argument (sizes, pointers, indices) */
     MMCQ_ERR_UNSUPPORTED = -2, /* valid request this build does not handle (e.g. padded size > 4096) */
     MMCQ_ERR_CUDA = -3,        /* a CUDA runtime call failed; see mmcq_last_error */
-    MMCQ_ERR_NUMERIC = -4,     /* non-finite m / field, or adaptive step underflow */
+    MMCQ_ERR_NUMERIC = -4,     /* non-finite m / field (RK4), or adaptive step underflow (DP45: a
+                                  non-finite trial attempt is rejected and the step shrunk) */
     MMCQ_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
     MMCQ_ERR_STATE = -6        /* call not valid in the current state */
 };

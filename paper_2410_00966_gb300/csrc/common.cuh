@@ -89,6 +89,7 @@ struct InstState {
     int k1slot;             // DP45: k buffer holding stage 1 (FSAL)
     int have_k1;            // DP45: stage 1 valid for the current state
     int done;               // reached t_end
+    int poison;             // DP45: a stage of the current attempt was not finite
 };
 
 // Device buffers of one handle.

@@ -109,8 +109,8 @@ static __device__ void finish_stage(const Plan& P, const Material& mat, const St
     int accept = 1;
     if (K == KIND_DP45) {
         float tol = A.tol;
+        if (s.poison || !(errmax == errmax)) errmax = INFINITY;
         accept = errmax <= tol;
-        if (!(errmax == errmax)) { accept = 0; atomicOr(flags, FLAG_NAN); }
     }
     if (accept) {
         if (K == KIND_RK4) {
@@ -168,6 +168,7 @@ static __device__ void finish_stage(const Plan& P, const Material& mat, const St
         f = fmin(5.0, fmax(0.2, f));
         double nd = dt * f;
         s.err = err;
+        s.poison = 0;
         if (s.t_end > 0.0) {
             if (s.t >= s.t_end * (1.0 - 1e-14)) s.done = 1;
             else if (s.t + nd > s.t_end) nd = s.t_end - s.t;
@@ -398,7 +399,9 @@ struct CellUpdate {
                 float4 e = Bf.e6[i];
                 float c7 = c_ef[6] * dt;
                 float exx = e.x + c7 * kk.x, eyy = e.y + c7 * kk.y, ezz = e.z + c7 * kk.z;
-                emax = fmaxf(emax, sqrtf(exx * exx + eyy * eyy + ezz * ezz));
+                const float en = sqrtf(exx * exx + eyy * eyy + ezz * ezz);
+                if (!(en <= 3.0e38f)) bad = true;    // fmaxf would drop a NaN
+                emax = fmaxf(emax, en);
             }
         }
         // per-cell products in FP32, accumulated in FP64 (the sum over cells is
@@ -438,7 +441,13 @@ template <bool REC, int NM>
 static __device__ void stage_epilogue(const Plan& P, const Material& mat, const Buffers& Bf, const StageArgs& A,
                                       int b, int part, int nparts, const double (&xacc)[NM], float emax, bool bad,
                                       double* s_red, float* s_redf, int* s_last, const double* macc) {
-    if (bad) atomicOr(Bf.flags, FLAG_NAN);
+    // RK4: a non-finite torque is an error.  DP45: it marks the attempt, which
+    // is then rejected with the smallest step factor (an overflowing trial
+    // step); a state that stays non-finite ends in step-size underflow.
+    if (bad) {
+        if (A.kind == KIND_DP45) atomicOr(&Bf.st[b].poison, 1);
+        else atomicOr(Bf.flags, FLAG_NAN);
+    }
     const int nm = NM == 1 ? 1 : A.nmodes;
     double xb[NM];
 #pragma unroll
