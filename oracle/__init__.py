@@ -108,7 +108,7 @@ def _load():
         "or_rhs_modes": (None, [p, dp, dp, d, dp, dp]),
         "or_cavity_X_mode": (d, [p, dp, i]),
         "or_max_modes": (i, []),
-        "or_adjoint_rk4": (d, [p, l, d, dp, d, dp, dp]),
+        "or_adjoint_rk4": (d, [p, l, d, dp, d, d, l, dp, dp, dp]),
         "or_drive_factor": (d, [p, d]),
         "or_set_recording": (None, [p, i]),
         "or_mavg_history": (l, [p, dp, l]),
@@ -350,14 +350,16 @@ class Oracle:
     def cavity_X_mode(self, m, k):
         return self._lib.or_cavity_X_mode(self._h, _dp(_f64(m, 3 * self.n)), k)
 
-    def adjoint_rk4(self, nsteps, dt, w=(0.0, 0.0, 0.0), wn=0.0):
-        """J = w . <m>(T) + wn |alpha(T)|^2 after nsteps RK4 steps (E-mode, mode 0) and its
-        gradient by the discrete adjoint: (J, dJ/d(Bx, By, Bz, eta, omega_c, kappa), dJ/dm0)."""
+    def adjoint_rk4(self, nsteps, dt, w=(0.0, 0.0, 0.0), wn=0.0, wavg=0.0, window=1):
+        """J = w . <m>(T) + wn |alpha(T)|^2 + wavg * (mean |alpha_n|^2 over the last `window` steps)
+        after nsteps RK4 steps (E-mode, mode 0) and its gradient by the discrete adjoint:
+        (J, dJ/d(Bx, By, Bz, eta, omega_c, kappa), dJ/dm0 (n, 3), dJ/dMs (n,))."""
         wv = _f64(w, 3)
         g = np.zeros(6)
         gm = np.zeros((self.n, 3))
-        J = self._lib.or_adjoint_rk4(self._h, nsteps, dt, _dp(wv), wn, _dp(g), _dp(gm))
-        return J, g, gm
+        gs = np.zeros(self.n)
+        J = self._lib.or_adjoint_rk4(self._h, nsteps, dt, _dp(wv), wn, wavg, window, _dp(g), _dp(gm), _dp(gs))
+        return J, g, gm, gs
 
     def set_drive(self, amp, omega_cut, t0=0.0):
         """Appendix C excitation: B_ext += amp * B_rms,i * sinc(omega_cut (t - t0)); amp = 0 turns it off."""

@@ -952,7 +952,7 @@ void or_demag_at(const oracle* o, const double* m, const long* cells, long nc, d
 // B_rms map (B_rms -> eta B_rms, at eta = 1).  Written from Eq. (llg), the
 // field terms of Sec. 2.1, Eq. (bcav) and the amplitude equation of Sec. 2.2.
 static void rhs_vjp(const oracle* o, const double* m, cplx a, const double* u, const double* nu, double* gm,
-                    double* ga, double* dp) {
+                    double* ga, double* dp, double* gms) {
     const long n = o->n;
     const double G = 2.0 * a.real();
     double Gam[OR_MAX_MODES] = {G, 0, 0, 0};
@@ -1011,6 +1011,22 @@ static void rhs_vjp(const oracle* o, const double* m, cplx a, const double* u, c
     double pb = 0, sb[3] = {0, 0, 0};
     for (long i = 0; i < n; i++)
         for (int c = 0; c < 3; c++) { pb += br[3 * i + c] * lb[3 * i + c]; sb[c] += lb[3 * i + c]; }
+    // Ms_i (mask fixed, B_rms map fixed) enters through the demag input Ms m,
+    // the 1/Ms_i of exchange and anisotropy, and X:
+    // dJ/dMs_i += m_i . D(lb)_i - lb_i . (B_exch,i + B_anis,i) / Ms_i + lX V_c m_i . B_rms,i
+    if (gms) {
+        std::vector<double> Bx(3 * n), Ba(3 * n);
+        exchange_field(o, m, Bx.data());
+        anis_field(o, m, Ba.data());
+        for (long i = 0; i < n; i++) {
+            if (o->ms[i] <= 0) continue;
+            double v = 0;
+            for (int c = 0; c < 3; c++)
+                v += m[3 * i + c] * D[3 * i + c] - lb[3 * i + c] * (Bx[3 * i + c] + Ba[3 * i + c]) / o->ms[i] +
+                     lX * o->vc * m[3 * i + c] * br[3 * i + c];
+            gms[i] += v;
+        }
+    }
     const double kap = o->kappa[0], w = o->wc[0];
     // d alpha/dt = -(kappa + i omega) alpha + i X / hbar as a real pair; B_cav = B_rms 2 Re alpha
     ga[0] = -kap * nu[0] - w * nu[1] + 2.0 * pb;
@@ -1021,39 +1037,51 @@ static void rhs_vjp(const oracle* o, const double* m, cplx a, const double* u, c
     dp[5] = -nu[0] * a.real() - nu[1] * a.imag();
 }
 
-// J = w . <m>(T) + wn |alpha(T)|^2 after nsteps RK4 steps of dt from the current
-// state (E-mode, cavity mode 0 only, no drive), and its gradient by the
-// discrete adjoint of the RK4 map with the per-step renormalisation:
-// grad = dJ/d(B_ext x, y, z; eta; omega_c; kappa) and, if gm0 is given,
-// dJ/dm0 (per cell).  The state is left at step nsteps.  Returns J.
-double or_adjoint_rk4(oracle* o, long nsteps, double dt, const double* wv, double wn, double* grad,
-                      double* gm0) {
+// Objective after nsteps RK4 steps of dt from the current state (E-mode,
+// cavity mode 0 only, no drive):
+//   J = w . <m>(T) + wn |alpha(T)|^2 + wavg (1/W) sum_{n = N-W+1}^{N} |alpha_n|^2,
+// the last term the photon number averaged over the last W steps.  Gradient
+// by the discrete adjoint of the RK4 map with the per-step renormalisation:
+// grad = dJ/d(B_ext x, y, z; eta; omega_c; kappa); if gm0 is given dJ/dm0 (per
+// cell), if gms is given dJ/dMs (per cell, mask and B_rms map held fixed).
+// The state is left at step nsteps.  Returns J.
+double or_adjoint_rk4(oracle* o, long nsteps, double dt, const double* wv, double wn, double wavg, long window,
+                      double* grad, double* gm0, double* gms) {
     const long n3 = 3 * o->n;
     std::vector<std::vector<double>> ms_ck((size_t)nsteps + 1);
     std::vector<cplx> a_ck((size_t)nsteps + 1);
-    for (long q = 0; q < nsteps; q++) {
+    for (long q = 0; q <= nsteps; q++) {
         ms_ck[q] = o->m;
         a_ck[q] = o->a[0];
-        step_rk4(o, dt);
+        if (q < nsteps) step_rk4(o, dt);
     }
+    if (window < 1) window = 1;
+    if (window > nsteps) window = nsteps;
     long nm = 0;
     double avg[3] = {0, 0, 0};
     for (long i = 0; i < o->n; i++)
         if (o->ms[i] > 0) { nm++; for (int c = 0; c < 3; c++) avg[c] += o->m[3 * i + c]; }
     double J = wn * std::norm(o->a[0]);
     for (int c = 0; c < 3; c++) J += wv[c] * (nm ? avg[c] / nm : 0.0);
+    for (long q = nsteps - window + 1; q <= nsteps; q++) J += wavg / window * std::norm(a_ck[q]);
     // terminal cotangents
     std::vector<double> lm(n3, 0.0);
     for (long i = 0; i < o->n; i++)
         if (o->ms[i] > 0) for (int c = 0; c < 3; c++) lm[3 * i + c] = wv[c] / nm;
     double la[2] = {2.0 * wn * o->a[0].real(), 2.0 * wn * o->a[0].imag()};
     for (int c = 0; c < 6; c++) grad[c] = 0;
+    if (gms) for (long i = 0; i < o->n; i++) gms[i] = 0;
     const double cc[4] = {0.0, 0.5, 0.5, 1.0}, bb[4] = {1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6};
     std::vector<double> Y[4], K[4], lk[4], g(n3), mp(n3), lp(n3);
     cplx Ya[4], Ka[4];
     double lka[4][2];
     for (int s = 0; s < 4; s++) { Y[s].resize(n3); K[s].resize(n3); lk[s].resize(n3); }
     for (long q = nsteps - 1; q >= 0; q--) {
+        // the averaged photon number sees alpha at step q + 1
+        if (q + 1 >= nsteps - window + 1) {
+            la[0] += 2.0 * wavg / window * a_ck[q + 1].real();
+            la[1] += 2.0 * wavg / window * a_ck[q + 1].imag();
+        }
         // recompute the stages of step q from its checkpoint
         const std::vector<double>& m0 = ms_ck[q];
         const cplx a0 = a_ck[q];
@@ -1087,7 +1115,7 @@ double or_adjoint_rk4(oracle* o, long nsteps, double dt, const double* wv, doubl
         double nla[2] = {la[0], la[1]};
         for (int s = 3; s >= 0; s--) {
             double ga[2], dp[6];
-            rhs_vjp(o, Y[s].data(), Ya[s], lk[s].data(), lka[s], g.data(), ga, dp);
+            rhs_vjp(o, Y[s].data(), Ya[s], lk[s].data(), lka[s], g.data(), ga, dp, gms);
             for (long e = 0; e < n3; e++) nl[e] += g[e];
             nla[0] += ga[0];
             nla[1] += ga[1];

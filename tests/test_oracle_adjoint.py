@@ -1,7 +1,8 @@
 """Pins of the oracle's discrete adjoint of the RK4 path (gradients of
-J = w . <m>(T) + wn |alpha(T)|^2 with respect to the bias, the B_rms scale,
-omega_c, kappa and the initial magnetisation): central finite differences of
-the oracle's own forward map in FP64."""
+J = w . <m>(T) + wn |alpha(T)|^2 + wavg <|alpha|^2>_(last W steps) with
+respect to the bias, the B_rms scale, omega_c, kappa, the initial
+magnetisation and the per-cell Ms map): central finite differences of the
+oracle's own forward map in FP64."""
 import math
 
 import numpy as np
@@ -12,6 +13,7 @@ import oracle
 NX, NY, NZ, D = 5, 4, 2, 4e-9
 W = (0.3, -0.7, 0.2)
 WN = 5.0
+WAVG, WINDOW = 3.0, 12
 STEPS, DT = 40, 2e-13
 
 
@@ -37,7 +39,7 @@ def _make(bias=(0.05, 0.01, 0.0), eta=1.0, wc=2 * math.pi * 7e9, kappa=2 * math.
 
 def _J(**kw):
     o, _ = _make(**kw)
-    J, _, _ = o.adjoint_rk4(STEPS, DT, W, WN)
+    J = o.adjoint_rk4(STEPS, DT, W, WN, WAVG, WINDOW)[0]
     return J
 
 
@@ -52,7 +54,7 @@ def _ms_map():
 def test_parameter_gradients_match_finite_differences(masked):
     ms = _ms_map() if masked else None
     o, _ = _make(ms=ms)
-    J, g, _ = o.adjoint_rk4(STEPS, DT, W, WN)
+    J, g, _, _ = o.adjoint_rk4(STEPS, DT, W, WN, WAVG, WINDOW)
     base = dict(bias=(0.05, 0.01, 0.0), eta=1.0, wc=2 * math.pi * 7e9, kappa=2 * math.pi * 3e8)
     checks = []
     for c in range(3):
@@ -73,7 +75,7 @@ def test_parameter_gradients_match_finite_differences(masked):
 
 def test_initial_state_gradient_matches_finite_differences():
     o, m0 = _make()
-    _, _, gm = o.adjoint_rk4(STEPS, DT, W, WN)
+    _, _, gm, _ = o.adjoint_rk4(STEPS, DT, W, WN, WAVG, WINDOW)
     # set_m normalises its input, so a perturbation of that input sees the
     # tangential part of dJ/dm0 (the derivative of m/|m| at |m| = 1 is the projector)
     gm = gm - np.sum(gm * m0, axis=1)[:, None] * m0
@@ -86,6 +88,33 @@ def test_initial_state_gradient_matches_finite_differences():
         mm[i, c] -= h
         fd = (_J(m0=mp) - _J(m0=mm)) / (2 * h)
         assert abs(gm[i, c] - fd) <= 1e-5 * abs(fd) + 1e-9, (i, c, gm[i, c], fd)
+
+
+def test_ms_map_gradient_matches_finite_differences():
+    ms = _ms_map()
+    o, _ = _make(ms=ms)
+    _, _, _, gs = o.adjoint_rk4(STEPS, DT, W, WN, WAVG, WINDOW)
+    assert gs[3] == 0.0                                  # empty cells carry no gradient
+    for i in (0, 8, 13, 29, 39):
+        h = 1e-4 * ms[i]
+        mp, mm = ms.copy(), ms.copy()
+        mp[i] += h
+        mm[i] -= h
+        fd = (_J(ms=mp) - _J(ms=mm)) / (2 * h)
+        assert abs(gs[i] - fd) <= 1e-4 * abs(fd) + 1e-12 * np.abs(gs).max(), (i, gs[i], fd)
+
+
+def test_averaged_photon_term_alone():
+    # with only the averaged term, J is the mean photon number over the window
+    o, _ = _make()
+    J, g, _, _ = o.adjoint_rk4(STEPS, DT, (0, 0, 0), 0.0, 1.0, WINDOW)
+    p, _ = _make()
+    ns = []
+    for _ in range(STEPS):
+        p.step(1, DT)
+        ns.append(p.cavity()["n_photon"])
+    assert abs(J - np.mean(ns[-WINDOW:])) <= 1e-12 * J
+    assert abs(g[4]) > 0
 
 
 def test_adjoint_leaves_the_forward_state():
