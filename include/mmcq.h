@@ -234,21 +234,39 @@ int mmcq_get_mavg_history(mmcq_t* h, int inst, double* out, int64_t max, int64_t
 int mmcq_spectrum(mmcq_t* h, int inst, int comp, const double* omega, int nw, double* out);
 
 /* ---- gradients: discrete adjoint of the RK4 path ------------------------
+ * Objective per instance b (mode 0 amplitude alpha, <m> the mean over the
+ * magnetised cells, alpha_n the amplitude after step n of N):
+ *   J_b = w . <m>(T) + wn |alpha_N|^2 + wavg (1/W) sum_{n = N-W+1}^{N} |alpha_n|^2,
+ * the last term the photon number averaged over the final W = window steps
+ * (times hbar omega_c: the photon energy).
+ *
  * mmcq_adjoint_rk4 runs nsteps RK4 steps of dt from the current state of
  * every instance (E-mode, cavity mode 0 only, no drive), keeping a
- * checkpoint of every step on the device (16 B x cells x instances per
- * step), then sweeps back through the discrete adjoint of each step
- * (stages recomputed from the checkpoint, the renormalisation included).
- * Objective per instance b:  J_b = w . <m>(T) + wn |alpha(T)|^2, <m> the mean
- * over magnetised cells.  J (host, B doubles, may be NULL) receives J_b;
- * grad (host, B x 6 doubles) receives dJ_b/d(B_ext x, y, z; eta; omega_c;
- * kappa), eta the scale of the instance's B_rms map at eta = 1 (so
- * dJ/dg = grad[3] / g when B_rms comes from g).  The demag convolution of
- * the adjoint field reuses the forward passes (the tensor is symmetric).
- * The state is left at step nsteps; the integrator setting is restored.
- * MMCQ_ERR_UNSUPPORTED in P-mode, with more than one mode or with the drive
- * on; MMCQ_ERR_ARG for nsteps < 1, dt <= 0 or a NULL w / grad. */
-int mmcq_adjoint_rk4(mmcq_t* h, int64_t nsteps, double dt, const double w[3], double wn, double* J, double* grad);
+ * checkpoint (m and the FP64 instance state) every ckpt_every steps on the
+ * device (0 or 1: every step; memory 16 B x cells x instances per checkpoint
+ * plus ckpt_every states for the segment being replayed), then sweeps back
+ * through the discrete adjoint of each step: the states of a segment are
+ * recomputed from its checkpoint, the four stages of each step from its
+ * state, and the renormalisation is included.
+ *   J (host, B doubles, may be NULL): J_b.
+ *   grad (host, B x 6 doubles): dJ_b/d(B_ext x, y, z; eta; omega_c; kappa), eta
+ *     the scale of the instance's B_rms map at eta = 1 (dJ/dg = grad[3] / g
+ *     when B_rms comes from g).
+ *   grad_ms (host, B x N floats, may be NULL): dJ_b/dMs_i per cell with the
+ *     magnetic mask and the B_rms map held fixed (0 on empty cells).
+ * The demag convolution of the adjoint field reuses the forward passes (the
+ * tensor is symmetric).  The state is left at step nsteps and the integrator
+ * setting is restored.  MMCQ_ERR_UNSUPPORTED in P-mode, with more than one
+ * mode or with the drive on; MMCQ_ERR_ARG for nsteps < 1, dt <= 0,
+ * ckpt_every < 0 or a NULL obj / grad. */
+typedef struct {
+    double w[3];      /* weights of <m>(T) */
+    double wn;        /* weight of |alpha(T)|^2 */
+    double wavg;      /* weight of the photon number averaged over the last `window` steps */
+    int64_t window;
+} mmcq_objective;
+int mmcq_adjoint_rk4(mmcq_t* h, int64_t nsteps, double dt, const mmcq_objective* obj, int64_t ckpt_every,
+                     double* J, double* grad, float* grad_ms);
 
 /* ---- checkpoint / resume -----------------------------------------------
  * A snapshot holds everything that evolves in time or was set per instance:

@@ -61,6 +61,11 @@ class mmcq_info(ctypes.Structure):
                 ("launches_per_step", ctypes.c_int64)]
 
 
+class mmcq_objective(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_double * 3), ("wn", ctypes.c_double), ("wavg", ctypes.c_double),
+                ("window", ctypes.c_int64)]
+
+
 class mmcq_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
                 ("bytes", ctypes.c_double)]
@@ -100,7 +105,8 @@ PROTOTYPES = {
     "mmcq_set_recording": (ctypes.c_int, [_H, ctypes.c_int]),
     "mmcq_get_mavg_history": (ctypes.c_int, [_H, ctypes.c_int, _DP, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "mmcq_spectrum": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, _DP, ctypes.c_int, _DP]),
-    "mmcq_adjoint_rk4": (ctypes.c_int, [_H, ctypes.c_int64, ctypes.c_double, _DP, ctypes.c_double, _DP, _DP]),
+    "mmcq_adjoint_rk4": (ctypes.c_int, [_H, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(mmcq_objective),
+                                        ctypes.c_int64, _DP, _DP, ctypes.POINTER(ctypes.c_float)]),
     "mmcq_get_state": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "mmcq_group_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(_H), ctypes.c_int,
                                          ctypes.c_int]),
@@ -354,15 +360,19 @@ class Sim:
                                          out.ctypes.data_as(_DP)))
         return out[0::2] + 1j * out[1::2]
 
-    def adjoint_rk4(self, nsteps, dt, w=(0.0, 0.0, 0.0), wn=0.0):
-        """J_b = w . <m>(T) + wn |alpha(T)|^2 after nsteps RK4 steps and its gradient by the
-        discrete adjoint: (J (B,), dJ/d(Bx, By, Bz, eta, omega_c, kappa) (B, 6))."""
-        wv = np.ascontiguousarray(np.asarray(w, dtype=np.float64).reshape(3))
+    def adjoint_rk4(self, nsteps, dt, w=(0.0, 0.0, 0.0), wn=0.0, wavg=0.0, window=1, ckpt_every=1,
+                    ms_grad=False):
+        """J_b = w . <m>(T) + wn |alpha(T)|^2 + wavg <|alpha|^2>_(last `window` steps) after nsteps
+        RK4 steps, and its gradient by the discrete adjoint (mmcq_adjoint_rk4):
+        (J (B,), dJ/d(Bx, By, Bz, eta, omega_c, kappa) (B, 6), dJ/dMs (B, N) or None)."""
+        obj = mmcq_objective((ctypes.c_double * 3)(*[float(v) for v in w]), float(wn), float(wavg), int(window))
         J = np.zeros(self.batch)
         g = np.zeros((self.batch, 6))
-        self._ck(self._lib.mmcq_adjoint_rk4(self._h, int(nsteps), float(dt), wv.ctypes.data_as(_DP), float(wn),
-                                            J.ctypes.data_as(_DP), g.ctypes.data_as(_DP)))
-        return J, g
+        gms = np.zeros((self.batch, self.n), dtype=np.float32) if ms_grad else None
+        self._ck(self._lib.mmcq_adjoint_rk4(self._h, int(nsteps), float(dt), ctypes.byref(obj), int(ckpt_every),
+                                            J.ctypes.data_as(_DP), g.ctypes.data_as(_DP),
+                                            None if gms is None else gms.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return J, g, gms
 
     def get_state(self) -> bytes:
         """Snapshot of every instance (checkpoint), as bytes."""
@@ -414,3 +424,45 @@ class Group:
 
     def __del__(self):
         self.close()
+
+
+def cavity_objective(sim, m0, params, nsteps, dt, w=(0.0, 0.0, 0.0), wn=0.0, wavg=0.0, window=1,
+                     ckpt_every=1, profile=None, ms=None):
+    """Differentiable objective (torch.autograd).  From the per-instance initial
+    states m0 ((B, N, 3) array) and parameters params (torch (B, 6): B_ext x, y,
+    z, coupling g, omega_c, kappa, all rad/s or T), and optionally the Ms map ms
+    (torch (N,)): configure `sim` (coupling from g with the given profile shape),
+    run nsteps RK4 steps and return J (torch (B,)) =
+    w . <m>(T) + wn |alpha(T)|^2 + wavg <|alpha|^2>_(last window steps).
+    The backward pass is the discrete adjoint on the device (Sim.adjoint_rk4)."""
+    import torch
+
+    class _Fn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, p, msv):
+            pc = p.detach().cpu().double().numpy()
+            if msv is not None:
+                sim.set_ms_map(msv.detach().cpu().float().numpy())
+            for b in range(sim.batch):
+                sim.set_m(np.asarray(m0[b], dtype=np.float32), inst=b)
+                sim.set_bias(tuple(pc[b, :3]), inst=b)
+                sim.set_cavity(pc[b, 4], pc[b, 5], pc[b, 3], profile=profile, inst=b)
+            J, g, gms = sim.adjoint_rk4(nsteps, dt, w, wn, wavg, window, ckpt_every, ms_grad=msv is not None)
+            gp = g.copy()
+            # B_rms is proportional to g: dJ/dg = dJ/deta / g
+            gsafe = np.where(pc[:, 3] != 0, pc[:, 3], 1.0)
+            gp[:, 3] = np.where(pc[:, 3] != 0, g[:, 3] / gsafe, 0.0)
+            ctx.save_for_backward(torch.from_numpy(gp).to(p.dtype),
+                                  torch.from_numpy(gms).to(p.dtype) if gms is not None else torch.zeros(0))
+            ctx.has_ms = msv is not None
+            return torch.from_numpy(J).to(p.dtype)
+
+        @staticmethod
+        def backward(ctx, gout):
+            gp, gms = ctx.saved_tensors
+            gout = gout.detach().cpu().to(gp.dtype)
+            dp = gout[:, None] * gp
+            dms = (gout[:, None] * gms).sum(0) if ctx.has_ms else None
+            return dp, dms
+
+    return _Fn.apply(params, ms)

@@ -122,9 +122,12 @@ __global__ void k_adj_local(const float4* Y, const float4* Bfield, const float4*
 //   exchange: sum_j w_ij (c_j lB_j - c_i lB_i), c = 2A/Ms, both cells magnetised
 //   anisotropy: (2 Ku / Ms_i)(lB_i . u) u
 // g = gd + those; then nl += g and lk = dtb * lp + cdt * g (next stage's cotangent).
+// With gms: the Ms-map cotangent (mask and B_rms map fixed) accumulates
+//   m_i . D(lB)_i - lB_i . (B_exch,i + B_anis,i) / Ms_i + lX V_c m_i . B_rms,i.
 __global__ void k_adj_combine(const float4* Y, const float4* lB, const float4* Dl, const float4* gd,
                               const float4* lp, float4* nl, float4* lk, Material mat, float dtb, float cdt,
-                              int nx, int ny, int nz) {
+                              int nx, int ny, int nz, float* gms, const double* lX, const InstParams* ip,
+                              const float4* prof) {
     const long long N = (long long)nx * ny * nz;
     const int b = blockIdx.y;
     const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -139,6 +142,7 @@ __global__ void k_adj_combine(const float4* Y, const float4* lB, const float4* D
         const float ci = 1.f / m.w;
         const long long st[3] = {1, nx, (long long)nx * ny};
         const int pos[3] = {x, y, z}, ext[3] = {nx, ny, nz};
+        float hx = 0.f, hy = 0.f, hz = 0.f;      // sum_j exch (m_j - m_i): Ms_i B_exch,i
         for (int a = 0; a < 3; a++) {
             for (int sgn = -1; sgn <= 1; sgn += 2) {
                 const int pn = pos[a] + sgn;
@@ -151,11 +155,24 @@ __global__ void k_adj_combine(const float4* Y, const float4* lB, const float4* D
                 g.x += mat.exch[a] * (cj * lj.x - ci * l.x);
                 g.y += mat.exch[a] * (cj * lj.y - ci * l.y);
                 g.z += mat.exch[a] * (cj * lj.z - ci * l.z);
+                hx += mat.exch[a] * (mj.x - m.x);
+                hy += mat.exch[a] * (mj.y - m.y);
+                hz += mat.exch[a] * (mj.z - m.z);
             }
         }
         const float lu = l.x * mat.u[0] + l.y * mat.u[1] + l.z * mat.u[2];
         const float f = mat.two_ku / m.w * lu;
         g.x += f * mat.u[0]; g.y += f * mat.u[1]; g.z += f * mat.u[2];
+        if (gms) {
+            const float mu = m.x * mat.u[0] + m.y * mat.u[1] + m.z * mat.u[2];
+            const float an = mat.two_ku * mu;    // Ms_i B_anis,i = an u
+            float px = 0.f, py = 1.f, pz = 0.f;
+            if (prof) { const float4 p = prof[c]; px = p.x; py = p.y; pz = p.z; }
+            const float bs = (float)ip[b].brms_scale[0];
+            const float xs = (float)(lX[b] * mat.vc) * bs * (m.x * px + m.y * py + m.z * pz);
+            const float ex = l.x * (hx + an * mat.u[0]) + l.y * (hy + an * mat.u[1]) + l.z * (hz + an * mat.u[2]);
+            gms[i] += m.x * d.x + m.y * d.y + m.z * d.z - ex * ci * ci + xs;
+        }
     }
     float4 a = nl[i];
     nl[i] = make_float4(a.x + g.x, a.y + g.y, a.z + g.z, 0.f);
@@ -196,10 +213,11 @@ cudaError_t launch_adj_local(const float4* Y, const float4* Bf, const float4* lk
 }
 cudaError_t launch_adj_combine(const float4* Y, const float4* lB, const float4* Dl, const float4* gd,
                                const float4* lp, float4* nl, float4* lk, const Material& mat, float dtb, float cdt,
-                               int nx, int ny, int nz, int B, cudaStream_t s) {
+                               int nx, int ny, int nz, int B, float* gms, const double* lX, const InstParams* ip,
+                               const float4* prof, cudaStream_t s) {
     const long long N = (long long)nx * ny * nz;
     dim3 grid(blocks_for(N, 256), B);
-    k_adj_combine<<<grid, 256, 0, s>>>(Y, lB, Dl, gd, lp, nl, lk, mat, dtb, cdt, nx, ny, nz);
+    k_adj_combine<<<grid, 256, 0, s>>>(Y, lB, Dl, gd, lp, nl, lk, mat, dtb, cdt, nx, ny, nz, gms, lX, ip, prof);
     return cudaGetLastError();
 }
 cudaError_t launch_adj_terminal(const float4* Y, float4* lam, const double w[3], long long total, cudaStream_t s) {

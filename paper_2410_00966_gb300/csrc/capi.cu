@@ -39,7 +39,8 @@ cudaError_t launch_adj_local(const float4*, const float4*, const float4*, const 
                              const float4*, float4*, float4*, double*, float, float, double, long long, int,
                              cudaStream_t);
 cudaError_t launch_adj_combine(const float4*, const float4*, const float4*, const float4*, const float4*, float4*,
-                               float4*, const Material&, float, float, int, int, int, int, cudaStream_t);
+                               float4*, const Material&, float, float, int, int, int, int, float*, const double*,
+                               const InstParams*, const float4*, cudaStream_t);
 cudaError_t launch_adj_terminal(const float4*, float4*, const double*, long long, cudaStream_t);
 cudaError_t build_demag_kernel(const Plan&, double, double, double, double, float*, double2*, cudaStream_t);
 }  // namespace mq
@@ -886,8 +887,16 @@ struct AdjScratch {
 
 }  // namespace
 
-int mmcq_adjoint_rk4(mmcq_t* h, int64_t nsteps, double dt, const double w[3], double wn, double* J, double* grad) {
-    if (!h || nsteps < 1 || !(dt > 0) || !std::isfinite(dt) || !w || !std::isfinite(wn) || !grad) return MMCQ_ERR_ARG;
+int mmcq_adjoint_rk4(mmcq_t* h, int64_t nsteps, double dt, const mmcq_objective* obj, int64_t ckpt_every,
+                     double* J, double* grad, float* grad_ms) {
+    if (!h || nsteps < 1 || !(dt > 0) || !std::isfinite(dt) || !obj || !grad || ckpt_every < 0) return MMCQ_ERR_ARG;
+    const double* w = obj->w;
+    const double wn = obj->wn, wavg = obj->wavg;
+    if (!std::isfinite(w[0]) || !std::isfinite(w[1]) || !std::isfinite(w[2]) || !std::isfinite(wn) ||
+        !std::isfinite(wavg))
+        return MMCQ_ERR_ARG;
+    int64_t window = obj->window < 1 ? 1 : (obj->window > nsteps ? nsteps : obj->window);
+    const int64_t K = ckpt_every < 1 ? 1 : (ckpt_every > nsteps ? nsteps : ckpt_every);
     if (h->mode != CAV_E || h->nmodes != 1) return fail(h, MMCQ_ERR_UNSUPPORTED, "adjoint: E-mode, one cavity mode");
     for (const InstParams& q : h->ip)
         if (q.drv_on) return fail(h, MMCQ_ERR_UNSUPPORTED, "adjoint: drive on");
@@ -898,14 +907,19 @@ int mmcq_adjoint_rk4(mmcq_t* h, int64_t nsteps, double dt, const double w[3], do
     const double tol0 = h->tol;
     int r = mmcq_set_integrator(h, MMCQ_RK4, tol0, MMCQ_CAVITY_E);
     if (r) return r;
+    const int64_t nck = (nsteps + K - 1) / K;          // checkpoints at q = 0, K, 2K, ...
     AdjScratch sc(h);
-    float4* ck = (float4*)sc.get(sv * (nsteps + 1));
-    InstState* ckst = (InstState*)sc.get(sizeof(InstState) * B * (nsteps + 1));
-    float4 *Y[4], *Bs[4], *K[4];
+    float4* ck = (float4*)sc.get(sv * nck);
+    InstState* ckst = (InstState*)sc.get(sizeof(InstState) * B * nck);
+    float4* seg = (float4*)sc.get(sv * K);              // states q of the current segment
+    InstState* segst = (InstState*)sc.get(sizeof(InstState) * B * (K + 1));
+    float4* mfin = (float4*)sc.get(sv);                  // the state at step nsteps
+    InstState* stfin = (InstState*)sc.get(sizeof(InstState) * B);
+    float4 *Y[4], *Bs[4], *Kb[4];
     for (int q = 0; q < 4; q++) {
         Y[q] = (float4*)sc.get(sv);
         Bs[q] = (float4*)sc.get(sv);
-        K[q] = (float4*)sc.get(sv);
+        Kb[q] = (float4*)sc.get(sv);
     }
     float4* lam = (float4*)sc.get(sv);
     float4* lp = (float4*)sc.get(sv);
@@ -914,37 +928,41 @@ int mmcq_adjoint_rk4(mmcq_t* h, int64_t nsteps, double dt, const double w[3], do
     float4* lB = (float4*)sc.get(sv);
     float4* gd = (float4*)sc.get(sv);
     float4* Dl = (float4*)sc.get(sv);
+    float* gms = (float*)sc.get(sizeof(float) * BN);
     InstState* adst = (InstState*)sc.get(sizeof(InstState) * B);
     double* dX = (double*)sc.get(sizeof(double) * B);
     double* dlX = (double*)sc.get(sizeof(double) * B);
     const int nblk = adj_local_blocks(N);
     double* part = (double*)sc.get(sizeof(double) * 4 * B * nblk);
-    for (void* p : sc.bufs)
-        if (!p) return fail(h, MMCQ_ERR_CUDA, "adjoint: device allocation failed");
-    if (sc.bufs.size() != (size_t)(2 + 12 + 7 + 4)) return fail(h, MMCQ_ERR_CUDA, "adjoint: device allocation failed");
+    if (sc.bufs.size() != (size_t)(6 + 12 + 8 + 4)) return fail(h, MMCQ_ERR_CUDA, "adjoint: device allocation failed");
+    CK(h, cudaMemsetAsync(gms, 0, sizeof(float) * BN, h->stream));
 
-    // forward: checkpoint every step (m and the instance states)
+    // forward: checkpoint every K steps (m and the instance states)
     CK(h, launch_set_dt(h->Bf.st, B, dt, h->stream));
-    for (int64_t q = 0; q <= nsteps; q++) {
-        CK(h, cudaMemcpyAsync(ck + q * BN, h->Bf.m[0], sv, cudaMemcpyDeviceToDevice, h->stream));
-        CK(h, cudaMemcpyAsync(ckst + q * B, h->Bf.st, sizeof(InstState) * B, cudaMemcpyDeviceToDevice, h->stream));
-        if (q < nsteps) {
-            r = enqueue_steps(h, 1);
-            if (r) return r;
+    for (int64_t q = 0; q < nsteps; q++) {
+        if (q % K == 0) {
+            CK(h, cudaMemcpyAsync(ck + (q / K) * BN, h->Bf.m[0], sv, cudaMemcpyDeviceToDevice, h->stream));
+            CK(h, cudaMemcpyAsync(ckst + (q / K) * B, h->Bf.st, sizeof(InstState) * B, cudaMemcpyDeviceToDevice,
+                                  h->stream));
         }
+        r = enqueue_steps(h, 1);
+        if (r) return r;
     }
-    // objective
+    CK(h, cudaMemcpyAsync(mfin, h->Bf.m[0], sv, cudaMemcpyDeviceToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(stfin, h->Bf.st, sizeof(InstState) * B, cudaMemcpyDeviceToDevice, h->stream));
+    // objective at the final state
     std::vector<float4> mf(BN);
     std::vector<InstState> st(B);
-    CK(h, cudaMemcpyAsync(mf.data(), h->Bf.m[0], sv, cudaMemcpyDeviceToHost, h->stream));
-    CK(h, cudaMemcpyAsync(st.data(), h->Bf.st, sizeof(InstState) * B, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(mf.data(), mfin, sv, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(st.data(), stfin, sizeof(InstState) * B, cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     r = check_flags(h);
     if (r) return r;
     long long nmag = 0;
     for (float v : h->ms_host) nmag += v > 0;
     const double wv[3] = {nmag ? w[0] / nmag : 0.0, nmag ? w[1] / nmag : 0.0, nmag ? w[2] / nmag : 0.0};
-    std::vector<double> la_re(B), la_im(B);
+    const double cav = wavg / (double)window;          // weight of each |alpha_n|^2 in the average
+    std::vector<double> la_re(B), la_im(B), Jv(B);
     for (int b = 0; b < B; b++) {
         double a[3] = {0, 0, 0};
         for (long long i = 0; i < N; i++) {
@@ -952,109 +970,151 @@ int mmcq_adjoint_rk4(mmcq_t* h, int64_t nsteps, double dt, const double w[3], do
             if (v.w > 0.f) { a[0] += v.x; a[1] += v.y; a[2] += v.z; }
         }
         const double ar = st[b].a_re[0], ai = st[b].a_im[0];
-        if (J) J[b] = wv[0] * a[0] + wv[1] * a[1] + wv[2] * a[2] + wn * (ar * ar + ai * ai);
+        Jv[b] = wv[0] * a[0] + wv[1] * a[1] + wv[2] * a[2] + wn * (ar * ar + ai * ai);
         la_re[b] = 2.0 * wn * ar;
         la_im[b] = 2.0 * wn * ai;
         for (int c = 0; c < 6; c++) grad[6 * b + c] = 0.0;
     }
-    CK(h, launch_adj_terminal(ck + nsteps * BN, lam, wv, BN, h->stream));
+    CK(h, launch_adj_terminal(mfin, lam, wv, BN, h->stream));
 
     const double cc[4] = {0.0, 0.5, 0.5, 1.0}, bb[4] = {1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6};
     const double vc = h->mat.vc, hbar = h->hbar;
-    std::vector<InstState> sts(B);
+    std::vector<InstState> sts(B), segh((size_t)B * (K + 1));
     std::vector<double> Xs(4 * B), ar_s(4 * B), ai_s(4 * B), hp(4 * B * nblk);
     std::vector<double> kar(4 * B), kai(4 * B), lX(B);
-    for (int64_t q = nsteps - 1; q >= 0; q--) {
-        // stages of step q from its checkpoint
-        CK(h, cudaMemcpyAsync(st.data(), ckst + q * B, sizeof(InstState) * B, cudaMemcpyDeviceToHost, h->stream));
+    for (int64_t c0 = (nck - 1) * K; c0 >= 0; c0 -= K) {
+        const int64_t c1 = std::min(c0 + K, nsteps);
+        // recompute the states of steps c0 .. c1 - 1 from checkpoint c0 (the state
+        // of step c1 is the next checkpoint or the final state)
+        CK(h, cudaMemcpyAsync(h->Bf.m[0], ck + (c0 / K) * BN, sv, cudaMemcpyDeviceToDevice, h->stream));
+        CK(h, cudaMemcpyAsync(h->Bf.st, ckst + (c0 / K) * B, sizeof(InstState) * B, cudaMemcpyDeviceToDevice,
+                              h->stream));
+        for (int64_t q = c0; q < c1; q++) {
+            CK(h, cudaMemcpyAsync(seg + (q - c0) * BN, h->Bf.m[0], sv, cudaMemcpyDeviceToDevice, h->stream));
+            CK(h, cudaMemcpyAsync(segst + (q - c0) * B, h->Bf.st, sizeof(InstState) * B, cudaMemcpyDeviceToDevice,
+                                  h->stream));
+            if (q + 1 < c1) {
+                r = enqueue_steps(h, 1);
+                if (r) return r;
+            }
+        }
+        if (c1 < nsteps)
+            CK(h, cudaMemcpyAsync(segst + (c1 - c0) * B, ckst + (c1 / K) * B, sizeof(InstState) * B,
+                                  cudaMemcpyDeviceToDevice, h->stream));
+        else
+            CK(h, cudaMemcpyAsync(segst + (c1 - c0) * B, stfin, sizeof(InstState) * B, cudaMemcpyDeviceToDevice,
+                                  h->stream));
+        CK(h, cudaMemcpyAsync(segh.data(), segst, sizeof(InstState) * B * (c1 - c0 + 1), cudaMemcpyDeviceToHost,
+                              h->stream));
         CK(h, cudaStreamSynchronize(h->stream));
-        const float4* Y1 = ck + q * BN;
-        CK(h, cudaMemcpyAsync(Y[0], Y1, sv, cudaMemcpyDeviceToDevice, h->stream));
-        for (int s = 0; s < 4; s++) {
-            for (int b = 0; b < B; b++) {
-                double re = st[b].a_re[0], im = st[b].a_im[0];
-                if (s > 0) { re += cc[s] * dt * kar[(s - 1) * B + b]; im += cc[s] * dt * kai[(s - 1) * B + b]; }
-                ar_s[s * B + b] = re;
-                ai_s[s * B + b] = im;
-                sts[b] = st[b];
-                sts[b].mcur = 0;
-                sts[b].a_re[0] = sts[b].as_re[0] = re;
-                sts[b].a_im[0] = sts[b].as_im[0] = im;
-            }
-            CK(h, cudaMemcpyAsync(adst, sts.data(), sizeof(InstState) * B, cudaMemcpyHostToDevice, h->stream));
-            Buffers Bq = h->Bf;
-            Bq.m[0] = Bq.m[1] = Y[s];
-            Bq.st = adst;
-            Bq.fout = Bs[s];
-            r = adj_field(h, Bq, MMCQ_TERM_ALL);
-            if (r) return r;
-            CK(h, launch_coupling_sum(Bq, N, vc, 0, B, 0, dX, h->stream));
-            CK(h, cudaMemcpyAsync(Xs.data() + s * B, dX, sizeof(double) * B, cudaMemcpyDeviceToHost, h->stream));
-            CK(h, launch_adj_torque(Y[s], Bs[s], Y1, K[s], s < 3 ? Y[s + 1] : nullptr, (float)(cc[s < 3 ? s + 1 : 0] * dt),
-                                    h->mat.pre, h->mat.alpha, BN, h->stream));
-            CK(h, cudaStreamSynchronize(h->stream));
-            for (int b = 0; b < B; b++) {
-                const InstParams& ip = h->ip[b];
-                const double re = ar_s[s * B + b], im = ai_s[s * B + b];
-                // d alpha/dt = -(kappa + i omega) alpha + i X / hbar
-                kar[s * B + b] = ip.cav_on[0] ? -ip.kappa[0] * re + ip.wc[0] * im : 0.0;
-                kai[s * B + b] = ip.cav_on[0] ? -ip.kappa[0] * im - ip.wc[0] * re + Xs[s * B + b] / hbar : 0.0;
-            }
-        }
-        // renormalisation and the stage cotangents
-        CK(h, launch_adj_norm(Y1, K, lam, lp, nl, lk, (float)dt, BN, h->stream));
-        std::vector<double> lpr(la_re), lpi(la_im), nlr(la_re), nli(la_im), lkr(B), lki(B);
-        for (int b = 0; b < B; b++) { lkr[b] = dt * bb[3] * lpr[b]; lki[b] = dt * bb[3] * lpi[b]; }
-        for (int s = 3; s >= 0; s--) {
-            for (int b = 0; b < B; b++) lX[b] = h->ip[b].cav_on[0] ? lki[b] / hbar : 0.0;
-            CK(h, cudaMemcpyAsync(dlX, lX.data(), sizeof(double) * B, cudaMemcpyHostToDevice, h->stream));
-            CK(h, launch_adj_local(Y[s], Bs[s], lk, dlX, h->Bf.ip, h->Bf.prof[0], lB, gd, part, h->mat.pre,
-                                   h->mat.alpha, vc, N, B, h->stream));
-            CK(h, cudaMemcpyAsync(hp.data(), part, sizeof(double) * 4 * B * nblk, cudaMemcpyDeviceToHost, h->stream));
-            Buffers Bq = h->Bf;
-            Bq.m[0] = Bq.m[1] = lB;
-            Bq.st = adst;
-            Bq.fout = Dl;
-            r = adj_field(h, Bq, MMCQ_TERM_DEMAG);
-            if (r) return r;
-            const float dtb = s > 0 ? (float)(dt * bb[s - 1]) : 0.f;
-            const float cdt = s > 0 ? (float)(cc[s] * dt) : 0.f;
-            CK(h, launch_adj_combine(Y[s], lB, Dl, gd, lp, nl, lk, h->mat, dtb, cdt, h->P.nx, h->P.ny, h->P.nz, B,
-                                     h->stream));
-            CK(h, cudaStreamSynchronize(h->stream));
-            for (int b = 0; b < B; b++) {
-                const InstParams& ip = h->ip[b];
-                double sb[4] = {0, 0, 0, 0};
-                for (int k = 0; k < nblk; k++)
-                    for (int c = 0; c < 4; c++) sb[c] += hp[(b * nblk + k) * 4 + c];
-                const double re = ar_s[s * B + b], im = ai_s[s * B + b];
-                const double nr = lkr[b], ni = lki[b];
-                const bool on = ip.cav_on[0] != 0;
-                // B_cav = B_rms 2 Re alpha; the amplitude equation as a real pair
-                const double gr = on ? -ip.kappa[0] * nr - ip.wc[0] * ni + 2.0 * sb[3] : 0.0;
-                const double gi = on ? ip.wc[0] * nr - ip.kappa[0] * ni : 0.0;
-                double* g = grad + 6 * b;
-                g[0] += sb[0]; g[1] += sb[1]; g[2] += sb[2];
-                if (on) {
-                    g[3] += 2.0 * re * sb[3] + lX[b] * Xs[s * B + b];
-                    g[4] += nr * im - ni * re;
-                    g[5] += -nr * re - ni * im;
+        for (int64_t q = c1 - 1; q >= c0; q--) {
+            // the averaged photon number sees alpha at step q + 1
+            if (q + 1 >= nsteps - window + 1)
+                for (int b = 0; b < B; b++) {
+                    const InstState& sn = segh[(q + 1 - c0) * B + b];
+                    const double ar = sn.a_re[0], ai = sn.a_im[0];
+                    Jv[b] += cav * (ar * ar + ai * ai);
+                    la_re[b] += 2.0 * cav * ar;
+                    la_im[b] += 2.0 * cav * ai;
                 }
-                nlr[b] += gr;
-                nli[b] += gi;
-                if (s > 0) {
-                    lkr[b] = dt * bb[s - 1] * lpr[b] + cc[s] * dt * gr;
-                    lki[b] = dt * bb[s - 1] * lpi[b] + cc[s] * dt * gi;
+            const float4* Y1 = seg + (q - c0) * BN;
+            for (int b = 0; b < B; b++) st[b] = segh[(q - c0) * B + b];
+            CK(h, cudaMemcpyAsync(Y[0], Y1, sv, cudaMemcpyDeviceToDevice, h->stream));
+            for (int s = 0; s < 4; s++) {
+                for (int b = 0; b < B; b++) {
+                    double re = st[b].a_re[0], im = st[b].a_im[0];
+                    if (s > 0) { re += cc[s] * dt * kar[(s - 1) * B + b]; im += cc[s] * dt * kai[(s - 1) * B + b]; }
+                    ar_s[s * B + b] = re;
+                    ai_s[s * B + b] = im;
+                    sts[b] = st[b];
+                    sts[b].mcur = 0;
+                    sts[b].a_re[0] = sts[b].as_re[0] = re;
+                    sts[b].a_im[0] = sts[b].as_im[0] = im;
+                }
+                CK(h, cudaMemcpyAsync(adst, sts.data(), sizeof(InstState) * B, cudaMemcpyHostToDevice, h->stream));
+                Buffers Bq = h->Bf;
+                Bq.m[0] = Bq.m[1] = Y[s];
+                Bq.st = adst;
+                Bq.fout = Bs[s];
+                r = adj_field(h, Bq, MMCQ_TERM_ALL);
+                if (r) return r;
+                CK(h, launch_coupling_sum(Bq, N, vc, 0, B, 0, dX, h->stream));
+                CK(h, cudaMemcpyAsync(Xs.data() + s * B, dX, sizeof(double) * B, cudaMemcpyDeviceToHost, h->stream));
+                CK(h, launch_adj_torque(Y[s], Bs[s], Y1, Kb[s], s < 3 ? Y[s + 1] : nullptr,
+                                        (float)(cc[s < 3 ? s + 1 : 0] * dt), h->mat.pre, h->mat.alpha, BN,
+                                        h->stream));
+                CK(h, cudaStreamSynchronize(h->stream));
+                for (int b = 0; b < B; b++) {
+                    const InstParams& ip = h->ip[b];
+                    const double re = ar_s[s * B + b], im = ai_s[s * B + b];
+                    // d alpha/dt = -(kappa + i omega) alpha + i X / hbar
+                    kar[s * B + b] = ip.cav_on[0] ? -ip.kappa[0] * re + ip.wc[0] * im : 0.0;
+                    kai[s * B + b] = ip.cav_on[0] ? -ip.kappa[0] * im - ip.wc[0] * re + Xs[s * B + b] / hbar : 0.0;
                 }
             }
+            // renormalisation and the stage cotangents
+            CK(h, launch_adj_norm(Y1, Kb, lam, lp, nl, lk, (float)dt, BN, h->stream));
+            std::vector<double> lpr(la_re), lpi(la_im), nlr(la_re), nli(la_im), lkr(B), lki(B);
+            for (int b = 0; b < B; b++) { lkr[b] = dt * bb[3] * lpr[b]; lki[b] = dt * bb[3] * lpi[b]; }
+            for (int s = 3; s >= 0; s--) {
+                for (int b = 0; b < B; b++) lX[b] = h->ip[b].cav_on[0] ? lki[b] / hbar : 0.0;
+                CK(h, cudaMemcpyAsync(dlX, lX.data(), sizeof(double) * B, cudaMemcpyHostToDevice, h->stream));
+                CK(h, launch_adj_local(Y[s], Bs[s], lk, dlX, h->Bf.ip, h->Bf.prof[0], lB, gd, part, h->mat.pre,
+                                       h->mat.alpha, vc, N, B, h->stream));
+                CK(h, cudaMemcpyAsync(hp.data(), part, sizeof(double) * 4 * B * nblk, cudaMemcpyDeviceToHost,
+                                      h->stream));
+                Buffers Bq = h->Bf;
+                Bq.m[0] = Bq.m[1] = lB;
+                Bq.st = adst;
+                Bq.fout = Dl;
+                r = adj_field(h, Bq, MMCQ_TERM_DEMAG);
+                if (r) return r;
+                const float dtb = s > 0 ? (float)(dt * bb[s - 1]) : 0.f;
+                const float cdt = s > 0 ? (float)(cc[s] * dt) : 0.f;
+                CK(h, launch_adj_combine(Y[s], lB, Dl, gd, lp, nl, lk, h->mat, dtb, cdt, h->P.nx, h->P.ny, h->P.nz,
+                                         B, grad_ms ? gms : nullptr, dlX, h->Bf.ip, h->Bf.prof[0], h->stream));
+                CK(h, cudaStreamSynchronize(h->stream));
+                for (int b = 0; b < B; b++) {
+                    const InstParams& ip = h->ip[b];
+                    double sb[4] = {0, 0, 0, 0};
+                    for (int k = 0; k < nblk; k++)
+                        for (int c = 0; c < 4; c++) sb[c] += hp[(b * nblk + k) * 4 + c];
+                    const double re = ar_s[s * B + b], im = ai_s[s * B + b];
+                    const double nr = lkr[b], ni = lki[b];
+                    const bool on = ip.cav_on[0] != 0;
+                    // B_cav = B_rms 2 Re alpha; the amplitude equation as a real pair
+                    const double gr = on ? -ip.kappa[0] * nr - ip.wc[0] * ni + 2.0 * sb[3] : 0.0;
+                    const double gi = on ? ip.wc[0] * nr - ip.kappa[0] * ni : 0.0;
+                    double* g = grad + 6 * b;
+                    g[0] += sb[0]; g[1] += sb[1]; g[2] += sb[2];
+                    if (on) {
+                        g[3] += 2.0 * re * sb[3] + lX[b] * Xs[s * B + b];
+                        g[4] += nr * im - ni * re;
+                        g[5] += -nr * re - ni * im;
+                    }
+                    nlr[b] += gr;
+                    nli[b] += gi;
+                    if (s > 0) {
+                        lkr[b] = dt * bb[s - 1] * lpr[b] + cc[s] * dt * gr;
+                        lki[b] = dt * bb[s - 1] * lpi[b] + cc[s] * dt * gi;
+                    }
+                }
+            }
+            std::swap(lam, nl);
+            la_re = nlr;
+            la_im = nli;
         }
-        std::swap(lam, nl);
-        la_re = nlr;
-        la_im = nli;
     }
+    if (J) for (int b = 0; b < B; b++) J[b] = Jv[b];
+    // the handle back at step nsteps
+    CK(h, cudaMemcpyAsync(h->Bf.m[0], mfin, sv, cudaMemcpyDeviceToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->Bf.m[1], mfin, sv, cudaMemcpyDeviceToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->Bf.st, stfin, sizeof(InstState) * B, cudaMemcpyDeviceToDevice, h->stream));
+    if (grad_ms) CK(h, cudaMemcpyAsync(grad_ms, gms, sizeof(float) * BN, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
     r = check_flags(h);
     if (r) return r;
-    // back to the integrator the caller had (the state stays at step nsteps)
+    // back to the integrator the caller had
     if (kind0 != KIND_RK4) return mmcq_set_integrator(h, kind0, tol0, MMCQ_CAVITY_E);
     return MMCQ_OK;
 }
