@@ -461,6 +461,68 @@ def run_batched(args):
     return 0
 
 
+def run_adjoint(args):
+    """Gradient workload: the vortex disk (128x128x4 cells of 2 nm, Ms map,
+    65 536 cells), `steps` RK4 steps forward and the discrete adjoint back
+    (checkpoints every 64 steps), objective = photon number averaged over the
+    last fifth of the run.  value = cells x steps / (forward + adjoint time)."""
+    import torch
+
+    import paper_2410_00966_gb300 as pkg
+    import synthetic
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    I, ms, m0 = synthetic.disk_vortex()
+    dt = 5e-14
+    steps = max(args.steps, 8)
+    sim = pkg.Sim(I.nx, I.ny, I.nz, I.d, I.d, I.d, I.Ms, I.Aex, I.alpha, device=local)
+    sim.set_ms_map(ms)
+    sim.set_m(m0)
+    sim.set_cavity(I.omega_c, I.kappa, I.g)
+
+    def run(n):
+        sim.set_m(m0)
+        sim.reset_cavity()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        out = sim.adjoint_rk4(n, dt, wavg=1.0, window=max(1, n // 5), ckpt_every=64, ms_grad=True)
+        torch.cuda.synchronize(dev)
+        return time.perf_counter() - t0, out
+
+    for _ in range(max(args.warmup, 1)):
+        run(8)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    el, (J, g, gms) = run(steps)
+    clk = clocks.stop()
+    sim.set_m(m0)
+    sim.reset_cavity()
+    sim.set_integrator(pkg.MMCQ_RK4, 0.0, pkg.MMCQ_CAVITY_E)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    sim.step(steps, dt)
+    sim.sync()
+    el_f = time.perf_counter() - t0
+    cells = I.n
+    line = {
+        "metric": "LLG cell-steps/s, forward + discrete adjoint (gradients w.r.t. bias, g, omega_c, kappa, Ms map)",
+        "value": cells * steps / el, "unit": "cell-steps/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "vortex disk 128x128x4 @2nm, Ms map, photon-number objective", "cells": cells,
+                   "dt": dt, "checkpoint_every": 64, "forward_only_value": cells * steps / el_f,
+                   "J": float(J[0]), "grad": [float(v) for v in g[0]],
+                   "timing": "host clock around the synchronous adjoint call"},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    sim.close()
+    return 0
+
+
 def ctypes_sizeof_cavity(pkg):
     import ctypes
     return ctypes.sizeof(pkg.mmcq_cavity)
@@ -472,7 +534,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="yig_wire", choices=["yig_wire", "film", "large", "batched"])
+    ap.add_argument("--workload", default="yig_wire", choices=["yig_wire", "film", "large", "batched", "adjoint"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--instances", type=int, default=0, help="use only the first N instances (profiling)")
@@ -485,6 +547,8 @@ def main():
     build.build()
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     return run_ours(args)
 
 

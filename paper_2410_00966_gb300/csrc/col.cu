@@ -322,6 +322,78 @@ __global__ void __launch_bounds__(192, 5) k_zconv2(Plan Pl, Buffers Bf, StageArg
     else zsplit_inverse<P, 1>(C, sm, W, col, C.out + off_out);
 }
 
+// y passes with P = 2 PH longer than the register path holds (P = 2048): the
+// zero padding leaves at most PH input rows (forward) and needs at most PH
+// output rows (inverse), so the P-point transform is two PH-point register
+// transforms per column (decimation in frequency):
+//   forward:  X[2k] = DFT_PH(x)[k],  X[2k+1] = DFT_PH(x_r W_P^r)[k],
+//   inverse:  y[n] = IDFT_PH(h_even)[n] + W_P^{-n} IDFT_PH(h_odd)[n],  n < PH.
+// The same threads do both halves one after the other; in the inverse the odd
+// half is added onto the rows the even half stored (each row stays with one
+// thread, so the read-back is the thread's own store).
+template <int PH>
+__global__ void __launch_bounds__(512) k_col_split(Plan Pl, Buffers Bf, StageArgs A, ColArgs C) {
+    constexpr int NPT = ColShape<PH>::NPT, N1 = ColShape<PH>::N1;
+    constexpr int P = 2 * PH;
+    extern __shared__ float2 sm[];
+    const int bz = blockIdx.z;
+    const int b = A.inst0 + (C.ncomp == 3 ? bz : bz / 3);
+    const int c0 = C.ncomp == 3 ? 0 : bz % 3;
+    if (stage_skips(Bf.st[b], A)) return;
+    const int TX = Pl.TX;
+    const int rw = C.ncomp * TX;
+    const int W = C.G * rw;
+    const int col = threadIdx.x % W;
+    const int j = threadIdx.x / W;
+    const int g = C.ncomp == 3 ? (col >> Pl.lt) / 3 : (col >> Pl.lt);
+    const int e = col - g * rw;
+    const int t = blockIdx.x * C.G + g, o = blockIdx.y;          // tiles are the groups here
+    const bool valid = t < Pl.NT && o < C.nouter;
+    const float2* in = C.in + b * C.in_b + o * C.in_o + t * C.in_t + c0 * TX + e;
+    float2* out = C.out + b * C.out_b + o * C.out_o + t * C.out_t + c0 * TX + e;
+    const int tstep = Pl.twn / P;
+#pragma unroll 1
+    for (int J = 0; J < 2; J++) {
+        float2 v[NPT];
+        if (C.fwd) {
+#pragma unroll
+            for (int n2 = 0; n2 < NPT; n2++) {
+                const int r = j + N1 * n2;
+                float2 x = (valid && r < C.n_in) ? in[r * C.in_r] : make_float2(0.f, 0.f);
+                if (J == 1) x = cmul(x, twiddle(Bf.tw, r * tstep, false));
+                v[n2] = x;
+            }
+            col_fft<PH, false>(v, sm, W, col, j, Bf.tw, Pl.twn);
+            if (valid) {
+#pragma unroll
+                for (int i = 0; i < NPT; i++) out[(2 * col_out_row<PH>(j, i) + J) * C.out_r] = v[i];
+            }
+        } else {
+#pragma unroll
+            for (int n2 = 0; n2 < NPT; n2++) {
+                const int r = 2 * (j + N1 * n2) + J;
+                v[n2] = (valid && r < C.n_in) ? in[r * C.in_r] : make_float2(0.f, 0.f);
+            }
+            col_fft<PH, true>(v, sm, W, col, j, Bf.tw, Pl.twn);
+            if (valid) {
+#pragma unroll
+                for (int i = 0; i < NPT; i++) {
+                    const int k = col_out_row<PH>(j, i);
+                    if (k >= C.n_out) continue;
+                    float2* q = out + k * C.out_r;
+                    if (J == 0) {
+                        *q = v[i];
+                    } else {
+                        const float2 y = cmul(v[i], twiddle(Bf.tw, k * tstep, true));
+                        const float2 a = *q;
+                        *q = make_float2(a.x + y.x, a.y + y.y);
+                    }
+                }
+            }
+        }
+    }
+}
+
 // Generic shared-memory version (any power-of-two P up to 4096).
 template <int SLOTS>
 __global__ void __launch_bounds__(MAX_THREADS) k_col_gen(Plan P, Buffers Bf, StageArgs A, ColArgs C) {
@@ -399,6 +471,16 @@ static cudaError_t launch_z2(const Plan& Pl, const Buffers& Bf, const StageArgs&
     const int W = C.G * 3 * Pl.TX;
     dim3 grid((Pl.py + C.G - 1) / C.G, Pl.NT, nb);
     k_zconv2<P><<<grid, 2 * W, (size_t)P * W * sizeof(float2), s>>>(Pl, Bf, A, C);
+    return cudaGetLastError();
+}
+
+template <int PH>
+static cudaError_t launch_split(const Plan& Pl, const Buffers& Bf, const StageArgs& A, const ColArgs& C, int nb,
+                                cudaStream_t s) {
+    constexpr int N1 = ColShape<PH>::N1;
+    const int W = C.G * C.ncomp * Pl.TX;
+    dim3 grid((Pl.NT + C.G - 1) / C.G, C.nouter, nb * (C.ncomp == 3 ? 1 : 3));
+    k_col_split<PH><<<grid, W * N1, (size_t)PH * W * sizeof(float2), s>>>(Pl, Bf, A, C);
     return cudaGetLastError();
 }
 
@@ -502,6 +584,13 @@ cudaError_t launch_conv_part(const Plan& P, const Buffers& Bf, const StageArgs& 
         C.ncomp = three ? 3 : 1;
         C.group_tiles = 1; C.nouter = P.nz;
         C.G = pick_groups(C.ncomp * P.TX, P.py, P.NT, COL_MAX_THREADS, COL_SMEM_CAP);
+        if (P.py == 2048 && 2 * P.ny <= P.py) {
+            // two register transforms of 1024 per column (split of the padded length)
+            const bool three = reg_threads(1024, 3 * P.TX) <= 512 && (size_t)1024 * 3 * P.TX * 8 <= 96 * 1024;
+            C.ncomp = three ? 3 : 1;
+            C.G = pick_groups(C.ncomp * P.TX, 1024, P.NT, 512, 96 * 1024);
+            return launch_split<1024>(P, Bf, A, C, nb, s);
+        }
     } else {
         C.in = Bf.spec2; C.out = Bf.spec2;
         C.in_b = C.out_b = tb; C.in_o = C.out_o = tr; C.in_t = C.out_t = tt; C.in_r = C.out_r = tz;
@@ -567,6 +656,8 @@ cudaError_t col_init() {
     MMCQ_SET(2) MMCQ_SET(4) MMCQ_SET(8) MMCQ_SET(16) MMCQ_SET(32)
 #undef MMCQ_SET
     if ((e = cudaFuncSetAttribute(k_zconv2<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_col_split<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
         return e;
     if ((e = cudaFuncSetAttribute(k_zconv2<32>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
         return e;

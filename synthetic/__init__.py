@@ -249,6 +249,21 @@ def large_cpw() -> Workload:
     return Workload("CPW-like 1024x1024x8 @4nm, Lorentzian coupling", [inst], "dp45", 1e-13, 5e-9)
 
 
+def disk_vortex():
+    """Gradient workload: Permalloy disk of 200 nm diameter, 128x128x4 cells of
+    2 nm, seeded vortex, alpha 0.02, Ms map U[7.5e5, 8.5e5] inside the disk,
+    g/2pi = 200 MHz, omega_c/2pi = 1.3 GHz (near the gyrotropic mode of this
+    disk, an estimate), kappa/2pi = 10 MHz, RK4 dt = 5e-14 s.  Returns
+    (instance, Ms map, initial m)."""
+    nx, ny, nz, d = 128, 128, 4, 2e-9
+    inst = Instance(nx, ny, nz, d, Ms=8e5, Aex=1.3e-11, alpha=0.02, bias=(0.0, 0.0, 0.0),
+                    omega_c=_twopi(1.3e9), kappa=_twopi(10e6), g=_twopi(200e6), seed=derive_seed(4, 0))
+    ms = disk_ms(nx, ny, nz, d, d, 200e-9, 1.0) * uniform_ms_map(nx * ny * nz, derive_seed(4, 1), 7.5e5, 8.5e5)
+    m0, _, _ = vortex_m(nx, ny, nz, d, d, derive_seed(4, 2))
+    m0[ms <= 0] = 0.0
+    return inst, ms.astype(np.float32), m0
+
+
 def scaled(inst: Instance, nx: int, ny: int, nz: int) -> Instance:
     """Same material and cavity on another grid (parity tests at reduced size)."""
     return replace(inst, nx=nx, ny=ny, nz=nz)

@@ -28,6 +28,7 @@ GRIDS = [
     (20, 12, 16, (5e-9, 5e-9, 5e-9)),
     (24, 20, 9, (4e-9, 4e-9, 3e-9)),
     (6, 5, 17, (4e-9, 4e-9, 4e-9)),
+    (4, 600, 2, (4e-9, 3e-9, 4e-9)),
 ]
 
 
