@@ -47,7 +47,11 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
     const int K = A.kind;
     float2* xs = sm;                                   // [L + 1][ld]
     const int xs_n = (L + 1) * ld + (((L + 1) * ld) & 1);
-    float4* mrow = reinterpret_cast<float4*>(sm + xs_n);  // [row][nx]
+    // m rows staged in shared memory while they are short; long rows
+    // (L >= 512) read m through the read-only path instead, which keeps the
+    // block's shared memory (and so its residency) at the half-spectrum lines
+    constexpr bool STAGE_M = xinv_stages_m(L);
+    float4* mrow = reinterpret_cast<float4*>(sm + xs_n);  // [row][nx] (STAGE_M)
 
     // which buffer holds the stage input m_s
     const float4* msrc;
@@ -76,7 +80,11 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
             cp_async8(xs + k * ld + 3 * r + c, in + t * tstride + c * TX + tx);
         }
     }
-    for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) cp_async16(mrow + i, msrc + base + i);
+    if (STAGE_M) {
+        for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) cp_async16(mrow + i, msrc + base + i);
+    } else if (threadIdx.x == 0) {
+        prefetch_l2(msrc + base, (unsigned)(nr * nx * sizeof(float4)));
+    }
     if (threadIdx.x == 0) {
         for (int q = 0; q < NM; q++) s_gamma[q] = stage_gamma(A, ip, st, mat, q);
         s_drive = (float)drive_factor(A, ip, st);
@@ -130,7 +138,7 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
         const int row = row0 + r;
         const int z = (int)fdiv((unsigned)row, P.fd_ny), y = row - z * P.ny;
         const long long i = base + ii;
-        float4 m = mrow[ii];
+        float4 m = STAGE_M ? mrow[ii] : __ldg(msrc + i);
         const float Ms = m.w;
         float Bx = 0.f, By = 0.f, Bz = 0.f;
         if (want_demag) {
@@ -145,14 +153,14 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
 #define MMCQ_NB(Q, C)                                                                   \
     q = (Q);                                                                            \
     if (q.w > 0.f) { hx += (C) * (q.x - m.x); hy += (C) * (q.y - m.y); hz += (C) * (q.z - m.z); }
-            if (x > 0) { MMCQ_NB(mrow[ii - 1], mat.exch[0]) }
-            if (x + 1 < nx) { MMCQ_NB(mrow[ii + 1], mat.exch[0]) }
+            if (x > 0) { MMCQ_NB(STAGE_M ? mrow[ii - 1] : __ldg(msrc + i - 1), mat.exch[0]) }
+            if (x + 1 < nx) { MMCQ_NB(STAGE_M ? mrow[ii + 1] : __ldg(msrc + i + 1), mat.exch[0]) }
             if (y > 0) {
-                if (r > 0) { MMCQ_NB(mrow[ii - nx], mat.exch[1]) }
+                if (STAGE_M && r > 0) { MMCQ_NB(mrow[ii - nx], mat.exch[1]) }
                 else { MMCQ_NB(__ldg(msrc + i - nx), mat.exch[1]) }
             }
             if (y + 1 < P.ny) {
-                if (r + 1 < nr) { MMCQ_NB(mrow[ii + nx], mat.exch[1]) }
+                if (STAGE_M && r + 1 < nr) { MMCQ_NB(mrow[ii + nx], mat.exch[1]) }
                 else { MMCQ_NB(__ldg(msrc + i + nx), mat.exch[1]) }
             }
             if (z > 0) { MMCQ_NB(__ldg(msrc + i - pl), mat.exch[2]) }

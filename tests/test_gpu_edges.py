@@ -100,3 +100,26 @@ def test_ragged_batch_one_instance_stops_early():
         o.replay(sim.dt_history(b))
         assert np.abs(sim.get_m(b).astype(np.float64) - o.get_m()).max() <= 1e-5
     sim.close()
+
+
+@pytest.mark.parametrize("shape", [(600, 3, 2), (4, 600, 2)], ids=["long-x", "long-y"])
+def test_long_rows_dynamics(shape):
+    # padded lengths 2048: the one-row x passes (L = 1024) and the split y passes
+    require_gpu()
+    import oracle
+    import paper_2410_00966_gb300 as pkg
+    import synthetic
+    nx, ny, nz = shape
+    sim, o = make_pair(nx, ny, nz, 4e-9, 8e5, 1.3e-11, 0.01)
+    m0 = synthetic.tilted_m(nx * ny * nz, synthetic.derive_seed(92), 0.3)
+    sim.set_m(m0)
+    o.set_m(m0.astype(np.float64))
+    for h in (sim, o):
+        h.set_bias((0.05, 0.02, 0.0))
+        h.set_cavity(2 * math.pi * 8e9, 2 * math.pi * 1e7, 2 * math.pi * 2e8)
+    sim.set_integrator(pkg.MMCQ_RK4, 0.0, pkg.MMCQ_CAVITY_E)
+    o.set_integrator(oracle.RK4, 0.0, oracle.CAV_E)
+    sim.step(20, 1e-13)
+    o.step(20, 1e-13)
+    assert np.abs(sim.get_m().astype(np.float64) - o.get_m()).max() <= 1e-5
+    sim.close()
