@@ -335,10 +335,15 @@ def run_ours(args):
         import oracle
         oracle.build()
         attempts = 3 if args.workload == "yig_wire" else 20
+        cores = oracle.set_threads(0)
         v, el, acc = cpu_oracle_sample(w, attempts)
-        cpu = {"value": v, "unit": "cell-steps/s", "cores": os.cpu_count(), "kind": "oracle",
+        oracle.set_threads(1)
+        v1, el1, acc1 = cpu_oracle_sample(w, 1)
+        oracle.set_threads(0)
+        cpu = {"value": v, "unit": "cell-steps/s", "cores": cores, "kind": "oracle",
                "sample": f"{acc} accepted {w.integrator} steps of instance 0 ({I0.nx}x{I0.ny}x{I0.nz} cells), "
-                         f"{el:.1f} s"}
+                         f"{el:.1f} s",
+               "single_thread": {"value": v1, "sample": f"{acc1} accepted steps, {el1:.1f} s"}}
 
     if rank == 0:
         line = {
@@ -351,7 +356,9 @@ def run_ours(args):
                        "accepted_steps": acc1 - acc0, "rejected_steps": rej,
                        "l2": f"inputs larger than L2 ({info['device_bytes'] / 1e9:.2f} GB resident)",
                        "padded": [info["px"], info["py"], info["pz"]], "tile": info["tile"],
-                       "algorithmic_bytes_per_step": step_bytes / args.steps},
+                       "algorithmic_bytes_per_step": step_bytes / args.steps,
+                       "field_evals_per_s": B * (6 if dp else 4) * args.steps / (ms_max / 1e3),
+                       "step_model_efficiency": (step_bytes / args.steps) / (ms_max / args.steps / 1e3) / 1e9 / peak},
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -108,6 +108,7 @@ def _load():
         "or_rhs_modes": (None, [p, dp, dp, d, dp, dp]),
         "or_cavity_X_mode": (d, [p, dp, i]),
         "or_max_modes": (i, []),
+        "or_set_threads": (i, [i]),
         "or_adjoint_rk4": (d, [p, l, d, dp, d, d, l, dp, dp, dp]),
         "or_drive_factor": (d, [p, d]),
         "or_set_recording": (None, [p, i]),
@@ -401,3 +402,8 @@ def spectrum(t, y, omega) -> np.ndarray:
 def max_modes() -> int:
     """Cavity modes the oracle holds (mode 0 is the paper's single mode)."""
     return _load().or_max_modes()
+
+
+def set_threads(n: int) -> int:
+    """OpenMP threads of the oracle (n < 1: all cores); returns the number in use."""
+    return _load().or_set_threads(int(n))

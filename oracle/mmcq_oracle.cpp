@@ -43,6 +43,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef std::complex<double> cplx;
 
@@ -918,6 +921,16 @@ void or_rhs_modes(const oracle* o, const double* m, const double* a, double tc, 
 double or_cavity_X(const oracle* o, const double* m) { return cavity_X(o, m, 0); }
 double or_cavity_X_mode(const oracle* o, const double* m, int k) { return cavity_X(o, m, k); }
 int or_max_modes(void) { return OR_MAX_MODES; }
+// Threads of the OpenMP loops (n < 1: all cores); returns the number in use.
+int or_set_threads(int n) {
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 // Demag field at a list of cells by the direct sum, with the tensor evaluated
 // on the fly (no table): usable on grids far too large for the O(N^2) table.
