@@ -8,6 +8,7 @@
 // State buffers are float4 [B][N] with Ms in w, like the forward path.
 #include <math.h>
 
+#include "adjoint.cuh"
 #include "common.cuh"
 #include "stagecore.cuh"
 
@@ -187,6 +188,109 @@ __global__ void k_adj_terminal(const float4* Y, float4* lam, float wx, float wy,
     lam[i] = Y[i].w > 0.f ? make_float4(wx, wy, wz, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// ---- FP64 scalar steps (one thread or block per instance) -------------------
+static __device__ const double ADJ_C[4] = {0.0, 0.5, 0.5, 1.0};
+static __device__ const double ADJ_B[4] = {1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6};
+
+// The averaged photon number sees alpha at step q + 1: J += c |alpha|^2 and
+// its cotangent 2 c alpha.
+__global__ void k_adj_window(AdjScalars* S, const InstState* st, double c, int B) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const double ar = st[b].a_re[0], ai = st[b].a_im[0];
+    S[b].J += c * (ar * ar + ai * ai);
+    S[b].la_re += 2.0 * c * ar;
+    S[b].la_im += 2.0 * c * ai;
+}
+
+// Start of a reversed step from its state: the field evaluations read their
+// cavity amplitude from adst (E-mode, field only).
+__global__ void k_adj_begin_step(AdjScalars* S, InstState* adst, const InstState* st, int B) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    InstState x = st[b];
+    x.mcur = 0;
+    x.as_re[0] = x.a_re[0];
+    x.as_im[0] = x.a_im[0];
+    adst[b] = x;
+    S[b].a0_re = S[b].as_re[0] = x.a_re[0];
+    S[b].a0_im = S[b].as_im[0] = x.a_im[0];
+}
+
+// Stage s of the recomputation: d alpha/dt = -(kappa + i omega) alpha + i X / hbar,
+// then the amplitude of stage s + 1 for the next field evaluation.
+__global__ void k_adj_alpha_stage(AdjScalars* S, InstState* adst, const InstParams* ip, const double* X, int s,
+                                  double dt, double hbar, int B) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    AdjScalars& q = S[b];
+    const double re = q.as_re[s], im = q.as_im[s];
+    const bool on = ip[b].cav_on[0] != 0;
+    q.X[s] = X[b];
+    q.ka_re[s] = on ? -ip[b].kappa[0] * re + ip[b].wc[0] * im : 0.0;
+    q.ka_im[s] = on ? -ip[b].kappa[0] * im - ip[b].wc[0] * re + X[b] / hbar : 0.0;
+    if (s < 3) {
+        const double nr = q.a0_re + ADJ_C[s + 1] * dt * q.ka_re[s];
+        const double ni = q.a0_im + ADJ_C[s + 1] * dt * q.ka_im[s];
+        q.as_re[s + 1] = nr;
+        q.as_im[s + 1] = ni;
+        adst[b].a_re[0] = adst[b].as_re[0] = nr;
+        adst[b].a_im[0] = adst[b].as_im[0] = ni;
+    }
+}
+
+// Start of the stage cotangents: y' = y + dt sum b_s k_s.
+__global__ void k_adj_begin_vjp(AdjScalars* S, const InstParams* ip, double* lX, double dt, double hbar, int B) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    AdjScalars& q = S[b];
+    q.lp_re = q.nl_re = q.la_re;
+    q.lp_im = q.nl_im = q.la_im;
+    q.lk_re = dt * ADJ_B[3] * q.lp_re;
+    q.lk_im = dt * ADJ_B[3] * q.lp_im;
+    lX[b] = ip[b].cav_on[0] ? q.lk_im / hbar : 0.0;
+}
+
+// After the local products of stage s: the block partials (sum lB, sum B_rms . lB)
+// reduced in a fixed order, the amplitude cotangent through
+// d alpha/dt = -(kappa + i omega) alpha + i X / hbar and B_cav = B_rms 2 Re alpha,
+// the parameter cotangents, and the next stage's d alpha/dt cotangent.
+__global__ void k_adj_scalar_vjp(AdjScalars* S, const double* part, int nblk, const InstParams* ip, double* lX, int s,
+                                 double dt, double hbar) {
+    __shared__ double red[32];
+    const int b = blockIdx.x;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int k = threadIdx.x; k < nblk; k += blockDim.x)
+        for (int c = 0; c < 4; c++) v[c] += part[((long long)b * nblk + k) * 4 + c];
+    for (int c = 0; c < 4; c++) v[c] = block_sum_d(v[c], red);
+    if (threadIdx.x != 0) return;
+    AdjScalars& q = S[b];
+    const bool on = ip[b].cav_on[0] != 0;
+    const double re = q.as_re[s], im = q.as_im[s], nr = q.lk_re, ni = q.lk_im, lx = lX[b];
+    const double gr = on ? -ip[b].kappa[0] * nr - ip[b].wc[0] * ni + 2.0 * v[3] : 0.0;
+    const double gi = on ? ip[b].wc[0] * nr - ip[b].kappa[0] * ni : 0.0;
+    q.grad[0] += v[0]; q.grad[1] += v[1]; q.grad[2] += v[2];
+    if (on) {
+        q.grad[3] += 2.0 * re * v[3] + lx * q.X[s];
+        q.grad[4] += nr * im - ni * re;
+        q.grad[5] += -nr * re - ni * im;
+    }
+    q.nl_re += gr;
+    q.nl_im += gi;
+    if (s > 0) {
+        q.lk_re = dt * ADJ_B[s - 1] * q.lp_re + ADJ_C[s] * dt * gr;
+        q.lk_im = dt * ADJ_B[s - 1] * q.lp_im + ADJ_C[s] * dt * gi;
+        lX[b] = on ? q.lk_im / hbar : 0.0;
+    }
+}
+
+__global__ void k_adj_end_step(AdjScalars* S, int B) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    S[b].la_re = S[b].nl_re;
+    S[b].la_im = S[b].nl_im;
+}
+
 // ---------------------------------------------------------------------------
 static unsigned blocks_for(long long n, int th) { return (unsigned)((n + th - 1) / th); }
 
@@ -225,4 +329,34 @@ cudaError_t launch_adj_terminal(const float4* Y, float4* lam, const double w[3],
     return cudaGetLastError();
 }
 
+static unsigned small_blocks(int B) { return (unsigned)((B + 63) / 64); }
+cudaError_t launch_adj_window(AdjScalars* S, const InstState* st, double c, int B, cudaStream_t s) {
+    k_adj_window<<<small_blocks(B), 64, 0, s>>>(S, st, c, B);
+    return cudaGetLastError();
+}
+cudaError_t launch_adj_begin_step(AdjScalars* S, InstState* adst, const InstState* st, int B, cudaStream_t s) {
+    k_adj_begin_step<<<small_blocks(B), 64, 0, s>>>(S, adst, st, B);
+    return cudaGetLastError();
+}
+cudaError_t launch_adj_alpha_stage(AdjScalars* S, InstState* adst, const InstParams* ip, const double* X, int st,
+                                   double dt, double hbar, int B, cudaStream_t s) {
+    k_adj_alpha_stage<<<small_blocks(B), 64, 0, s>>>(S, adst, ip, X, st, dt, hbar, B);
+    return cudaGetLastError();
+}
+cudaError_t launch_adj_begin_vjp(AdjScalars* S, const InstParams* ip, double* lX, double dt, double hbar, int B,
+                                 cudaStream_t s) {
+    k_adj_begin_vjp<<<small_blocks(B), 64, 0, s>>>(S, ip, lX, dt, hbar, B);
+    return cudaGetLastError();
+}
+cudaError_t launch_adj_scalar_vjp(AdjScalars* S, const double* part, int nblk, const InstParams* ip, double* lX,
+                                  int st, double dt, double hbar, int B, cudaStream_t s) {
+    k_adj_scalar_vjp<<<B, 128, 0, s>>>(S, part, nblk, ip, lX, st, dt, hbar);
+    return cudaGetLastError();
+}
+cudaError_t launch_adj_end_step(AdjScalars* S, int B, cudaStream_t s) {
+    k_adj_end_step<<<small_blocks(B), 64, 0, s>>>(S, B);
+    return cudaGetLastError();
+}
+
 }  // namespace mq
+

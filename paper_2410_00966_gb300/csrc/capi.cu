@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 
+#include "adjoint.cuh"
 #include "common.cuh"
 #include "mmcq.h"
 
@@ -42,6 +43,14 @@ cudaError_t launch_adj_combine(const float4*, const float4*, const float4*, cons
                                float4*, const Material&, float, float, int, int, int, int, float*, const double*,
                                const InstParams*, const float4*, cudaStream_t);
 cudaError_t launch_adj_terminal(const float4*, float4*, const double*, long long, cudaStream_t);
+cudaError_t launch_adj_window(AdjScalars*, const InstState*, double, int, cudaStream_t);
+cudaError_t launch_adj_begin_step(AdjScalars*, InstState*, const InstState*, int, cudaStream_t);
+cudaError_t launch_adj_alpha_stage(AdjScalars*, InstState*, const InstParams*, const double*, int, double, double, int,
+                                   cudaStream_t);
+cudaError_t launch_adj_begin_vjp(AdjScalars*, const InstParams*, double*, double, double, int, cudaStream_t);
+cudaError_t launch_adj_scalar_vjp(AdjScalars*, const double*, int, const InstParams*, double*, int, double, double,
+                                  int, cudaStream_t);
+cudaError_t launch_adj_end_step(AdjScalars*, int, cudaStream_t);
 cudaError_t build_demag_kernel(const Plan&, double, double, double, double, float*, double2*, cudaStream_t);
 }  // namespace mq
 
@@ -934,7 +943,8 @@ int mmcq_adjoint_rk4(mmcq_t* h, int64_t nsteps, double dt, const mmcq_objective*
     double* dlX = (double*)sc.get(sizeof(double) * B);
     const int nblk = adj_local_blocks(N);
     double* part = (double*)sc.get(sizeof(double) * 4 * B * nblk);
-    if (sc.bufs.size() != (size_t)(6 + 12 + 8 + 4)) return fail(h, MMCQ_ERR_CUDA, "adjoint: device allocation failed");
+    AdjScalars* S = (AdjScalars*)sc.get(sizeof(AdjScalars) * B);
+    if (sc.bufs.size() != (size_t)(6 + 12 + 8 + 5)) return fail(h, MMCQ_ERR_CUDA, "adjoint: device allocation failed");
     CK(h, cudaMemsetAsync(gms, 0, sizeof(float) * BN, h->stream));
 
     // forward: checkpoint every K steps (m and the instance states)
@@ -976,12 +986,19 @@ int mmcq_adjoint_rk4(mmcq_t* h, int64_t nsteps, double dt, const mmcq_objective*
         for (int c = 0; c < 6; c++) grad[6 * b + c] = 0.0;
     }
     CK(h, launch_adj_terminal(mfin, lam, wv, BN, h->stream));
+    {
+        std::vector<AdjScalars> Sh(B);
+        for (int b = 0; b < B; b++) {
+            std::memset(&Sh[b], 0, sizeof(AdjScalars));
+            Sh[b].la_re = la_re[b];
+            Sh[b].la_im = la_im[b];
+        }
+        CK(h, cudaMemcpyAsync(S, Sh.data(), sizeof(AdjScalars) * B, cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
 
     const double cc[4] = {0.0, 0.5, 0.5, 1.0}, bb[4] = {1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6};
     const double vc = h->mat.vc, hbar = h->hbar;
-    std::vector<InstState> sts(B), segh((size_t)B * (K + 1));
-    std::vector<double> Xs(4 * B), ar_s(4 * B), ai_s(4 * B), hp(4 * B * nblk);
-    std::vector<double> kar(4 * B), kai(4 * B), lX(B);
     for (int64_t c0 = (nck - 1) * K; c0 >= 0; c0 -= K) {
         const int64_t c1 = std::min(c0 + K, nsteps);
         // recompute the states of steps c0 .. c1 - 1 from checkpoint c0 (the state
@@ -998,40 +1015,15 @@ int mmcq_adjoint_rk4(mmcq_t* h, int64_t nsteps, double dt, const mmcq_objective*
                 if (r) return r;
             }
         }
-        if (c1 < nsteps)
-            CK(h, cudaMemcpyAsync(segst + (c1 - c0) * B, ckst + (c1 / K) * B, sizeof(InstState) * B,
-                                  cudaMemcpyDeviceToDevice, h->stream));
-        else
-            CK(h, cudaMemcpyAsync(segst + (c1 - c0) * B, stfin, sizeof(InstState) * B, cudaMemcpyDeviceToDevice,
-                                  h->stream));
-        CK(h, cudaMemcpyAsync(segh.data(), segst, sizeof(InstState) * B * (c1 - c0 + 1), cudaMemcpyDeviceToHost,
-                              h->stream));
-        CK(h, cudaStreamSynchronize(h->stream));
+        CK(h, cudaMemcpyAsync(segst + (c1 - c0) * B, c1 < nsteps ? ckst + (c1 / K) * B : stfin,
+                              sizeof(InstState) * B, cudaMemcpyDeviceToDevice, h->stream));
         for (int64_t q = c1 - 1; q >= c0; q--) {
             // the averaged photon number sees alpha at step q + 1
-            if (q + 1 >= nsteps - window + 1)
-                for (int b = 0; b < B; b++) {
-                    const InstState& sn = segh[(q + 1 - c0) * B + b];
-                    const double ar = sn.a_re[0], ai = sn.a_im[0];
-                    Jv[b] += cav * (ar * ar + ai * ai);
-                    la_re[b] += 2.0 * cav * ar;
-                    la_im[b] += 2.0 * cav * ai;
-                }
+            if (q + 1 >= nsteps - window + 1) CK(h, launch_adj_window(S, segst + (q + 1 - c0) * B, cav, B, h->stream));
             const float4* Y1 = seg + (q - c0) * BN;
-            for (int b = 0; b < B; b++) st[b] = segh[(q - c0) * B + b];
+            CK(h, launch_adj_begin_step(S, adst, segst + (q - c0) * B, B, h->stream));
             CK(h, cudaMemcpyAsync(Y[0], Y1, sv, cudaMemcpyDeviceToDevice, h->stream));
             for (int s = 0; s < 4; s++) {
-                for (int b = 0; b < B; b++) {
-                    double re = st[b].a_re[0], im = st[b].a_im[0];
-                    if (s > 0) { re += cc[s] * dt * kar[(s - 1) * B + b]; im += cc[s] * dt * kai[(s - 1) * B + b]; }
-                    ar_s[s * B + b] = re;
-                    ai_s[s * B + b] = im;
-                    sts[b] = st[b];
-                    sts[b].mcur = 0;
-                    sts[b].a_re[0] = sts[b].as_re[0] = re;
-                    sts[b].a_im[0] = sts[b].as_im[0] = im;
-                }
-                CK(h, cudaMemcpyAsync(adst, sts.data(), sizeof(InstState) * B, cudaMemcpyHostToDevice, h->stream));
                 Buffers Bq = h->Bf;
                 Bq.m[0] = Bq.m[1] = Y[s];
                 Bq.st = adst;
@@ -1039,30 +1031,17 @@ int mmcq_adjoint_rk4(mmcq_t* h, int64_t nsteps, double dt, const mmcq_objective*
                 r = adj_field(h, Bq, MMCQ_TERM_ALL);
                 if (r) return r;
                 CK(h, launch_coupling_sum(Bq, N, vc, 0, B, 0, dX, h->stream));
-                CK(h, cudaMemcpyAsync(Xs.data() + s * B, dX, sizeof(double) * B, cudaMemcpyDeviceToHost, h->stream));
+                CK(h, launch_adj_alpha_stage(S, adst, h->Bf.ip, dX, s, dt, hbar, B, h->stream));
                 CK(h, launch_adj_torque(Y[s], Bs[s], Y1, Kb[s], s < 3 ? Y[s + 1] : nullptr,
                                         (float)(cc[s < 3 ? s + 1 : 0] * dt), h->mat.pre, h->mat.alpha, BN,
                                         h->stream));
-                CK(h, cudaStreamSynchronize(h->stream));
-                for (int b = 0; b < B; b++) {
-                    const InstParams& ip = h->ip[b];
-                    const double re = ar_s[s * B + b], im = ai_s[s * B + b];
-                    // d alpha/dt = -(kappa + i omega) alpha + i X / hbar
-                    kar[s * B + b] = ip.cav_on[0] ? -ip.kappa[0] * re + ip.wc[0] * im : 0.0;
-                    kai[s * B + b] = ip.cav_on[0] ? -ip.kappa[0] * im - ip.wc[0] * re + Xs[s * B + b] / hbar : 0.0;
-                }
             }
             // renormalisation and the stage cotangents
             CK(h, launch_adj_norm(Y1, Kb, lam, lp, nl, lk, (float)dt, BN, h->stream));
-            std::vector<double> lpr(la_re), lpi(la_im), nlr(la_re), nli(la_im), lkr(B), lki(B);
-            for (int b = 0; b < B; b++) { lkr[b] = dt * bb[3] * lpr[b]; lki[b] = dt * bb[3] * lpi[b]; }
+            CK(h, launch_adj_begin_vjp(S, h->Bf.ip, dlX, dt, hbar, B, h->stream));
             for (int s = 3; s >= 0; s--) {
-                for (int b = 0; b < B; b++) lX[b] = h->ip[b].cav_on[0] ? lki[b] / hbar : 0.0;
-                CK(h, cudaMemcpyAsync(dlX, lX.data(), sizeof(double) * B, cudaMemcpyHostToDevice, h->stream));
                 CK(h, launch_adj_local(Y[s], Bs[s], lk, dlX, h->Bf.ip, h->Bf.prof[0], lB, gd, part, h->mat.pre,
                                        h->mat.alpha, vc, N, B, h->stream));
-                CK(h, cudaMemcpyAsync(hp.data(), part, sizeof(double) * 4 * B * nblk, cudaMemcpyDeviceToHost,
-                                      h->stream));
                 Buffers Bq = h->Bf;
                 Bq.m[0] = Bq.m[1] = lB;
                 Bq.st = adst;
@@ -1073,36 +1052,19 @@ int mmcq_adjoint_rk4(mmcq_t* h, int64_t nsteps, double dt, const mmcq_objective*
                 const float cdt = s > 0 ? (float)(cc[s] * dt) : 0.f;
                 CK(h, launch_adj_combine(Y[s], lB, Dl, gd, lp, nl, lk, h->mat, dtb, cdt, h->P.nx, h->P.ny, h->P.nz,
                                          B, grad_ms ? gms : nullptr, dlX, h->Bf.ip, h->Bf.prof[0], h->stream));
-                CK(h, cudaStreamSynchronize(h->stream));
-                for (int b = 0; b < B; b++) {
-                    const InstParams& ip = h->ip[b];
-                    double sb[4] = {0, 0, 0, 0};
-                    for (int k = 0; k < nblk; k++)
-                        for (int c = 0; c < 4; c++) sb[c] += hp[(b * nblk + k) * 4 + c];
-                    const double re = ar_s[s * B + b], im = ai_s[s * B + b];
-                    const double nr = lkr[b], ni = lki[b];
-                    const bool on = ip.cav_on[0] != 0;
-                    // B_cav = B_rms 2 Re alpha; the amplitude equation as a real pair
-                    const double gr = on ? -ip.kappa[0] * nr - ip.wc[0] * ni + 2.0 * sb[3] : 0.0;
-                    const double gi = on ? ip.wc[0] * nr - ip.kappa[0] * ni : 0.0;
-                    double* g = grad + 6 * b;
-                    g[0] += sb[0]; g[1] += sb[1]; g[2] += sb[2];
-                    if (on) {
-                        g[3] += 2.0 * re * sb[3] + lX[b] * Xs[s * B + b];
-                        g[4] += nr * im - ni * re;
-                        g[5] += -nr * re - ni * im;
-                    }
-                    nlr[b] += gr;
-                    nli[b] += gi;
-                    if (s > 0) {
-                        lkr[b] = dt * bb[s - 1] * lpr[b] + cc[s] * dt * gr;
-                        lki[b] = dt * bb[s - 1] * lpi[b] + cc[s] * dt * gi;
-                    }
-                }
+                CK(h, launch_adj_scalar_vjp(S, part, nblk, h->Bf.ip, dlX, s, dt, hbar, B, h->stream));
             }
+            CK(h, launch_adj_end_step(S, B, h->stream));
             std::swap(lam, nl);
-            la_re = nlr;
-            la_im = nli;
+        }
+    }
+    {
+        std::vector<AdjScalars> Sh(B);
+        CK(h, cudaMemcpyAsync(Sh.data(), S, sizeof(AdjScalars) * B, cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        for (int b = 0; b < B; b++) {
+            Jv[b] += Sh[b].J;
+            for (int c = 0; c < 6; c++) grad[6 * b + c] = Sh[b].grad[c];
         }
     }
     if (J) for (int b = 0; b < B; b++) J[b] = Jv[b];
