@@ -338,12 +338,12 @@ def run_ours(args):
         cores = oracle.set_threads(0)
         v, el, acc = cpu_oracle_sample(w, attempts)
         oracle.set_threads(1)
-        v1, el1, acc1 = cpu_oracle_sample(w, 1)
+        v1, el1, acc_1 = cpu_oracle_sample(w, 1)
         oracle.set_threads(0)
         cpu = {"value": v, "unit": "cell-steps/s", "cores": cores, "kind": "oracle",
                "sample": f"{acc} accepted {w.integrator} steps of instance 0 ({I0.nx}x{I0.ny}x{I0.nz} cells), "
                          f"{el:.1f} s",
-               "single_thread": {"value": v1, "sample": f"{acc1} accepted steps, {el1:.1f} s"}}
+               "single_thread": {"value": v1, "sample": f"{acc_1} accepted steps, {el1:.1f} s"}}
 
     if rank == 0:
         line = {
