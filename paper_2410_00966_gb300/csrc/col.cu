@@ -283,7 +283,8 @@ __global__ void __launch_bounds__(192, 5) k_zconv2(Plan Pl, Buffers Bf, StageArg
     // product at every (kz, g, tx) point of the block: symmetric kernel
     // (xx, yy, zz, xy, xz, yz) at (|kz|, |ky|, kx); xy is odd in ky, xz in kz,
     // yz in both.  The block has 2 W = 6 G TX threads, so a thread keeps its
-    // (g, tx) point and steps kz by 6.
+    // (g, tx) point and takes every sixth mirror pair (kz, P - kz): one read
+    // of the stored kernel row serves both, with xz and yz negated for P - kz.
     const int GT = C.G * TX;                      // power of two
     const int lgt = __ffs(GT) - 1;
     const long long zs = (long long)Pl.hyk * Pl.NT * TX * 6;
@@ -297,25 +298,31 @@ __global__ void __launch_bounds__(192, 5) k_zconv2(Plan Pl, Buffers Bf, StageArg
     const float* Kb = Bf.kern + ((long long)kyr * Pl.NT * TX + (live ? kx : 0)) * 6;
     float2* pm0 = sm + gg * 3 * TX + xx;
     const int kz0 = threadIdx.x >> lgt;           // 0 .. 5
-#pragma unroll
-    for (int it = 0; it < (P + 5) / 6; it++) {
-        const int kz = kz0 + 6 * it;
-        if (kz >= P) break;
-        float2* pm = pm0 + kz * W;
+    auto apply = [&](float2* pm, float Kxx, float Kyy, float Kzz, float Kxy, float Kxz, float Kyz) {
         const float2 mx = pm[0], my = pm[TX], mz = pm[2 * TX];
-        float2 hx = make_float2(0.f, 0.f), hy = hx, hz = hx;
+        pm[0] = make_float2(Kxx * mx.x + Kxy * my.x + Kxz * mz.x, Kxx * mx.y + Kxy * my.y + Kxz * mz.y);
+        pm[TX] = make_float2(Kxy * mx.x + Kyy * my.x + Kyz * mz.x, Kxy * mx.y + Kyy * my.y + Kyz * mz.y);
+        pm[2 * TX] = make_float2(Kxz * mx.x + Kyz * my.x + Kzz * mz.x, Kxz * mx.y + Kyz * my.y + Kzz * mz.y);
+    };
+#pragma unroll
+    for (int it = 0; it < (P / 2 + 6) / 6; it++) {
+        const int kzr = kz0 + 6 * it;
+        if (kzr > P / 2) break;
         if (live) {
-            const bool nz_ = kz > P / 2;
-            const int kzr = nz_ ? P - kz : kz;
             const float2* Kp = reinterpret_cast<const float2*>(Kb + kzr * zs);
             const float2 k0 = __ldg(Kp), k1 = __ldg(Kp + 1), k2 = __ldg(Kp + 2);
-            const float sz = nz_ ? -1.f : 1.f;
-            const float Kxx = k0.x, Kyy = k0.y, Kzz = k1.x, Kxy = sy * k1.y, Kxz = sz * k2.x, Kyz = sy * sz * k2.y;
-            hx = make_float2(Kxx * mx.x + Kxy * my.x + Kxz * mz.x, Kxx * mx.y + Kxy * my.y + Kxz * mz.y);
-            hy = make_float2(Kxy * mx.x + Kyy * my.x + Kyz * mz.x, Kxy * mx.y + Kyy * my.y + Kyz * mz.y);
-            hz = make_float2(Kxz * mx.x + Kyz * my.x + Kzz * mz.x, Kxz * mx.y + Kyz * my.y + Kzz * mz.y);
+            const float Kxy = sy * k1.y, Kyz = sy * k2.y;
+            apply(pm0 + kzr * W, k0.x, k0.y, k1.x, Kxy, k2.x, Kyz);
+            if (kzr > 0 && kzr < P / 2) apply(pm0 + (P - kzr) * W, k0.x, k0.y, k1.x, Kxy, -k2.x, -Kyz);
+        } else {
+            const float2 z0 = make_float2(0.f, 0.f);
+            float2* pm = pm0 + kzr * W;
+            pm[0] = z0; pm[TX] = z0; pm[2 * TX] = z0;
+            if (kzr > 0 && kzr < P / 2) {
+                pm = pm0 + (P - kzr) * W;
+                pm[0] = z0; pm[TX] = z0; pm[2 * TX] = z0;
+            }
         }
-        pm[0] = hx; pm[TX] = hy; pm[2 * TX] = hz;
     }
     __syncthreads();
     if (half == 0) zsplit_inverse<P, 0>(C, sm, W, col, C.out + off_out);
