@@ -83,6 +83,32 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xfwd(Pla
     // X[k] = E[k] + W^k O[k], E = (Z[k] + conj Z[L-k]) / 2, O = -i (Z[k] - conj Z[L-k]) / 2
     const int TX = P.TX, lt = P.lt;
     const long long tstride = (long long)P.ny * 3 * TX;
+    auto unpack = [&](int k, int line) {
+        float2 X = make_float2(0.f, 0.f);
+        if (k <= L) {
+            float2 Zk = zs[(k == L ? 0 : k) * ld + line];
+            float2 Zc = conjf2(zs[(k == 0 ? 0 : L - k) * ld + line]);
+            float2 E = make_float2(0.5f * (Zk.x + Zc.x), 0.5f * (Zk.y + Zc.y));
+            float2 D = make_float2(0.5f * (Zk.x - Zc.x), 0.5f * (Zk.y - Zc.y));
+            float2 wD = cmul(stw[k], D);
+            X = make_float2(E.x + wD.y, E.y - wD.x);
+        }
+        return X;
+    };
+    // tile t of a row holds the 3 TX values (c, tx) contiguously; when 3 TX
+    // divides the block, a thread keeps one (c, tx) and steps over the tiles
+    const int w3 = 3 * TX;
+    if (blockDim.x % w3 == 0) {
+        const int e = threadIdx.x % w3, t0 = threadIdx.x / w3, dtt = blockDim.x / w3;
+        const int c = e >> lt, tx = e & (TX - 1);
+        for (int r = 0; r < nr; r++) {
+            const int row = row0 + r;
+            const int z = (int)fdiv((unsigned)row, P.fd_ny), y = row - z * P.ny;
+            float2* out = Bf.spec + (((long long)b * P.nz + z) * P.NT * P.ny + y) * 3 * TX + e;
+            for (int t = t0; t < P.NT; t += dtt) out[t * tstride] = unpack(t * TX + tx, 3 * r + c);
+        }
+        return;
+    }
     const int W3 = P.NT * 3 * TX;
     for (int r = 0; r < nr; r++) {
         const int row = row0 + r;
@@ -92,18 +118,7 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xfwd(Pla
             const int t = (idx >> lt) / 3;
             const int ctx = idx - t * 3 * TX;
             const int c = ctx >> lt, tx = ctx & (TX - 1);
-            const int k = t * TX + tx;
-            const int line = 3 * r + c;
-            float2 X = make_float2(0.f, 0.f);
-            if (k <= L) {
-                float2 Zk = zs[(k == L ? 0 : k) * ld + line];
-                float2 Zc = conjf2(zs[(k == 0 ? 0 : L - k) * ld + line]);
-                float2 E = make_float2(0.5f * (Zk.x + Zc.x), 0.5f * (Zk.y + Zc.y));
-                float2 D = make_float2(0.5f * (Zk.x - Zc.x), 0.5f * (Zk.y - Zc.y));
-                float2 wD = cmul(stw[k], D);
-                X = make_float2(E.x + wD.y, E.y - wD.x);
-            }
-            out[t * tstride + ctx] = X;
+            out[t * tstride + ctx] = unpack(t * TX + tx, 3 * r + c);
         }
     }
 }

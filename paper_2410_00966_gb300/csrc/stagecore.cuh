@@ -335,7 +335,7 @@ struct CellUpdate {
     // (Bx, By, Bz) holds demag + exchange on entry
     template <bool REC>
     __device__ __forceinline__ void run(const Material& mat, const Buffers& Bf, long long i, float4 m, float Bx,
-                                        float By, float Bz, double (&xacc)[NM], double (&macc)[REC ? 3 : 1],
+                                        float By, float Bz, float (&xacc)[NM], double (&macc)[REC ? 3 : 1],
                                         float& emax, bool& bad) const {
         const float Ms = m.w;
         float px_[NM], py_[NM], pz_[NM];
@@ -344,7 +344,7 @@ struct CellUpdate {
         if (Ms > 0.f) {
             if (want_anis) {
                 float mu = m.x * mat.u[0] + m.y * mat.u[1] + m.z * mat.u[2];
-                float f = mat.two_ku / Ms * mu;
+                float f = mat.two_ku * __fdividef(mu, Ms);
                 Bx += f * mat.u[0]; By += f * mat.u[1]; Bz += f * mat.u[2];
             }
             if (want_zee) { Bx += bex; By += bey; Bz += bez; }
@@ -371,7 +371,9 @@ struct CellUpdate {
         float4 kk = make_float4(mat.pre * (cx + mat.alpha * dx), mat.pre * (cy + mat.alpha * dy),
                                 mat.pre * (cz + mat.alpha * dz), 0.f);
         if (!(Ms > 0.f)) kk = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (!isfinite(kk.x) || !isfinite(kk.y) || !isfinite(kk.z)) bad = true;
+        // a NaN or infinite component makes the sum non-finite (so does a
+        // component sum beyond the float range, itself an overflowing torque)
+        if (!(fabsf(kk.x + kk.y + kk.z) <= 3.0e38f)) bad = true;
         float4 mx = m;   // m used for the coupling sums of this launch
         float4 mrec = m; // state being accepted (recorded spatial average)
         if (K == KIND_RK4) {
@@ -404,11 +406,13 @@ struct CellUpdate {
                 emax = fmaxf(emax, en);
             }
         }
-        // per-cell products in FP32, accumulated in FP64 (the sum over cells is
-        // the quantity that needs the range; FP64 arithmetic is ~1/64 rate here)
+        // per-cell products, and a thread's partial over its few cells, in
+        // FP32; the caller widens the partial to FP64 for the block and
+        // instance sums (the sum over all cells is the quantity that needs the
+        // range, and FP64 issues at a small fraction of the FP32 rate here)
 #pragma unroll
         for (int q = 0; q < NM; q++)
-            if (on[q]) xacc[q] += (double)(Ms * (mx.x * px_[q] + mx.y * py_[q] + mx.z * pz_[q]));
+            if (on[q]) xacc[q] += Ms * (mx.x * px_[q] + mx.y * py_[q] + mx.z * pz_[q]);
         if constexpr (REC) {
             if (Ms > 0.f) { macc[0] += mrec.x; macc[1] += mrec.y; macc[2] += mrec.z; }
         }

@@ -18,7 +18,7 @@ namespace mq {
 
 // ---------------------------------------------------------------------------
 // x inverse + local fields + torque + RK bookkeeping + cavity reduction.
-// Shared memory: xs[k][line] (k <= L, line = 3 r + comp), then m rows.
+// Shared memory: xs[k][line] (k <= L, line = 3 r + comp).
 // ---------------------------------------------------------------------------
 // REC: this launch records the spatial average of the state being accepted
 // (the last stage of a step with recording on); NM: cavity modes compiled in
@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
     __shared__ double s_gamma[NM];
     __shared__ float s_drive;
     __shared__ int s_last;
+    __shared__ int2 s_yz[64];                          // rows per block <= 64
     const int b = A.inst0 + blockIdx.y;
     const InstState& st = Bf.st[b];
     if (stage_skips(st, A)) return;
@@ -46,12 +47,6 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
     const int s = A.stage;
     const int K = A.kind;
     float2* xs = sm;                                   // [L + 1][ld]
-    const int xs_n = (L + 1) * ld + (((L + 1) * ld) & 1);
-    // m rows staged in shared memory while they are short; long rows
-    // (L >= 512) read m through the read-only path instead, which keeps the
-    // block's shared memory (and so its residency) at the half-spectrum lines
-    constexpr bool STAGE_M = xinv_stages_m(L);
-    float4* mrow = reinterpret_cast<float4*>(sm + xs_n);  // [row][nx] (STAGE_M)
 
     // which buffer holds the stage input m_s
     const float4* msrc;
@@ -68,23 +63,47 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
         if (row0 + nr - 1 + P.ny < P.nrows) prefetch_l2(msrc + base + pl_, bytes);
     }
 
-    // half-spectrum rows X[0..L] of the three components of every row
+    // (y, z) of the block's rows, for the cell loop
+    if (threadIdx.x < nr) {
+        const int row = row0 + threadIdx.x;
+        const int z = (int)fdiv((unsigned)row, P.fd_ny);
+        s_yz[threadIdx.x] = make_int2(row - z * P.ny, z);
+    }
+
+    // half-spectrum rows X[0..L] of the three components of every row.  In the
+    // spectrum, tile t of a row holds the 3 TX values (c, tx) contiguously
+    // (k = t TX + tx); when 3 TX divides the block, a thread keeps one (c, tx)
+    // and steps over the tiles.
     const long long tstride = (long long)P.ny * 3 * TX;
-    for (int r = 0; r < nr; r++) {
-        const int row = row0 + r;
-        const int z = (int)fdiv((unsigned)row, P.fd_ny), y = row - z * P.ny;
-        const float2* in = Bf.spec + (((long long)b * P.nz + z) * P.NT * P.ny + y) * 3 * TX;
-        for (int idx = threadIdx.x; idx < 3 * (L + 1); idx += blockDim.x) {
-            const int c = idx / (L + 1), k = idx - c * (L + 1);
-            const int t = k >> lt, tx = k & (TX - 1);
-            cp_async8(xs + k * ld + 3 * r + c, in + t * tstride + c * TX + tx);
+    const int w3 = 3 * TX;
+    if (blockDim.x % w3 == 0) {
+        const int e = threadIdx.x % w3, t0 = threadIdx.x / w3, dtt = blockDim.x / w3;
+        const int c = e >> lt, tx = e & (TX - 1);
+        for (int r = 0; r < nr; r++) {
+            const int row = row0 + r;
+            const int z = (int)fdiv((unsigned)row, P.fd_ny), y = row - z * P.ny;
+            const float2* in = Bf.spec + (((long long)b * P.nz + z) * P.NT * P.ny + y) * 3 * TX + e;
+            float2* dst = xs + 3 * r + c;
+            for (int t = t0; t < P.NT; t += dtt) {
+                const int k = t * TX + tx;
+                if (k <= L) cp_async8(dst + k * ld, in + t * tstride);
+            }
+        }
+    } else {
+        for (int r = 0; r < nr; r++) {
+            const int row = row0 + r;
+            const int z = (int)fdiv((unsigned)row, P.fd_ny), y = row - z * P.ny;
+            const float2* in = Bf.spec + (((long long)b * P.nz + z) * P.NT * P.ny + y) * 3 * TX;
+            for (int idx = threadIdx.x; idx < 3 * (L + 1); idx += blockDim.x) {
+                const int c = idx / (L + 1), k = idx - c * (L + 1);
+                const int t = k >> lt, tx = k & (TX - 1);
+                cp_async8(xs + k * ld + 3 * r + c, in + t * tstride + c * TX + tx);
+            }
         }
     }
-    if (STAGE_M) {
-        for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) cp_async16(mrow + i, msrc + base + i);
-    } else if (threadIdx.x == 0) {
-        prefetch_l2(msrc + base, (unsigned)(nr * nx * sizeof(float4)));
-    }
+    // the block's own rows of m are read in the cell loop (through L1, which
+    // then serves the x and y neighbours as well)
+    if (threadIdx.x == 0) prefetch_l2(msrc + base, (unsigned)(nr * nx * sizeof(float4)));
     if (threadIdx.x == 0) {
         for (int q = 0; q < NM; q++) s_gamma[q] = stage_gamma(A, ip, st, mat, q);
         s_drive = (float)drive_factor(A, ip, st);
@@ -100,12 +119,14 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
         float2 a = xs[k * ld + line], bq = xs[kk * ld + line];
         float2 ca = conjf2(bq);
         float2 sum = cadd(a, ca), dif = csub(a, ca);
-        float2 wd = cmul(twiddle(Bf.tw, k * twstep, true), dif);
+        const float2 w = twiddle(Bf.tw, k * twstep, true);
+        float2 wd = cmul(w, dif);
         float2 zk = make_float2(sum.x - wd.y, sum.y + wd.x);   // sum + i wd
         if (k != 0 && kk != k) {
             float2 cb2 = conjf2(a);
             float2 sum2 = cadd(bq, cb2), dif2 = csub(bq, cb2);
-            float2 wd2 = cmul(twiddle(Bf.tw, kk * twstep, true), dif2);
+            // e^{2 pi i (L - k) / px} = -conj(e^{2 pi i k / px}) since px = 2 L
+            float2 wd2 = cmul(make_float2(-w.x, w.y), dif2);
             xs[kk * ld + line] = make_float2(sum2.x - wd2.y, sum2.y + wd2.x);
         }
         xs[k * ld + line] = zk;
@@ -126,19 +147,22 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
     const bool want_demag = A.terms & 1, want_exch = A.terms & 2;
     CellUpdate<NM> cu;
     cu.init(Bf, A, st, ip, s_gamma, s_drive, cb, (long long)A.inst0 * P.N);
-    const long long pl = (long long)nx * P.ny;
-    double xacc[NM];
+    const int pl = nx * P.ny;
+    float xacc[NM];
 #pragma unroll
-    for (int q = 0; q < NM; q++) xacc[q] = 0.0;
+    for (int q = 0; q < NM; q++) xacc[q] = 0.f;
     double macc[REC ? 3 : 1] = {};
     float emax = 0.f;
     bool bad = false;
+    // cell ii = r nx + x of the block; (x, r) advance by the block size
+    const int stepr = blockDim.x / nx, stepx = blockDim.x - stepr * nx;
+    int r = threadIdx.x / nx, x = threadIdx.x - r * nx;
     for (int ii = threadIdx.x; ii < nr * nx; ii += blockDim.x) {
-        const int r = (int)fdiv((unsigned)ii, P.fd_nx), x = ii - r * nx;
-        const int row = row0 + r;
-        const int z = (int)fdiv((unsigned)row, P.fd_ny), y = row - z * P.ny;
+        const int2 yz = s_yz[r];
+        const int y = yz.x, z = yz.y;
         const long long i = base + ii;
-        float4 m = STAGE_M ? mrow[ii] : __ldg(msrc + i);
+        const float4* mc = msrc + i;
+        const float4 m = __ldg(mc);
         const float Ms = m.w;
         float Bx = 0.f, By = 0.f, Bz = 0.f;
         if (want_demag) {
@@ -147,32 +171,41 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
             if (x & 1) { Bx = zx.y; By = zy.y; Bz = zz.y; }
             else { Bx = zx.x; By = zy.x; Bz = zz.x; }
         }
-        if (Ms > 0.f && want_exch) {
-            float hx = 0.f, hy = 0.f, hz = 0.f;
-            float4 q;
-#define MMCQ_NB(Q, C)                                                                   \
-    q = (Q);                                                                            \
-    if (q.w > 0.f) { hx += (C) * (q.x - m.x); hy += (C) * (q.y - m.y); hz += (C) * (q.z - m.z); }
-            if (x > 0) { MMCQ_NB(STAGE_M ? mrow[ii - 1] : __ldg(msrc + i - 1), mat.exch[0]) }
-            if (x + 1 < nx) { MMCQ_NB(STAGE_M ? mrow[ii + 1] : __ldg(msrc + i + 1), mat.exch[0]) }
-            if (y > 0) {
-                if (STAGE_M && r > 0) { MMCQ_NB(mrow[ii - nx], mat.exch[1]) }
-                else { MMCQ_NB(__ldg(msrc + i - nx), mat.exch[1]) }
-            }
-            if (y + 1 < P.ny) {
-                if (STAGE_M && r + 1 < nr) { MMCQ_NB(mrow[ii + nx], mat.exch[1]) }
-                else { MMCQ_NB(__ldg(msrc + i + nx), mat.exch[1]) }
-            }
-            if (z > 0) { MMCQ_NB(__ldg(msrc + i - pl), mat.exch[2]) }
-            if (z + 1 < P.nz) { MMCQ_NB(__ldg(msrc + i + pl), mat.exch[2]) }
-#undef MMCQ_NB
-            float inv = 1.f / Ms;
-            Bx += hx * inv; By += hy * inv; Bz += hz * inv;
+        if (want_exch) {
+            // sum over the six neighbours j of w_j (m_j - m_i), w_j = C_d for
+            // a non-empty neighbour and 0 for an empty one; a neighbour outside
+            // the grid is read as the cell itself (m_i - m_i = 0), so every
+            // load is unconditional and all six are in flight together
+            const float4 q0 = __ldg(mc + (x > 0 ? -1 : 0));
+            const float4 q1 = __ldg(mc + (x + 1 < nx ? 1 : 0));
+            const float4 q2 = __ldg(mc + (y > 0 ? -nx : 0));
+            const float4 q3 = __ldg(mc + (y + 1 < P.ny ? nx : 0));
+            const float4 q4 = __ldg(mc + (z > 0 ? -pl : 0));
+            const float4 q5 = __ldg(mc + (z + 1 < P.nz ? pl : 0));
+            const float2 nm = make_float2(-m.x, -m.y);
+            float2 hxy = make_float2(0.f, 0.f);
+            float hz = 0.f;
+            auto nb = [&](const float4& q, float C) {
+                const float w = q.w > 0.f ? C : 0.f;
+                hxy = __ffma2_rn(make_float2(w, w), __fadd2_rn(make_float2(q.x, q.y), nm), hxy);
+                hz = fmaf(w, q.z - m.z, hz);
+            };
+            nb(q0, mat.exch[0]); nb(q1, mat.exch[0]);
+            nb(q2, mat.exch[1]); nb(q3, mat.exch[1]);
+            nb(q4, mat.exch[2]); nb(q5, mat.exch[2]);
+            const float inv = Ms > 0.f ? __fdividef(1.f, Ms) : 0.f;
+            Bx += hxy.x * inv; By += hxy.y * inv; Bz += hz * inv;
         }
         cu.template run<REC>(mat, Bf, i, m, Bx, By, Bz, xacc, macc, emax, bad);
+        x += stepx;
+        r += stepr;
+        if (x >= nx) { x -= nx; r++; }
     }
     if (A.field_only) return;
-    stage_epilogue<REC, NM>(P, mat, Bf, A, b, blockIdx.x, P.nblk, xacc, emax, bad, s_red, s_redf, &s_last, macc);
+    double xd[NM];
+#pragma unroll
+    for (int q = 0; q < NM; q++) xd[q] = (double)xacc[q];
+    stage_epilogue<REC, NM>(P, mat, Bf, A, b, blockIdx.x, P.nblk, xd, emax, bad, s_red, s_redf, &s_last, macc);
 }
 
 cudaError_t launch_xinv(const Plan& P, const Material& mat, const Buffers& Bf, const StageArgs& A, int nb,

@@ -19,15 +19,8 @@ constexpr int xpass_min_blocks(int L) { return L >= 512 ? 3 : 5; }
 
 static inline int xthreads(const Plan& P) { return 3 * P.R * col_threads_per_column(P.L); }
 
-// Whether the x inverse stages its m rows in shared memory (short rows).
-__host__ __device__ constexpr bool xinv_stages_m(int L) { return L < 512; }
-
-// Shared memory of the x inverse: the half-spectrum lines and (short rows) the m rows.
-static inline size_t xinv_smem(const Plan& P) {
-    size_t n2 = (size_t)(P.L + 1) * xpass_ld(P.R);
-    n2 += n2 & 1;
-    return n2 * sizeof(float2) + (xinv_stages_m(P.L) ? (size_t)P.nx * P.R * sizeof(float4) : 0);
-}
+// Shared memory of the x inverse: the half-spectrum lines.
+static inline size_t xinv_smem(const Plan& P) { return (size_t)(P.L + 1) * xpass_ld(P.R) * sizeof(float2); }
 
 #define MMCQ_XCASES(F) F(1) F(2) F(4) F(8) F(16) F(32) F(64) F(128) F(256) F(512) F(1024)
 
