@@ -79,14 +79,23 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
     if (blockDim.x % w3 == 0) {
         const int e = threadIdx.x % w3, t0 = threadIdx.x / w3, dtt = blockDim.x / w3;
         const int c = e >> lt, tx = e & (TX - 1);
+        // 32-bit steps: the shared-window address and the offset in the spectrum
+        const unsigned sx = (unsigned)__cvta_generic_to_shared(xs) + 8u * (unsigned)((t0 * TX + tx) * ld + c);
+        const unsigned sstep = 8u * (unsigned)(dtt * TX * ld);
+        const int gstep = dtt * (int)tstride;
+        const int nt = t0 < P.NT ? (P.NT - 1 - t0) / dtt + 1 : 0;     // tiles of this thread
         for (int r = 0; r < nr; r++) {
             const int row = row0 + r;
             const int z = (int)fdiv((unsigned)row, P.fd_ny), y = row - z * P.ny;
-            const float2* in = Bf.spec + (((long long)b * P.nz + z) * P.NT * P.ny + y) * 3 * TX + e;
-            float2* dst = xs + 3 * r + c;
-            for (int t = t0; t < P.NT; t += dtt) {
-                const int k = t * TX + tx;
-                if (k <= L) cp_async8(dst + k * ld, in + t * tstride);
+            const float2* in = Bf.spec + (((long long)b * P.nz + z) * P.NT * P.ny + y) * 3 * TX + e +
+                               (long long)t0 * tstride;
+            unsigned sa = sx + 8u * (unsigned)(3 * r);
+            int go = 0, k = t0 * TX + tx;
+            for (int n = 0; n < nt; n++) {
+                if (k <= L) cp_async8s(sa, in + go);
+                sa += sstep;
+                go += gstep;
+                k += dtt * TX;
             }
         }
     } else {
