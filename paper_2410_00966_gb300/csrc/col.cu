@@ -216,12 +216,14 @@ __global__ void __launch_bounds__(256) k_zconv(Plan Pl, Buffers Bf, StageArgs A,
 // the same way, y[n] = IDFT_H(h_even)[n] + W_P^{-n} IDFT_H(h_odd)[n] for the
 // n < H rows kept; the halves add their parts through shared memory, each
 // storing H / 2 rows.  Threads [0, W) form half 0, [W, 2W) half 1.
-template <int P, int J>
-__device__ __forceinline__ void zsplit_forward(const ColArgs& C, float2* sm, int W, int col, const float2* in) {
+// FULL: all H rows hold data (nz = pz / 2), so no row is predicated; S: the
+// integer type of the row stride rs.
+template <int P, int J, bool FULL, typename S>
+__device__ __forceinline__ void zsplit_forward(const ColArgs& C, float2* sm, int W, int col, const float2* in, S rs) {
     constexpr int H = P / 2;
     float2 v[H];
 #pragma unroll
-    for (int r = 0; r < H; r++) v[r] = r < C.n_in ? in[r * C.in_r] : make_float2(0.f, 0.f);
+    for (int r = 0; r < H; r++) v[r] = (FULL || r < C.n_in) ? in[r * rs] : make_float2(0.f, 0.f);
     if (J == 1) {
 #pragma unroll
         for (int r = 1; r < H; r++) {
@@ -235,8 +237,8 @@ __device__ __forceinline__ void zsplit_forward(const ColArgs& C, float2* sm, int
     for (int m = 0; m < H; m++) sm[(2 * m + J) * W + col] = v[m];
 }
 
-template <int P, int J>
-__device__ __forceinline__ void zsplit_inverse(const ColArgs& C, float2* sm, int W, int col, float2* out) {
+template <int P, int J, bool FULL, typename S>
+__device__ __forceinline__ void zsplit_inverse(const ColArgs& C, float2* sm, int W, int col, float2* out, S rs) {
     constexpr int H = P / 2, Q = H / 2;
     float2 v[H];
 #pragma unroll
@@ -258,26 +260,36 @@ __device__ __forceinline__ void zsplit_inverse(const ColArgs& C, float2* sm, int
     for (int n = 0; n < Q; n++) {
         const int r = (J == 0 ? 0 : Q) + n;
         const float2 u = sm[r * W + col];
-        if (r < C.n_out) out[r * C.out_r] = make_float2(v[r].x + u.x, v[r].y + u.y);
+        if (FULL || r < C.n_out) out[r * rs] = cadd(v[r], u);
     }
 }
 
-template <int P>
+// TXC, GC: tile width and groups per block fixed at compile time (0: from the
+// plan), so that the shared-memory offsets are immediates; with them the rows
+// are all data (FULL) and the row strides fit in int.
+template <int P, int TXC, int GC>
 __global__ void __launch_bounds__(192, 5) k_zconv2(Plan Pl, Buffers Bf, StageArgs A, ColArgs C) {
     extern __shared__ float2 sm[];      // [P][W]
+    constexpr bool FIXED = TXC > 0 && GC > 0;
     const int b = A.inst0 + blockIdx.z;
     if (stage_skips(Bf.st[b], A)) return;
-    const int TX = Pl.TX, lt = Pl.lt;
-    const int W = C.G * 3 * TX;
+    const int TX = FIXED ? TXC : Pl.TX, lt = FIXED ? ilog2<(TXC > 0 ? TXC : 1)>() : Pl.lt;
+    const int Gb = FIXED ? GC : C.G;
+    const int W = Gb * 3 * TX;
     const int half = threadIdx.x >= W;
     const int col = threadIdx.x - half * W;
     const int q = col >> lt;
     const int g = q / 3, c = q - 3 * g, tx = col & (TX - 1);
-    const int t = blockIdx.y, o0 = blockIdx.x * C.G;
+    const int t = blockIdx.y, o0 = blockIdx.x * Gb;
     const long long off_in = b * C.in_b + (o0 + g) * C.in_o + t * C.in_t + c * TX + tx;
     const long long off_out = b * C.out_b + (o0 + g) * C.out_o + t * C.out_t + c * TX + tx;
-    if (half == 0) zsplit_forward<P, 0>(C, sm, W, col, C.in + off_in);
-    else zsplit_forward<P, 1>(C, sm, W, col, C.in + off_in);
+    if (FIXED) {
+        if (half == 0) zsplit_forward<P, 0, true>(C, sm, W, col, C.in + off_in, (int)C.in_r);
+        else zsplit_forward<P, 1, true>(C, sm, W, col, C.in + off_in, (int)C.in_r);
+    } else {
+        if (half == 0) zsplit_forward<P, 0, false>(C, sm, W, col, C.in + off_in, C.in_r);
+        else zsplit_forward<P, 1, false>(C, sm, W, col, C.in + off_in, C.in_r);
+    }
     __syncthreads();
 
     // product at every (kz, g, tx) point of the block: symmetric kernel
@@ -285,7 +297,7 @@ __global__ void __launch_bounds__(192, 5) k_zconv2(Plan Pl, Buffers Bf, StageArg
     // yz in both.  The block has 2 W = 6 G TX threads, so a thread keeps its
     // (g, tx) point and takes every sixth mirror pair (kz, P - kz): one read
     // of the stored kernel row serves both, with xz and yz negated for P - kz.
-    const int GT = C.G * TX;                      // power of two
+    const int GT = Gb * TX;                       // power of two
     const int lgt = __ffs(GT) - 1;
     const long long zs = (long long)Pl.hyk * Pl.NT * TX * 6;
     const int p = threadIdx.x & (GT - 1);
@@ -325,8 +337,13 @@ __global__ void __launch_bounds__(192, 5) k_zconv2(Plan Pl, Buffers Bf, StageArg
         }
     }
     __syncthreads();
-    if (half == 0) zsplit_inverse<P, 0>(C, sm, W, col, C.out + off_out);
-    else zsplit_inverse<P, 1>(C, sm, W, col, C.out + off_out);
+    if (FIXED) {
+        if (half == 0) zsplit_inverse<P, 0, true>(C, sm, W, col, C.out + off_out, (int)C.out_r);
+        else zsplit_inverse<P, 1, true>(C, sm, W, col, C.out + off_out, (int)C.out_r);
+    } else {
+        if (half == 0) zsplit_inverse<P, 0, false>(C, sm, W, col, C.out + off_out, C.out_r);
+        else zsplit_inverse<P, 1, false>(C, sm, W, col, C.out + off_out, C.out_r);
+    }
 }
 
 // y passes with P = 2 PH longer than the register path holds (P = 2048): the
@@ -472,12 +489,19 @@ static cudaError_t launch_z(const Plan& Pl, const Buffers& Bf, const StageArgs& 
     return cudaGetLastError();
 }
 
+// The fixed-shape z pass: tiles of 8 kx columns, 4 ky per block, all pz / 2 rows data.
+static bool z2_fixed(const Plan& Pl, const ColArgs& C, int P) {
+    return Pl.TX == 8 && C.G == 4 && C.n_in == P / 2 && C.n_out == P / 2 && (long long)C.in_r * P < (1LL << 31) &&
+           (long long)C.out_r * P < (1LL << 31);
+}
+
 template <int P>
 static cudaError_t launch_z2(const Plan& Pl, const Buffers& Bf, const StageArgs& A, const ColArgs& C, int nb,
                              cudaStream_t s) {
     const int W = C.G * 3 * Pl.TX;
     dim3 grid((Pl.py + C.G - 1) / C.G, Pl.NT, nb);
-    k_zconv2<P><<<grid, 2 * W, (size_t)P * W * sizeof(float2), s>>>(Pl, Bf, A, C);
+    if (z2_fixed(Pl, C, P)) k_zconv2<P, 8, 4><<<grid, 2 * W, (size_t)P * W * sizeof(float2), s>>>(Pl, Bf, A, C);
+    else k_zconv2<P, 0, 0><<<grid, 2 * W, (size_t)P * W * sizeof(float2), s>>>(Pl, Bf, A, C);
     return cudaGetLastError();
 }
 
@@ -662,11 +686,15 @@ cudaError_t col_init() {
         return e;
     MMCQ_SET(2) MMCQ_SET(4) MMCQ_SET(8) MMCQ_SET(16) MMCQ_SET(32)
 #undef MMCQ_SET
-    if ((e = cudaFuncSetAttribute(k_zconv2<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(k_zconv2<32, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_zconv2<32, 8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
         return e;
     if ((e = cudaFuncSetAttribute(k_col_split<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(k_zconv2<32>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(k_zconv2<32, 0, 0>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_zconv2<32, 8, 4>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
         return e;
     return cudaSuccess;
 }
