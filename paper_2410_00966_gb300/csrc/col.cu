@@ -77,23 +77,34 @@ __device__ __forceinline__ void block_product(const Plan& P, const Buffers& Bf, 
 // One block = G groups x ncomp x TX columns (W columns) x N1 threads per
 // column.  Groups are consecutive kx tiles (y passes) or consecutive outer
 // indices (z pass); in both cases consecutive columns are adjacent in memory.
-template <int P>
+// Transform lengths with a fixed-shape instantiation of k_col_reg.
+constexpr bool col_fixed_len(int P) { return P >= 64 && P <= 512; }
+
+// WC > 0: the block is one kx tile of WC / 3 columns with all three
+// components (G = 1), rows WC apart in both spectra, fixed at compile time so
+// that the row and shared-memory offsets are immediates.
+template <int P, int WC>
 __global__ void __launch_bounds__(512) k_col_reg(Plan Pl, Buffers Bf, StageArgs A, ColArgs C) {
     constexpr int NPT = ColShape<P>::NPT, N1 = ColShape<P>::N1;
+    constexpr bool FIXED = WC > 0;
     extern __shared__ float2 sm[];
+    const int ncomp = FIXED ? 3 : C.ncomp;
     const int bz = blockIdx.z;
-    const int b = A.inst0 + (C.ncomp == 3 ? bz : bz / 3);
-    const int c0 = C.ncomp == 3 ? 0 : bz % 3;
+    const int b = A.inst0 + (ncomp == 3 ? bz : bz / 3);
+    const int c0 = ncomp == 3 ? 0 : bz % 3;
     if (stage_skips(Bf.st[b], A)) return;
-    const int TX = Pl.TX;
-    const int rw = C.ncomp * TX;
-    const int W = C.G * rw;
+    const int TX = FIXED ? WC / 3 : Pl.TX;
+    const int lt = FIXED ? ilog2<(FIXED ? WC / 3 : 1)>() : Pl.lt;
+    const int G = FIXED ? 1 : C.G;
+    const int rw = ncomp * TX;
+    const int W = G * rw;
+    const long long in_r = FIXED ? WC : C.in_r, out_r = FIXED ? WC : C.out_r;
     const int col = threadIdx.x % W;
     const int j = threadIdx.x / W;
-    const int g = C.ncomp == 3 ? (col >> Pl.lt) / 3 : (col >> Pl.lt);
+    const int g = ncomp == 3 ? (col >> lt) / 3 : (col >> lt);
     const int e = col - g * rw;
-    const int t0 = C.group_tiles ? blockIdx.x * C.G : blockIdx.y;
-    const int o0 = C.group_tiles ? blockIdx.y : blockIdx.x * C.G;
+    const int t0 = C.group_tiles ? blockIdx.x * G : blockIdx.y;
+    const int o0 = C.group_tiles ? blockIdx.y : blockIdx.x * G;
     const int t = C.group_tiles ? t0 + g : t0;
     const int o = C.group_tiles ? o0 : o0 + g;
     const bool valid = t < Pl.NT && o < C.nouter;
@@ -104,7 +115,7 @@ __global__ void __launch_bounds__(512) k_col_reg(Plan Pl, Buffers Bf, StageArgs 
 #pragma unroll
     for (int n2 = 0; n2 < NPT; n2++) {
         const int r = j + N1 * n2;
-        v[n2] = (valid && r < C.n_in) ? in[r * C.in_r] : make_float2(0.f, 0.f);
+        v[n2] = (valid && r < C.n_in) ? in[r * in_r] : make_float2(0.f, 0.f);
     }
     if (C.fwd) col_fft<P, false>(v, sm, W, col, j, Bf.tw, Pl.twn);
     if (C.mult) {
@@ -123,7 +134,7 @@ __global__ void __launch_bounds__(512) k_col_reg(Plan Pl, Buffers Bf, StageArgs 
 #pragma unroll
     for (int i = 0; i < NPT; i++) {
         const int r = transformed ? col_out_row<P>(j, i) : j + N1 * i;
-        if (r < C.n_out) out[r * C.out_r] = v[i];
+        if (r < C.n_out) out[r * out_r] = v[i];
     }
 }
 
@@ -476,7 +487,16 @@ template <int P>
 static cudaError_t launch_reg(const Plan& Pl, const Buffers& Bf, const StageArgs& A, const ColArgs& C, dim3 grid,
                               int W, cudaStream_t s) {
     constexpr int N1 = ColShape<P>::N1;
-    k_col_reg<P><<<grid, W * N1, (size_t)P * W * sizeof(float2), s>>>(Pl, Bf, A, C);
+    const bool fixed = Pl.TX == 8 && C.ncomp == 3 && C.G == 1 && !C.mult && C.group_tiles && C.in_r == 24 &&
+                       C.out_r == 24;
+    if constexpr (col_fixed_len(P)) {
+        if (fixed) {
+            k_col_reg<P, 24><<<grid, W * N1, (size_t)P * W * sizeof(float2), s>>>(Pl, Bf, A, C);
+            return cudaGetLastError();
+        }
+    }
+    (void)fixed;
+    k_col_reg<P, 0><<<grid, W * N1, (size_t)P * W * sizeof(float2), s>>>(Pl, Bf, A, C);
     return cudaGetLastError();
 }
 
@@ -675,11 +695,13 @@ cudaError_t col_init() {
     const int lim = 200 * 1024;
     if ((e = cudaFuncSetAttribute(k_col_gen<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_col_gen<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess) return e;
-#define MMCQ_SET(Pv)                                                                                              \
-    if ((e = cudaFuncSetAttribute(k_col_reg<Pv>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess) \
+#define MMCQ_SET(Pv, Wv)                                                                                 \
+    if ((e = cudaFuncSetAttribute(k_col_reg<Pv, Wv>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != \
+        cudaSuccess)                                                                                        \
         return e;
-    MMCQ_SET(1) MMCQ_SET(2) MMCQ_SET(4) MMCQ_SET(8) MMCQ_SET(16) MMCQ_SET(32) MMCQ_SET(64) MMCQ_SET(128)
-    MMCQ_SET(256) MMCQ_SET(512) MMCQ_SET(1024)
+    MMCQ_SET(1, 0) MMCQ_SET(2, 0) MMCQ_SET(4, 0) MMCQ_SET(8, 0) MMCQ_SET(16, 0) MMCQ_SET(32, 0) MMCQ_SET(64, 0)
+    MMCQ_SET(128, 0) MMCQ_SET(256, 0) MMCQ_SET(512, 0) MMCQ_SET(1024, 0)
+    MMCQ_SET(64, 24) MMCQ_SET(128, 24) MMCQ_SET(256, 24) MMCQ_SET(512, 24)
 #undef MMCQ_SET
 #define MMCQ_SET(Pv)                                                                                            \
     if ((e = cudaFuncSetAttribute(k_zconv<Pv>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess) \
