@@ -27,17 +27,22 @@ namespace mq {
 // x forward: stage input, M = Ms m_s, packed real FFT of length px = 2L.
 // R consecutive rows per block; shared memory zs[n][line], line = 3 r + comp.
 // ---------------------------------------------------------------------------
-template <int L>
+// FX: the fixed shape of the large grids (see xpass_fixed) at compile time.
+template <int L, bool FX>
 __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xfwd(Plan P, Buffers Bf, StageArgs A) {
     constexpr int NPT = ColShape<L>::NPT, N1 = ColShape<L>::N1;
+    constexpr int RF = xpass_rows(L);
     extern __shared__ float2 sm[];
     const int b = A.inst0 + blockIdx.y;
     const InstState& st = Bf.st[b];
     if (stage_skips(st, A)) return;
-    const int nx = P.nx;
-    const int row0 = blockIdx.x * P.R;
-    const int nr = min(P.R, P.nrows - row0);
-    const int ld = xpass_ld(P.R);
+    const int Rb = FX ? RF : P.R;
+    const int nx = FX ? L : P.nx;
+    const int px = FX ? 2 * L : P.px;
+    const int nthr = FX ? 3 * RF * N1 : (int)blockDim.x;
+    const int row0 = blockIdx.x * Rb;
+    const int nr = FX ? RF : min(P.R, P.nrows - row0);
+    const int ld = xpass_ld(Rb);
     const long long base = (long long)b * P.N + (long long)row0 * nx;
     const float4* m0 = Bf.m[st.mcur] + base;
     StageInput si;
@@ -51,17 +56,17 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xfwd(Pla
     }
     float2* zs = sm;
     float2* stw = sm + L * ld;                 // exp(-2 pi i e / px), e < px
-    const int tws = P.twn / P.px;
-    for (int e = threadIdx.x; e < P.px; e += blockDim.x) stw[e] = __ldg(Bf.tw + e * tws);
+    const int tws = P.twn / px;
+    for (int e = threadIdx.x; e < px; e += nthr) stw[e] = __ldg(Bf.tw + e * tws);
     // rows nx/2.. of the packed line are zero padding (rows below are all written)
-    for (int i = (nx >> 1) * ld + threadIdx.x; i < L * ld; i += blockDim.x) zs[i] = make_float2(0.f, 0.f);
+    for (int i = (nx >> 1) * ld + threadIdx.x; i < L * ld; i += nthr) zs[i] = make_float2(0.f, 0.f);
     __syncthreads();
 
 
-    for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) {
+    for (int i = threadIdx.x; i < nr * nx; i += nthr) {
         float4 v = m0[i];
         si.apply(Bf, v, i);
-        const int r = (int)fdiv((unsigned)i, P.fd_nx), x = i - r * nx;
+        const int r = FX ? i / L : (int)fdiv((unsigned)i, P.fd_nx), x = i - r * nx;
         float2* zr = zs + (x >> 1) * ld + 3 * r;
         float Mx = v.w * v.x, My = v.w * v.y, Mz = v.w * v.z;
         if (x & 1) { zr[0].y = Mx; zr[1].y = My; zr[2].y = Mz; }
@@ -69,19 +74,20 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xfwd(Pla
     }
     __syncthreads();
     {
-        const int nl = 3 * P.R;
+        const int nl = 3 * Rb;
         const int line = threadIdx.x % nl, j = threadIdx.x / nl;
         float2 v[NPT];
 #pragma unroll
         for (int n2 = 0; n2 < NPT; n2++) v[n2] = zs[(j + N1 * n2) * ld + line];
-        col_fft<L, false, true>(v, zs, ld, line, j, stw, P.px);
+        col_fft<L, false, true>(v, zs, ld, line, j, stw, px);
 #pragma unroll
         for (int i = 0; i < NPT; i++) zs[col_out_row<L>(j, i) * ld + line] = v[i];
     }
     __syncthreads();
 
     // X[k] = E[k] + W^k O[k], E = (Z[k] + conj Z[L-k]) / 2, O = -i (Z[k] - conj Z[L-k]) / 2
-    const int TX = P.TX, lt = P.lt;
+    const int TX = FX ? 8 : P.TX, lt = FX ? 3 : P.lt;
+    const int NT = FX ? L / 8 + 1 : P.NT;
     const long long tstride = (long long)P.ny * 3 * TX;
     auto unpack = [&](int k, int line) {
         float2 X = make_float2(0.f, 0.f);
@@ -98,23 +104,23 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xfwd(Pla
     // tile t of a row holds the 3 TX values (c, tx) contiguously; when 3 TX
     // divides the block, a thread keeps one (c, tx) and steps over the tiles
     const int w3 = 3 * TX;
-    if (blockDim.x % w3 == 0) {
-        const int e = threadIdx.x % w3, t0 = threadIdx.x / w3, dtt = blockDim.x / w3;
+    if (nthr % w3 == 0) {
+        const int e = threadIdx.x % w3, t0 = threadIdx.x / w3, dtt = nthr / w3;
         const int c = e >> lt, tx = e & (TX - 1);
         for (int r = 0; r < nr; r++) {
             const int row = row0 + r;
             const int z = (int)fdiv((unsigned)row, P.fd_ny), y = row - z * P.ny;
-            float2* out = Bf.spec + (((long long)b * P.nz + z) * P.NT * P.ny + y) * 3 * TX + e;
-            for (int t = t0; t < P.NT; t += dtt) out[t * tstride] = unpack(t * TX + tx, 3 * r + c);
+            float2* out = Bf.spec + (((long long)b * P.nz + z) * NT * P.ny + y) * 3 * TX + e;
+            for (int t = t0; t < NT; t += dtt) out[t * tstride] = unpack(t * TX + tx, 3 * r + c);
         }
         return;
     }
-    const int W3 = P.NT * 3 * TX;
+    const int W3 = NT * 3 * TX;
     for (int r = 0; r < nr; r++) {
         const int row = row0 + r;
         const int z = (int)fdiv((unsigned)row, P.fd_ny), y = row - z * P.ny;
-        float2* out = Bf.spec + (((long long)b * P.nz + z) * P.NT * P.ny + y) * 3 * TX;
-        for (int idx = threadIdx.x; idx < W3; idx += blockDim.x) {
+        float2* out = Bf.spec + (((long long)b * P.nz + z) * NT * P.ny + y) * 3 * TX;
+        for (int idx = threadIdx.x; idx < W3; idx += nthr) {
             const int t = (idx >> lt) / 3;
             const int ctx = idx - t * 3 * TX;
             const int c = ctx >> lt, tx = ctx & (TX - 1);
@@ -261,8 +267,16 @@ cudaError_t launch_xfwd(const Plan& P, const Buffers& Bf, const StageArgs& A, in
     dim3 grid(P.nblk, nb);
     const int th = xthreads(P);
     const size_t sm = xfwd_smem(P);
+    if (xpass_fixed(P)) {
+        switch (P.L) {
+#define MMCQ_CASE(Lv) case Lv: k_xfwd<Lv, true><<<grid, th, sm, s>>>(P, Bf, A); return cudaGetLastError();
+            MMCQ_XFIXED(MMCQ_CASE)
+#undef MMCQ_CASE
+            default: break;
+        }
+    }
     switch (P.L) {
-#define MMCQ_CASE(Lv) case Lv: k_xfwd<Lv><<<grid, th, sm, s>>>(P, Bf, A); break;
+#define MMCQ_CASE(Lv) case Lv: k_xfwd<Lv, false><<<grid, th, sm, s>>>(P, Bf, A); break;
         MMCQ_XCASES(MMCQ_CASE)
 #undef MMCQ_CASE
         default: return cudaErrorInvalidValue;
@@ -313,10 +327,17 @@ cudaError_t set_smem_limits() {
     upload_tableaux();
     if ((e = upload_tw32()) != cudaSuccess) return e;
     const int lim = 200 * 1024;
-#define MMCQ_CASE(Lv)                                                                                         \
-    if ((e = cudaFuncSetAttribute(k_xfwd<Lv>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess) \
+#define MMCQ_CASE(Lv)                                                                                \
+    if ((e = cudaFuncSetAttribute(k_xfwd<Lv, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != \
+        cudaSuccess)                                                                                        \
         return e;
     MMCQ_XCASES(MMCQ_CASE)
+#undef MMCQ_CASE
+#define MMCQ_CASE(Lv)                                                                               \
+    if ((e = cudaFuncSetAttribute(k_xfwd<Lv, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != \
+        cudaSuccess)                                                                                       \
+        return e;
+    MMCQ_XFIXED(MMCQ_CASE)
 #undef MMCQ_CASE
     if ((e = xinv_init()) != cudaSuccess) return e;
     return col_init();

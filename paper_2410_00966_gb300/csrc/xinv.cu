@@ -24,9 +24,12 @@ namespace mq {
 // (the last stage of a step with recording on); NM: cavity modes compiled in
 // (1, or MAX_MODES when more than one mode is enabled).  Separate
 // instantiations so that the common launches carry no extra accumulators.
-template <int L, bool REC, int NM>
+// FX: the fixed shape of the large grids (rows of nx = L cells, XPASS_ROWS(L)
+// rows per block with none left over, tiles of 8 kx columns) at compile time.
+template <int L, bool REC, int NM, bool FX>
 __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Plan P, Material mat, Buffers Bf, StageArgs A) {
     constexpr int NPT = ColShape<L>::NPT, N1 = ColShape<L>::N1;
+    constexpr int RF = xpass_rows(L);
     extern __shared__ float2 sm[];
     __shared__ double s_red[32];
     __shared__ float s_redf[32];
@@ -38,10 +41,13 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
     const InstState& st = Bf.st[b];
     if (stage_skips(st, A)) return;
     const InstParams& ip = Bf.ip[b];
-    const int TX = P.TX, nx = P.nx, lt = P.lt;
-    const int row0 = blockIdx.x * P.R;
-    const int nr = min(P.R, P.nrows - row0);
-    const int ld = xpass_ld(P.R);
+    const int Rb = FX ? RF : P.R;
+    const int TX = FX ? 8 : P.TX, nx = FX ? L : P.nx, lt = FX ? 3 : P.lt;
+    const int NT = FX ? L / 8 + 1 : P.NT;
+    const int nthr = FX ? 3 * RF * N1 : (int)blockDim.x;
+    const int row0 = blockIdx.x * Rb;
+    const int nr = FX ? RF : min(P.R, P.nrows - row0);
+    const int ld = xpass_ld(Rb);
     const long long cb = (long long)b * P.N;
     const long long base = cb + (long long)row0 * nx;
     const int s = A.stage;
@@ -76,18 +82,18 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
     // and steps over the tiles.
     const long long tstride = (long long)P.ny * 3 * TX;
     const int w3 = 3 * TX;
-    if (blockDim.x % w3 == 0) {
-        const int e = threadIdx.x % w3, t0 = threadIdx.x / w3, dtt = blockDim.x / w3;
+    if (nthr % w3 == 0) {
+        const int e = threadIdx.x % w3, t0 = threadIdx.x / w3, dtt = nthr / w3;
         const int c = e >> lt, tx = e & (TX - 1);
         // 32-bit steps: the shared-window address and the offset in the spectrum
         const unsigned sx = (unsigned)__cvta_generic_to_shared(xs) + 8u * (unsigned)((t0 * TX + tx) * ld + c);
         const unsigned sstep = 8u * (unsigned)(dtt * TX * ld);
         const int gstep = dtt * (int)tstride;
-        const int nt = t0 < P.NT ? (P.NT - 1 - t0) / dtt + 1 : 0;     // tiles of this thread
+        const int nt = t0 < NT ? (NT - 1 - t0) / dtt + 1 : 0;     // tiles of this thread
         for (int r = 0; r < nr; r++) {
             const int row = row0 + r;
             const int z = (int)fdiv((unsigned)row, P.fd_ny), y = row - z * P.ny;
-            const float2* in = Bf.spec + (((long long)b * P.nz + z) * P.NT * P.ny + y) * 3 * TX + e +
+            const float2* in = Bf.spec + (((long long)b * P.nz + z) * NT * P.ny + y) * 3 * TX + e +
                                (long long)t0 * tstride;
             unsigned sa = sx + 8u * (unsigned)(3 * r);
             int go = 0, k = t0 * TX + tx;
@@ -102,8 +108,8 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
         for (int r = 0; r < nr; r++) {
             const int row = row0 + r;
             const int z = (int)fdiv((unsigned)row, P.fd_ny), y = row - z * P.ny;
-            const float2* in = Bf.spec + (((long long)b * P.nz + z) * P.NT * P.ny + y) * 3 * TX;
-            for (int idx = threadIdx.x; idx < 3 * (L + 1); idx += blockDim.x) {
+            const float2* in = Bf.spec + (((long long)b * P.nz + z) * NT * P.ny + y) * 3 * TX;
+            for (int idx = threadIdx.x; idx < 3 * (L + 1); idx += nthr) {
                 const int c = idx / (L + 1), k = idx - c * (L + 1);
                 const int t = k >> lt, tx = k & (TX - 1);
                 cp_async8(xs + k * ld + 3 * r + c, in + t * tstride + c * TX + tx);
@@ -122,7 +128,7 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
     // Z[k] = (X[k] + conj X[L-k]) + i e^{+2 pi i k / px} (X[k] - conj X[L-k]), in place by pairs
     const int twstep = P.twn / P.px;
     constexpr int HALF = L / 2 + 1;
-    for (int idx = threadIdx.x; idx < 3 * nr * HALF; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < 3 * nr * HALF; idx += nthr) {
         const int line = idx / HALF, k = idx - line * HALF;
         const int kk = L - k;
         float2 a = xs[k * ld + line], bq = xs[kk * ld + line];
@@ -142,7 +148,7 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
     }
     __syncthreads();
     {
-        const int nl = 3 * P.R;
+        const int nl = 3 * Rb;
         const int line = threadIdx.x % nl, j = threadIdx.x / nl;
         float2 v[NPT];
 #pragma unroll
@@ -164,9 +170,9 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
     float emax = 0.f;
     bool bad = false;
     // cell ii = r nx + x of the block; (x, r) advance by the block size
-    const int stepr = blockDim.x / nx, stepx = blockDim.x - stepr * nx;
+    const int stepr = nthr / nx, stepx = nthr - stepr * nx;
     int r = threadIdx.x / nx, x = threadIdx.x - r * nx;
-    for (int ii = threadIdx.x; ii < nr * nx; ii += blockDim.x) {
+    for (int ii = threadIdx.x; ii < nr * nx; ii += nthr) {
         const int2 yz = s_yz[r];
         const int y = yz.x, z = yz.y;
         const long long i = base + ii;
@@ -224,15 +230,26 @@ cudaError_t launch_xinv(const Plan& P, const Material& mat, const Buffers& Bf, c
     const size_t sm = xinv_smem(P);
     const bool rec = A.record > 0 && !A.field_only && A.stage == (A.kind == KIND_RK4 ? 3 : 6);
     const bool multi = A.nmodes > 1;
+    if (!multi && !rec && xpass_fixed(P)) {
+        switch (P.L) {
+#define MMCQ_CASE(Lv)                                                          \
+    case Lv:                                                                   \
+        k_xinv<Lv, false, 1, true><<<grid, th, sm, s>>>(P, mat, Bf, A);        \
+        return cudaGetLastError();
+            MMCQ_XFIXED(MMCQ_CASE)
+#undef MMCQ_CASE
+            default: break;
+        }
+    }
     switch (P.L) {
 #define MMCQ_CASE(Lv)                                                                          \
     case Lv:                                                                                   \
         if (multi) {                                                                           \
-            if (rec) k_xinv<Lv, true, MAX_MODES><<<grid, th, sm, s>>>(P, mat, Bf, A);          \
-            else k_xinv<Lv, false, MAX_MODES><<<grid, th, sm, s>>>(P, mat, Bf, A);             \
+            if (rec) k_xinv<Lv, true, MAX_MODES, false><<<grid, th, sm, s>>>(P, mat, Bf, A);   \
+            else k_xinv<Lv, false, MAX_MODES, false><<<grid, th, sm, s>>>(P, mat, Bf, A);      \
         } else {                                                                               \
-            if (rec) k_xinv<Lv, true, 1><<<grid, th, sm, s>>>(P, mat, Bf, A);                  \
-            else k_xinv<Lv, false, 1><<<grid, th, sm, s>>>(P, mat, Bf, A);                     \
+            if (rec) k_xinv<Lv, true, 1, false><<<grid, th, sm, s>>>(P, mat, Bf, A);           \
+            else k_xinv<Lv, false, 1, false><<<grid, th, sm, s>>>(P, mat, Bf, A);              \
         }                                                                                      \
         break;
         MMCQ_XCASES(MMCQ_CASE)
@@ -253,12 +270,16 @@ cudaError_t xinv_init() {
     upload_tableaux();
     if ((e = upload_tw32()) != cudaSuccess) return e;
     const int lim = 200 * 1024;
-#define MMCQ_CASE(Lv)                                                                   \
-    if ((e = xinv_attr(k_xinv<Lv, false, 1>, lim)) != cudaSuccess) return e;            \
-    if ((e = xinv_attr(k_xinv<Lv, true, 1>, lim)) != cudaSuccess) return e;             \
-    if ((e = xinv_attr(k_xinv<Lv, false, MAX_MODES>, lim)) != cudaSuccess) return e;    \
-    if ((e = xinv_attr(k_xinv<Lv, true, MAX_MODES>, lim)) != cudaSuccess) return e;
+#define MMCQ_CASE(Lv)                                                                          \
+    if ((e = xinv_attr(k_xinv<Lv, false, 1, false>, lim)) != cudaSuccess) return e;            \
+    if ((e = xinv_attr(k_xinv<Lv, true, 1, false>, lim)) != cudaSuccess) return e;             \
+    if ((e = xinv_attr(k_xinv<Lv, false, MAX_MODES, false>, lim)) != cudaSuccess) return e;    \
+    if ((e = xinv_attr(k_xinv<Lv, true, MAX_MODES, false>, lim)) != cudaSuccess) return e;
     MMCQ_XCASES(MMCQ_CASE)
+#undef MMCQ_CASE
+#define MMCQ_CASE(Lv) \
+    if ((e = xinv_attr(k_xinv<Lv, false, 1, true>, lim)) != cudaSuccess) return e;
+    MMCQ_XFIXED(MMCQ_CASE)
 #undef MMCQ_CASE
     return cudaSuccess;
 }
