@@ -279,7 +279,7 @@ __device__ __forceinline__ void zsplit_inverse(const ColArgs& C, float2* sm, int
 // plan), so that the shared-memory offsets are immediates; with them the rows
 // are all data (FULL) and the row strides fit in int.
 template <int P, int TXC, int GC>
-__global__ void __launch_bounds__(192, 5) k_zconv2(Plan Pl, Buffers Bf, StageArgs A, ColArgs C) {
+__global__ void __launch_bounds__(192, 6) k_zconv2(Plan Pl, Buffers Bf, StageArgs A, ColArgs C) {
     extern __shared__ float2 sm[];      // [P][W]
     constexpr bool FIXED = TXC > 0 && GC > 0;
     const int b = A.inst0 + blockIdx.z;
