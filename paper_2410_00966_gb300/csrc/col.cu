@@ -366,27 +366,39 @@ __global__ void __launch_bounds__(192, 6) k_zconv2(Plan Pl, Buffers Bf, StageArg
 // The same threads do both halves one after the other; in the inverse the odd
 // half is added onto the rows the even half stored (each row stays with one
 // thread, so the read-back is the thread's own store).
-template <int PH>
+// FIXED: one component of one 8-column tile per block (G = 1), rows 24 apart
+// in both spectra, at compile time.
+template <int PH, bool FIXED>
 __global__ void __launch_bounds__(512) k_col_split(Plan Pl, Buffers Bf, StageArgs A, ColArgs C) {
     constexpr int NPT = ColShape<PH>::NPT, N1 = ColShape<PH>::N1;
     constexpr int P = 2 * PH;
     extern __shared__ float2 sm[];
+    const int ncomp = FIXED ? 1 : C.ncomp;
     const int bz = blockIdx.z;
-    const int b = A.inst0 + (C.ncomp == 3 ? bz : bz / 3);
-    const int c0 = C.ncomp == 3 ? 0 : bz % 3;
+    const int b = A.inst0 + (ncomp == 3 ? bz : bz / 3);
+    const int c0 = ncomp == 3 ? 0 : bz % 3;
     if (stage_skips(Bf.st[b], A)) return;
-    const int TX = Pl.TX;
-    const int rw = C.ncomp * TX;
-    const int W = C.G * rw;
+    const int TX = FIXED ? 8 : Pl.TX, lt = FIXED ? 3 : Pl.lt;
+    const int G = FIXED ? 1 : C.G;
+    const long long in_r = FIXED ? 24 : C.in_r, out_r = FIXED ? 24 : C.out_r;
+    const int rw = ncomp * TX;
+    const int W = G * rw;
     const int col = threadIdx.x % W;
     const int j = threadIdx.x / W;
-    const int g = C.ncomp == 3 ? (col >> Pl.lt) / 3 : (col >> Pl.lt);
+    const int g = ncomp == 3 ? (col >> lt) / 3 : (col >> lt);
     const int e = col - g * rw;
-    const int t = blockIdx.x * C.G + g, o = blockIdx.y;          // tiles are the groups here
+    const int t = blockIdx.x * G + g, o = blockIdx.y;          // tiles are the groups here
     const bool valid = t < Pl.NT && o < C.nouter;
     const float2* in = C.in + b * C.in_b + o * C.in_o + t * C.in_t + c0 * TX + e;
     float2* out = C.out + b * C.out_b + o * C.out_o + t * C.out_t + c0 * TX + e;
-    const int tstep = Pl.twn / P;
+    // exp(-2 pi i e / P), e < P, after the transform buffer: the odd-half
+    // twiddles W_P^r and the four-step twiddles W_PH^{j k2} = W_P^{2 j k2}
+    float2* stw = sm + PH * W;
+    {
+        const int tstep = Pl.twn / P;
+        for (int q = threadIdx.x; q < P; q += blockDim.x) stw[q] = __ldg(Bf.tw + q * tstep);
+    }
+    __syncthreads();
 #pragma unroll 1
     for (int J = 0; J < 2; J++) {
         float2 v[NPT];
@@ -394,32 +406,32 @@ __global__ void __launch_bounds__(512) k_col_split(Plan Pl, Buffers Bf, StageArg
 #pragma unroll
             for (int n2 = 0; n2 < NPT; n2++) {
                 const int r = j + N1 * n2;
-                float2 x = (valid && r < C.n_in) ? in[r * C.in_r] : make_float2(0.f, 0.f);
-                if (J == 1) x = cmul(x, twiddle(Bf.tw, r * tstep, false));
+                float2 x = (valid && r < C.n_in) ? in[r * in_r] : make_float2(0.f, 0.f);
+                if (J == 1) x = cmul(x, stw[r]);
                 v[n2] = x;
             }
-            col_fft<PH, false>(v, sm, W, col, j, Bf.tw, Pl.twn);
+            col_fft<PH, false, true>(v, sm, W, col, j, stw, P);
             if (valid) {
 #pragma unroll
-                for (int i = 0; i < NPT; i++) out[(2 * col_out_row<PH>(j, i) + J) * C.out_r] = v[i];
+                for (int i = 0; i < NPT; i++) out[(2 * col_out_row<PH>(j, i) + J) * out_r] = v[i];
             }
         } else {
 #pragma unroll
             for (int n2 = 0; n2 < NPT; n2++) {
                 const int r = 2 * (j + N1 * n2) + J;
-                v[n2] = (valid && r < C.n_in) ? in[r * C.in_r] : make_float2(0.f, 0.f);
+                v[n2] = (valid && r < C.n_in) ? in[r * in_r] : make_float2(0.f, 0.f);
             }
-            col_fft<PH, true>(v, sm, W, col, j, Bf.tw, Pl.twn);
+            col_fft<PH, true, true>(v, sm, W, col, j, stw, P);
             if (valid) {
 #pragma unroll
                 for (int i = 0; i < NPT; i++) {
                     const int k = col_out_row<PH>(j, i);
                     if (k >= C.n_out) continue;
-                    float2* q = out + k * C.out_r;
+                    float2* q = out + k * out_r;
                     if (J == 0) {
                         *q = v[i];
                     } else {
-                        const float2 y = cmul(v[i], twiddle(Bf.tw, k * tstep, true));
+                        const float2 y = cmul(v[i], conjf2(stw[k]));
                         const float2 a = *q;
                         *q = make_float2(a.x + y.x, a.y + y.y);
                     }
@@ -531,7 +543,10 @@ static cudaError_t launch_split(const Plan& Pl, const Buffers& Bf, const StageAr
     constexpr int N1 = ColShape<PH>::N1;
     const int W = C.G * C.ncomp * Pl.TX;
     dim3 grid((Pl.NT + C.G - 1) / C.G, C.nouter, nb * (C.ncomp == 3 ? 1 : 3));
-    k_col_split<PH><<<grid, W * N1, (size_t)PH * W * sizeof(float2), s>>>(Pl, Bf, A, C);
+    const bool fixed = Pl.TX == 8 && C.ncomp == 1 && C.G == 1 && C.in_r == 24 && C.out_r == 24;
+    const size_t smem = ((size_t)PH * W + 2 * PH) * sizeof(float2);   // transform buffer + twiddle table
+    if (fixed) k_col_split<PH, true><<<grid, W * N1, smem, s>>>(Pl, Bf, A, C);
+    else k_col_split<PH, false><<<grid, W * N1, smem, s>>>(Pl, Bf, A, C);
     return cudaGetLastError();
 }
 
@@ -712,7 +727,11 @@ cudaError_t col_init() {
         return e;
     if ((e = cudaFuncSetAttribute(k_zconv2<32, 8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(k_col_split<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(k_col_split<1024, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_col_split<1024, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) !=
+        cudaSuccess)
         return e;
     if ((e = cudaFuncSetAttribute(k_zconv2<32, 0, 0>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
         return e;
