@@ -67,10 +67,11 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xfwd(Pla
         float4 v = m0[i];
         si.apply(Bf, v, i);
         const int r = FX ? i / L : (int)fdiv((unsigned)i, P.fd_nx), x = i - r * nx;
-        float2* zr = zs + (x >> 1) * ld + 3 * r;
-        float Mx = v.w * v.x, My = v.w * v.y, Mz = v.w * v.z;
-        if (x & 1) { zr[0].y = Mx; zr[1].y = My; zr[2].y = Mz; }
-        else { zr[0].x = Mx; zr[1].x = My; zr[2].x = Mz; }
+        // z_n = x_2n + i x_2n+1: cell x is the real (even x) or imaginary part
+        float* zr = reinterpret_cast<float*>(zs + (x >> 1) * ld + 3 * r) + (x & 1);
+        zr[0] = v.w * v.x;
+        zr[2] = v.w * v.y;
+        zr[4] = v.w * v.z;
     }
     __syncthreads();
     {

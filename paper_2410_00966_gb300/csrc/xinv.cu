@@ -181,10 +181,9 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
         const float Ms = m.w;
         float Bx = 0.f, By = 0.f, Bz = 0.f;
         if (want_demag) {
-            const float2* zr = xs + (x >> 1) * ld + 3 * r;
-            float2 zx = zr[0], zy = zr[1], zz = zr[2];
-            if (x & 1) { Bx = zx.y; By = zy.y; Bz = zz.y; }
-            else { Bx = zx.x; By = zy.x; Bz = zz.x; }
+            // x_2n = Re z_n, x_2n+1 = Im z_n
+            const float* zr = reinterpret_cast<const float*>(xs + (x >> 1) * ld + 3 * r) + (x & 1);
+            Bx = zr[0]; By = zr[2]; Bz = zr[4];
         }
         if (want_exch) {
             // sum over the six neighbours j of w_j (m_j - m_i), w_j = C_d for
