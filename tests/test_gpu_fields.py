@@ -29,6 +29,12 @@ GRIDS = [
     (24, 20, 9, (4e-9, 4e-9, 3e-9)),
     (6, 5, 17, (4e-9, 4e-9, 4e-9)),
     (4, 600, 2, (4e-9, 3e-9, 4e-9)),
+    # rows of 256 / 512 / 1024 cells in whole blocks: the compile-time shapes of
+    # the x passes; 256 x 40 x 16 also takes the fixed y (P = 128) and z
+    # (pz = 32, 4 ky per block) shapes
+    (256, 40, 16, (5e-9, 5e-9, 5e-9)),
+    (512, 8, 2, (4e-9, 4e-9, 4e-9)),
+    (1024, 2, 2, (4e-9, 4e-9, 4e-9)),
 ]
 
 
