@@ -115,6 +115,35 @@ def test_dp45_replay(mode):
     assert oc["t"] == pytest.approx(c["t"], rel=1e-12)
 
 
+def test_dp45_replay_fixed_shapes():
+    """Adaptive Dormand-Prince on 256x40x16, a grid that takes the compile-time
+    shapes of the x passes (rows of 256 cells), the y passes (P = 128) and the
+    z pass (pz = 32): anisotropy, an Ms mask and a coupling profile, replayed by
+    the oracle over the GPU's accepted steps."""
+    require_gpu()
+    import synthetic
+    nx, ny, nz, d = 256, 40, 16, 5e-9
+    sim, o = make_pair(nx, ny, nz, d, 1.4e5, 3.65e-12, 1e-3, Ku=1e3, axis=(1.0, 0.0, 0.0))
+    sim.set_integrator(1, 1e-6, 0)
+    o.set_integrator(1, 1e-6, 0)
+    n = nx * ny * nz
+    ms = synthetic.disk_ms(nx, ny, nz, d, d, 190e-9, 1.4e5)
+    m0 = synthetic.tilted_m(n, synthetic.derive_seed(11, 0), 0.2)
+    prof = synthetic.lorentzian_profile(nx, ny, nz, d, 300e-9, direction=(0.0, 1.0, 0.0))
+    _setup(sim, o, m0, (0.1, 0.0, 0.0), (2 * math.pi * 5e9, 2 * math.pi * 10e6, 2 * math.pi * 200e6),
+           ms=ms, profile=prof)
+    sim.step(30, 1e-13)
+    c = sim.cavity()
+    hist = sim.dt_history()
+    assert len(hist) == c["accepted"] and c["accepted"] >= 10
+    o.replay(hist)
+    dm = np.abs(sim.get_m().astype(np.float64) - o.get_m()).max()
+    oc = o.cavity()
+    print(f"dp45 fixed shapes: accepted {c['accepted']} rejected {c['rejected']} max|dm| = {dm:.3e}")
+    assert dm <= TOL_M
+    assert abs(_alpha(c) - _alpha(oc)) <= 1e-4 * abs(_alpha(oc))
+
+
 def test_dp45_horizon_lands_exactly():
     require_gpu()
     import synthetic
