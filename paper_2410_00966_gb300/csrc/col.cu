@@ -5,11 +5,16 @@
 // demag field among the effective-field terms (Sec. 2.1); the zero-padded
 // convolution is the standard way to evaluate it.
 //
-// k_col_reg<P>: transform length P <= 1024 in registers (fftreg.cuh); each
-//   thread owns one column and loads its strided rows straight from global
-//   memory (consecutive threads = consecutive columns = contiguous memory).
-// k_col_gen: any power-of-two length, shared-memory Stockham (fft.cuh); used
-//   for transforms longer than 1024.
+// k_col_reg<P, WC>: transform length P <= 1024 in registers (fftreg.cuh);
+//   a thread group owns one column and loads its strided rows straight from
+//   global memory (consecutive threads = consecutive columns = contiguous
+//   memory).  WC > 0: the common tile shape fixed at compile time.
+// k_zconv<P> / k_zconv2<P, TXC, GC>: the z pass (pz <= 16 / pz = 32) with the
+//   demag product between the forward and the inverse z transform.
+// k_col_split<PH, FIXED>: y passes whose padded length 2 PH exceeds the
+//   register path, as two PH-point register transforms per column.
+// k_col_gen: any power-of-two length, shared-memory Stockham (fft.cuh); the
+//   remaining long transforms.
 #include <algorithm>
 
 #include "common.cuh"

@@ -9,7 +9,7 @@
 //   k_xinv : (xinv.cu) complex-to-real inverse FFT along x giving B_demag, then per cell
 //            exchange + anisotropy + Zeeman + cavity B_rms Gamma (Sec. 2.1
 //            field terms, Eq. bcav), the LLG torque (Eq. llg), the RK
-//            bookkeeping, and FP64 block partials of the coupling sum
+//            bookkeeping, and block partials of the coupling sum
 //            X = V_c sum_i Ms_i m_i . B_rms,i (Eq. gammafinal).  The last block
 //            of each instance to finish reduces the partials in a fixed order
 //            and advances the cavity amplitude / step-size controller in FP64.

@@ -2,10 +2,11 @@
 // cell (Mumax3-cQED, arXiv 2410.00966): complex-to-real inverse FFT along x
 // giving B_demag, then exchange + anisotropy + Zeeman (with the Appendix C
 // excitation) + cavity sum_k B_rms,k Gamma_k (Sec. 2.1 field terms, Eq. bcav),
-// the LLG torque (Eq. llg), the RK bookkeeping, and FP64 block partials of the
-// coupling sums X_k = V_c sum_i Ms_i m_i . B_rms,k,i (Eq. gammafinal).  The last
-// block of each instance to finish reduces the partials in a fixed order and
-// advances the cavity amplitudes and the step-size controller in FP64.
+// the LLG torque (Eq. llg), the RK bookkeeping, and block partials of the
+// coupling sums X_k = V_c sum_i Ms_i m_i . B_rms,k,i (Eq. gammafinal): FP32
+// over a thread's few cells, FP64 over the block.  The last block of each
+// instance to finish reduces the partials in a fixed order and advances the
+// cavity amplitudes and the step-size controller in FP64.
 #include <math.h>
 
 #include "common.cuh"
