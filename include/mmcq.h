@@ -202,6 +202,25 @@ int mmcq_get_cavity(mmcq_t* h, int inst, mmcq_cavity* out);
 /* The same read-out for cavity mode `mode` (mmcq_get_cavity reads mode 0). */
 int mmcq_get_cavity_mode(mmcq_t* h, int inst, int mode, mmcq_cavity* out);
 
+/* Pipelined read-out (mode 0, every instance), for a loop that reads each
+ * step's result without draining the GPU between steps:
+ *   mmcq_post_cavity enqueues on the handle's stream the read-out as of the
+ *   work enqueued so far (the coupling sums, then a copy of the instance
+ *   states, the sums and the error flags into one of MMCQ_POST_SLOTS pinned
+ *   host buffers owned by the handle) and returns without waiting.
+ *   mmcq_take_cavity waits for the oldest posted read-out and fills
+ *   out[0..batch-1] with what mmcq_get_cavity(h, -1, out) would have returned
+ *   at that point (converted with the instance parameters current at take).
+ * Steps enqueued between a post and its take run while the host waits.
+ * Errors: MMCQ_ERR_STATE when every slot is taken (post) or nothing is posted
+ * (take); MMCQ_ERR_NUMERIC from take when the device raised a non-finite or
+ * step-underflow flag before the posted point (the flag is then cleared, as by
+ * mmcq_sync); MMCQ_ERR_CUDA on a failed copy or allocation (the slots are
+ * allocated by the first post). */
+#define MMCQ_POST_SLOTS 4
+int mmcq_post_cavity(mmcq_t* h);
+int mmcq_take_cavity(mmcq_t* h, mmcq_cavity* out);
+
 /* Accepted step lengths of one instance in order (at most max are copied;
  * *n receives the total count).  Used to replay adaptive runs. */
 int mmcq_get_dt_history(mmcq_t* h, int inst, double* out, int64_t max, int64_t* n);

@@ -28,6 +28,7 @@ MMCQ_RK4, MMCQ_DP45 = 0, 1
 MMCQ_CAVITY_E, MMCQ_CAVITY_P = 0, 1
 MMCQ_TERM_DEMAG, MMCQ_TERM_EXCHANGE, MMCQ_TERM_ANIS, MMCQ_TERM_ZEEMAN, MMCQ_TERM_CAVITY = 1, 2, 4, 8, 16
 MMCQ_TERM_ALL = 31
+MMCQ_POST_SLOTS = 4
 
 _ERRNAMES = {-1: "MMCQ_ERR_ARG", -2: "MMCQ_ERR_UNSUPPORTED", -3: "MMCQ_ERR_CUDA", -4: "MMCQ_ERR_NUMERIC",
              -5: "MMCQ_ERR_TIMEOUT", -6: "MMCQ_ERR_STATE"}
@@ -99,6 +100,8 @@ PROTOTYPES = {
     "mmcq_step": (ctypes.c_int, [_H, ctypes.c_int64, ctypes.c_double]),
     "mmcq_sync": (ctypes.c_int, [_H]),
     "mmcq_get_cavity": (ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(mmcq_cavity)]),
+    "mmcq_post_cavity": (ctypes.c_int, [_H]),
+    "mmcq_take_cavity": (ctypes.c_int, [_H, ctypes.POINTER(mmcq_cavity)]),
     "mmcq_get_dt_history": (ctypes.c_int, [_H, ctypes.c_int, _DP, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "mmcq_eval_field": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, _FP, ctypes.c_int]),
     "mmcq_set_drive": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
@@ -313,6 +316,16 @@ class Sim:
         self._ck(self._lib.mmcq_get_cavity_mode(self._h, inst, int(mode), c))
         res = [{k: getattr(c[i], k) for k, _ in mmcq_cavity._fields_} for i in range(n)]
         return res if inst == -1 else res[0]
+
+    def post_cavity(self):
+        """Enqueue the read-out of every instance as of the work enqueued so far (no wait)."""
+        self._ck(self._lib.mmcq_post_cavity(self._h))
+
+    def take_cavity(self):
+        """Wait for the oldest posted read-out; list of dicts, one per instance."""
+        c = (mmcq_cavity * self.batch)()
+        self._ck(self._lib.mmcq_take_cavity(self._h, c))
+        return [{k: getattr(c[i], k) for k, _ in mmcq_cavity._fields_} for i in range(self.batch)]
 
     def dt_history(self, inst=0) -> np.ndarray:
         n = ctypes.c_int64()

@@ -92,6 +92,11 @@ struct mmcq {
     struct Rec { int cls; int ev; double bytes; };
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> events;   // pool, two per record
+    // pipelined cavity read-out: a ring of pinned host slots, each holding the
+    // instance states, the coupling sums and the error flags as of one post
+    struct Post { void* host = nullptr; cudaEvent_t ev = nullptr; };
+    std::vector<Post> posts;
+    int post_head = 0, post_count = 0;
 };
 
 enum { CLS_XFWD = 0, CLS_CONV2D, CLS_YFWD, CLS_ZCONV, CLS_YINV, CLS_XINV, NCLS };
@@ -487,6 +492,10 @@ void mmcq_destroy(mmcq_t* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (void* p : h->allocs) dev_release(h, p);
     for (auto e : h->events) cudaEventDestroy(e);
+    for (auto& q : h->posts) {
+        if (q.host) cudaFreeHost(q.host);
+        if (q.ev) cudaEventDestroy(q.ev);
+    }
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -686,17 +695,10 @@ int mmcq_sync(mmcq_t* h) {
     return check_flags(h);
 }
 
-int mmcq_get_cavity_mode(mmcq_t* h, int inst, int mode, mmcq_cavity* out) {
-    if (!h || !out || !valid_inst(h, inst, true) || mode < 0 || mode >= MAX_MODES) return MMCQ_ERR_ARG;
-    int r = check_flags(h);
-    const int b0 = inst < 0 ? 0 : inst, nb = inst < 0 ? h->P.B : 1;
-    const int k = mode;
-    std::vector<InstState> st(nb);
-    std::vector<double> X(nb, 0.0);
-    CK(h, cudaMemcpy(st.data(), h->Bf.st + b0, sizeof(InstState) * nb, cudaMemcpyDeviceToHost));
-    CK(h, launch_coupling_sum(h->Bf, h->P.N, h->mat.vc, b0, nb, k, h->dscratch, h->stream));
-    CK(h, cudaMemcpyAsync(X.data(), h->dscratch, sizeof(double) * nb, cudaMemcpyDeviceToHost, h->stream));
-    CK(h, cudaStreamSynchronize(h->stream));
+namespace {
+// Cavity read-out of mode k for instances b0 .. b0 + nb - 1 from their states
+// and coupling sums (Sec. 2.2; in P-mode alpha is rebuilt from S and C).
+void fill_cavity(const mmcq_t* h, const InstState* st, const double* X, int b0, int nb, int k, mmcq_cavity* out) {
     for (int q = 0; q < nb; q++) {
         const InstState& s = st[q];
         const InstParams& ip = h->ip[b0 + q];
@@ -724,10 +726,71 @@ int mmcq_get_cavity_mode(mmcq_t* h, int inst, int mode, mmcq_cavity* out) {
         o.accepted = s.nacc;
         o.rejected = s.nrej;
     }
+}
+}  // namespace
+
+int mmcq_get_cavity_mode(mmcq_t* h, int inst, int mode, mmcq_cavity* out) {
+    if (!h || !out || !valid_inst(h, inst, true) || mode < 0 || mode >= MAX_MODES) return MMCQ_ERR_ARG;
+    int r = check_flags(h);
+    const int b0 = inst < 0 ? 0 : inst, nb = inst < 0 ? h->P.B : 1;
+    std::vector<InstState> st(nb);
+    std::vector<double> X(nb, 0.0);
+    CK(h, cudaMemcpy(st.data(), h->Bf.st + b0, sizeof(InstState) * nb, cudaMemcpyDeviceToHost));
+    CK(h, launch_coupling_sum(h->Bf, h->P.N, h->mat.vc, b0, nb, mode, h->dscratch, h->stream));
+    CK(h, cudaMemcpyAsync(X.data(), h->dscratch, sizeof(double) * nb, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    fill_cavity(h, st.data(), X.data(), b0, nb, mode, out);
     return r;
 }
 
 int mmcq_get_cavity(mmcq_t* h, int inst, mmcq_cavity* out) { return mmcq_get_cavity_mode(h, inst, 0, out); }
+
+// Slot layout: B InstState, B doubles (X), one int (flags).
+static size_t post_bytes(const mmcq_t* h) {
+    return sizeof(InstState) * h->P.B + sizeof(double) * h->P.B + sizeof(int);
+}
+
+int mmcq_post_cavity(mmcq_t* h) {
+    if (!h) return MMCQ_ERR_ARG;
+    if (h->post_count == MMCQ_POST_SLOTS) return fail(h, MMCQ_ERR_STATE, "post_cavity: every slot holds an untaken read-out");
+    if (h->posts.empty()) {
+        h->posts.resize(MMCQ_POST_SLOTS);
+        for (auto& q : h->posts) {
+            CK(h, cudaMallocHost(&q.host, post_bytes(h)));
+            CK(h, cudaEventCreateWithFlags(&q.ev, cudaEventDisableTiming));
+        }
+    }
+    const int B = h->P.B;
+    mmcq::Post& q = h->posts[(h->post_head + h->post_count) % MMCQ_POST_SLOTS];
+    char* p = static_cast<char*>(q.host);
+    CK(h, launch_coupling_sum(h->Bf, h->P.N, h->mat.vc, 0, B, 0, h->dscratch, h->stream));
+    CK(h, cudaMemcpyAsync(p, h->Bf.st, sizeof(InstState) * B, cudaMemcpyDeviceToHost, h->stream));
+    p += sizeof(InstState) * B;
+    CK(h, cudaMemcpyAsync(p, h->dscratch, sizeof(double) * B, cudaMemcpyDeviceToHost, h->stream));
+    p += sizeof(double) * B;
+    CK(h, cudaMemcpyAsync(p, h->Bf.flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaEventRecord(q.ev, h->stream));
+    h->post_count++;
+    return MMCQ_OK;
+}
+
+int mmcq_take_cavity(mmcq_t* h, mmcq_cavity* out) {
+    if (!h || !out) return MMCQ_ERR_ARG;
+    if (h->post_count == 0) return fail(h, MMCQ_ERR_STATE, "take_cavity: nothing posted");
+    const int B = h->P.B;
+    mmcq::Post& q = h->posts[h->post_head];
+    CK(h, cudaEventSynchronize(q.ev));
+    h->post_head = (h->post_head + 1) % MMCQ_POST_SLOTS;
+    h->post_count--;
+    const char* p = static_cast<const char*>(q.host);
+    const InstState* st = reinterpret_cast<const InstState*>(p);
+    const double* X = reinterpret_cast<const double*>(p + sizeof(InstState) * B);
+    int f = 0;
+    std::memcpy(&f, p + sizeof(InstState) * B + sizeof(double) * B, sizeof(int));
+    fill_cavity(h, st, X, 0, B, 0, out);
+    if (f & (FLAG_NAN | FLAG_DT_UNDERFLOW)) return check_flags(h);
+    return MMCQ_OK;
+}
 
 int mmcq_get_dt_history(mmcq_t* h, int inst, double* out, int64_t max, int64_t* n) {
     if (!h || !valid_inst(h, inst, false) || max < 0 || (max > 0 && !out)) return MMCQ_ERR_ARG;
