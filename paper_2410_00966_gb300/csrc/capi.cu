@@ -23,6 +23,7 @@ int convolution_launches(const Plan&);
 bool col_fits(const Plan&);
 bool fft_fits(int, int);
 int rows_per_block(int, int);
+int coupling_blocks(long long);
 bool x_fits(const Plan&);
 cudaError_t launch_set_m(float4*, const float*, const float*, long long, int, int, int*, cudaStream_t);
 cudaError_t launch_get_m(const float4*, float*, long long, cudaStream_t);
@@ -429,6 +430,8 @@ int mmcq_create(mmcq_t** out, const mmcq_grid* g, double Ms, double Aex, double 
     h->ms_dev = (float*)A(sizeof(float) * P.N);
     h->stage3 = (float*)A(sizeof(float) * 3 * P.N);
     h->dscratch = (double*)A(sizeof(double) * P.B);
+    Bf.cpart_n = coupling_blocks(P.N);
+    Bf.cpart = (double*)A(sizeof(double) * (long long)P.B * Bf.cpart_n);
     if (!ok) { h->err = "device allocation failed"; return bail(MMCQ_ERR_CUDA); }
 
     if (set_smem_limits() != cudaSuccess) return bail(MMCQ_ERR_CUDA);

@@ -114,6 +114,8 @@ struct Buffers {
     int* flags;
     const float2* tw; // [twn] exp(-2 pi i k / twn)
     float4* fout;     // [N] field output of eval_field
+    double* cpart;    // [B][cpart_n] FP64 block partials of the read-out coupling sum
+    int cpart_n;      // blocks per instance of that sum
 };
 
 // What one launch of the stage kernels does.

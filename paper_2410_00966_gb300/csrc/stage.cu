@@ -181,21 +181,45 @@ __global__ void k_get_field(const float4* f, float* dst, long long N) {
 }
 
 // X = V_c sum Ms m . B_rms of each instance at its accepted state (read-out
-// only): one block per instance, fixed-order reduction.
-__global__ void k_coupling_sum(const float4* m0, const float4* m1, const InstState* st, const InstParams* ip,
-                               const float4* prof, long long N, double vc, int b0, int k, double* out) {
+// and gradient path), all in FP64.  Pass 1: cpart_n blocks per instance, each
+// a contiguous chunk of at most CSUM_THREADS x CSUM_CELLS cells, spread over
+// the whole GPU (FP64 issues at a small fraction of the FP32 rate, so one
+// block per instance would leave it to a few SMs).  Pass 2: one block per
+// instance sums its partials in a fixed order.
+constexpr int CSUM_THREADS = 256, CSUM_CELLS = 16;
+__global__ void __launch_bounds__(CSUM_THREADS) k_coupling_part(const float4* m0, const float4* m1,
+                                                                const InstState* st, const float4* prof, long long N,
+                                                                int b0, double* part, int nblk) {
+    __shared__ double red[32];
+    const int b = b0 + blockIdx.y;
+    const float4* m = (st[b].mcur ? m1 : m0) + (long long)b * N;
+    const long long chunk = (N + nblk - 1) / nblk;
+    const long long i0 = blockIdx.x * chunk;
+    const long long i1 = i0 + chunk < N ? i0 + chunk : N;
+    double acc = 0.0;
+    for (long long i = i0 + threadIdx.x; i < i1; i += CSUM_THREADS) {
+        const float4 v = m[i];
+        const float4 p = prof ? prof[i] : make_float4(0.f, 1.f, 0.f, 0.f);
+        acc += (double)v.w * ((double)v.x * p.x + (double)v.y * p.y + (double)v.z * p.z);
+    }
+    const double s = block_sum_d(acc, red);
+    if (threadIdx.x == 0) part[(long long)blockIdx.y * nblk + blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(CSUM_THREADS) k_coupling_fin(const InstParams* ip, const double* part, int nblk,
+                                                               double vc, int b0, int k, double* out) {
     __shared__ double red[32];
     const int b = b0 + blockIdx.x;
-    const float4* m = (st[b].mcur ? m1 : m0) + (long long)b * N;
     double acc = 0.0;
-    for (long long i = threadIdx.x; i < N; i += blockDim.x) {
-        float4 v = m[i];
-        double px = 0, py = 1, pz = 0;
-        if (prof) { float4 p = prof[i]; px = p.x; py = p.y; pz = p.z; }
-        acc += (double)v.w * (v.x * px + v.y * py + v.z * pz);
-    }
+    for (int q = threadIdx.x; q < nblk; q += CSUM_THREADS) acc += part[(long long)blockIdx.x * nblk + q];
     acc = block_sum_d(acc, red);
     if (threadIdx.x == 0) out[blockIdx.x] = ip[b].cav_on[k] ? acc * ip[b].brms_scale[k] * vc : 0.0;
+}
+
+// Blocks per instance of the coupling sum (host side, for the allocation).
+int coupling_blocks(long long N) {
+    const long long per = (long long)CSUM_THREADS * CSUM_CELLS;
+    return (int)((N + per - 1) / per);
 }
 
 // Trapezoid-weighted Fourier transform of one component of the recorded
@@ -312,7 +336,9 @@ cudaError_t launch_get_field(const float4* f, float* dst, long long N, cudaStrea
 }
 cudaError_t launch_coupling_sum(const Buffers& Bf, long long N, double vc, int b0, int nb, int k, double* out,
                                 cudaStream_t s) {
-    k_coupling_sum<<<nb, 1024, 0, s>>>(Bf.m[0], Bf.m[1], Bf.st, Bf.ip, Bf.prof[k], N, vc, b0, k, out);
+    k_coupling_part<<<dim3(Bf.cpart_n, nb), CSUM_THREADS, 0, s>>>(Bf.m[0], Bf.m[1], Bf.st, Bf.prof[k], N, b0,
+                                                                  Bf.cpart, Bf.cpart_n);
+    k_coupling_fin<<<nb, CSUM_THREADS, 0, s>>>(Bf.ip, Bf.cpart, Bf.cpart_n, vc, b0, k, out);
     return cudaGetLastError();
 }
 cudaError_t launch_set_dt(InstState* st, int B, double dt, cudaStream_t s) {
