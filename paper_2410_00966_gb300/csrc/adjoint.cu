@@ -192,11 +192,43 @@ __global__ void k_adj_terminal(const float4* Y, float4* lam, float wx, float wy,
 static __device__ const double ADJ_C[4] = {0.0, 0.5, 0.5, 1.0};
 static __device__ const double ADJ_B[4] = {1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6};
 
-// The averaged photon number sees alpha at step q + 1: J += c |alpha|^2 and
-// its cotangent 2 c alpha.
-__global__ void k_adj_window(AdjScalars* S, const InstState* st, double c, int B) {
+// Cursor of the reversed loop in device memory, so that one captured step
+// serves every step: cur[0] = q - c0 (the step within its checkpoint segment),
+// cur[1] = c0.
+__global__ void k_adj_set_cursor(long long* cur, long long qrel, long long c0) {
+    cur[0] = qrel;
+    cur[1] = c0;
+}
+__global__ void k_adj_next(long long* cur) { cur[0] -= 1; }
+
+// Inputs of reversed step q from the segment arrays at the cursor: the state
+// m_q into Ybase and Y0 (the first stage input), the instance states of steps
+// q and q + 1.
+__global__ void k_adj_step_inputs(const float4* seg, const InstState* segst, float4* Ybase, float4* Y0,
+                                  InstState* stq, InstState* stq1, const long long* cur, long long BN, int B) {
+    const long long qrel = cur[0];
+    const float4* src = seg + qrel * BN;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < BN; i += (long long)gridDim.x * blockDim.x) {
+        const float4 v = src[i];
+        Ybase[i] = v;
+        Y0[i] = v;
+    }
+    if (blockIdx.x == 0) {
+        for (int b = threadIdx.x; b < B; b += blockDim.x) {
+            stq[b] = segst[qrel * B + b];
+            stq1[b] = segst[(qrel + 1) * B + b];
+        }
+    }
+}
+
+// The averaged photon number sees alpha at step q + 1 (q from the cursor;
+// only steps with q + 1 >= wstart count): J += c |alpha|^2 and its cotangent
+// 2 c alpha.
+__global__ void k_adj_window(AdjScalars* S, const InstState* st, double c, int B, const long long* cur,
+                             long long wstart) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
+    if (cur[1] + cur[0] + 1 < wstart) return;
     const double ar = st[b].a_re[0], ai = st[b].a_im[0];
     S[b].J += c * (ar * ar + ai * ai);
     S[b].la_re += 2.0 * c * ar;
@@ -330,8 +362,23 @@ cudaError_t launch_adj_terminal(const float4* Y, float4* lam, const double w[3],
 }
 
 static unsigned small_blocks(int B) { return (unsigned)((B + 63) / 64); }
-cudaError_t launch_adj_window(AdjScalars* S, const InstState* st, double c, int B, cudaStream_t s) {
-    k_adj_window<<<small_blocks(B), 64, 0, s>>>(S, st, c, B);
+cudaError_t launch_adj_window(AdjScalars* S, const InstState* st, double c, int B, const long long* cur,
+                              long long wstart, cudaStream_t s) {
+    k_adj_window<<<small_blocks(B), 64, 0, s>>>(S, st, c, B, cur, wstart);
+    return cudaGetLastError();
+}
+cudaError_t launch_adj_set_cursor(long long* cur, long long qrel, long long c0, cudaStream_t s) {
+    k_adj_set_cursor<<<1, 1, 0, s>>>(cur, qrel, c0);
+    return cudaGetLastError();
+}
+cudaError_t launch_adj_next(long long* cur, cudaStream_t s) {
+    k_adj_next<<<1, 1, 0, s>>>(cur);
+    return cudaGetLastError();
+}
+cudaError_t launch_adj_step_inputs(const float4* seg, const InstState* segst, float4* Ybase, float4* Y0,
+                                   InstState* stq, InstState* stq1, const long long* cur, long long BN, int B,
+                                   cudaStream_t s) {
+    k_adj_step_inputs<<<blocks_for(BN, 256), 256, 0, s>>>(seg, segst, Ybase, Y0, stq, stq1, cur, BN, B);
     return cudaGetLastError();
 }
 cudaError_t launch_adj_begin_step(AdjScalars* S, InstState* adst, const InstState* st, int B, cudaStream_t s) {

@@ -6,6 +6,7 @@
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -44,7 +45,11 @@ cudaError_t launch_adj_combine(const float4*, const float4*, const float4*, cons
                                float4*, const Material&, float, float, int, int, int, int, float*, const double*,
                                const InstParams*, const float4*, cudaStream_t);
 cudaError_t launch_adj_terminal(const float4*, float4*, const double*, long long, cudaStream_t);
-cudaError_t launch_adj_window(AdjScalars*, const InstState*, double, int, cudaStream_t);
+cudaError_t launch_adj_window(AdjScalars*, const InstState*, double, int, const long long*, long long, cudaStream_t);
+cudaError_t launch_adj_set_cursor(long long*, long long, long long, cudaStream_t);
+cudaError_t launch_adj_next(long long*, cudaStream_t);
+cudaError_t launch_adj_step_inputs(const float4*, const InstState*, float4*, float4*, InstState*, InstState*,
+                                   const long long*, long long, int, cudaStream_t);
 cudaError_t launch_adj_begin_step(AdjScalars*, InstState*, const InstState*, int, cudaStream_t);
 cudaError_t launch_adj_alpha_stage(AdjScalars*, InstState*, const InstParams*, const double*, int, double, double, int,
                                    cudaStream_t);
@@ -946,6 +951,39 @@ int adj_field(mmcq_t* h, const Buffers& Bq, int terms) {
     return MMCQ_OK;
 }
 
+// A reversed adjoint step captured once and replayed (falls back to direct
+// launches when the stream cannot be captured).
+struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    bool failed = false;
+    int capture(mmcq_t* h, const std::function<int()>& enqueue) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            failed = true;
+            return MMCQ_OK;
+        }
+        const int r = enqueue();
+        const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+        if (r != MMCQ_OK || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            failed = true;
+            return r;
+        }
+        if (cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) {
+            exec = nullptr;
+            cudaGetLastError();
+            failed = true;
+        }
+        cudaGraphDestroy(g);
+        return MMCQ_OK;
+    }
+    ~StepGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+};
+
 struct AdjScratch {
     std::vector<void*> bufs;
     mmcq_t* h;
@@ -1010,7 +1048,11 @@ int mmcq_adjoint_rk4(mmcq_t* h, int64_t nsteps, double dt, const mmcq_objective*
     const int nblk = adj_local_blocks(N);
     double* part = (double*)sc.get(sizeof(double) * 4 * B * nblk);
     AdjScalars* S = (AdjScalars*)sc.get(sizeof(AdjScalars) * B);
-    if (sc.bufs.size() != (size_t)(6 + 12 + 8 + 5)) return fail(h, MMCQ_ERR_CUDA, "adjoint: device allocation failed");
+    float4* Ybase = (float4*)sc.get(sv);                // m_q of the reversed step
+    InstState* stq = (InstState*)sc.get(sizeof(InstState) * B);
+    InstState* stq1 = (InstState*)sc.get(sizeof(InstState) * B);
+    long long* cur = (long long*)sc.get(sizeof(long long) * 2);
+    if (sc.bufs.size() != (size_t)(6 + 12 + 8 + 5 + 4)) return fail(h, MMCQ_ERR_CUDA, "adjoint: device allocation failed");
     CK(h, cudaMemsetAsync(gms, 0, sizeof(float) * BN, h->stream));
 
     // forward: checkpoint every K steps (m and the instance states)
@@ -1065,6 +1107,50 @@ int mmcq_adjoint_rk4(mmcq_t* h, int64_t nsteps, double dt, const mmcq_objective*
 
     const double cc[4] = {0.0, 0.5, 0.5, 1.0}, bb[4] = {1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6};
     const double vc = h->mat.vc, hbar = h->hbar;
+    // One reversed step q (q and the segment from the device cursor), enqueued
+    // with fixed pointers only, so that it is captured once as a CUDA graph and
+    // replayed for every step.
+    auto back_step = [&]() -> int {
+        int rr;
+        CK(h, launch_adj_step_inputs(seg, segst, Ybase, Y[0], stq, stq1, cur, BN, B, h->stream));
+        // the averaged photon number sees alpha at step q + 1
+        CK(h, launch_adj_window(S, stq1, cav, B, cur, nsteps - window + 1, h->stream));
+        CK(h, launch_adj_begin_step(S, adst, stq, B, h->stream));
+        for (int s = 0; s < 4; s++) {
+            Buffers Bq = h->Bf;
+            Bq.m[0] = Bq.m[1] = Y[s];
+            Bq.st = adst;
+            Bq.fout = Bs[s];
+            if ((rr = adj_field(h, Bq, MMCQ_TERM_ALL))) return rr;
+            CK(h, launch_coupling_sum(Bq, N, vc, 0, B, 0, dX, h->stream));
+            CK(h, launch_adj_alpha_stage(S, adst, h->Bf.ip, dX, s, dt, hbar, B, h->stream));
+            CK(h, launch_adj_torque(Y[s], Bs[s], Ybase, Kb[s], s < 3 ? Y[s + 1] : nullptr,
+                                    (float)(cc[s < 3 ? s + 1 : 0] * dt), h->mat.pre, h->mat.alpha, BN, h->stream));
+        }
+        // renormalisation and the stage cotangents
+        CK(h, launch_adj_norm(Ybase, Kb, lam, lp, nl, lk, (float)dt, BN, h->stream));
+        CK(h, launch_adj_begin_vjp(S, h->Bf.ip, dlX, dt, hbar, B, h->stream));
+        for (int s = 3; s >= 0; s--) {
+            CK(h, launch_adj_local(Y[s], Bs[s], lk, dlX, h->Bf.ip, h->Bf.prof[0], lB, gd, part, h->mat.pre,
+                                   h->mat.alpha, vc, N, B, h->stream));
+            Buffers Bq = h->Bf;
+            Bq.m[0] = Bq.m[1] = lB;
+            Bq.st = adst;
+            Bq.fout = Dl;
+            if ((rr = adj_field(h, Bq, MMCQ_TERM_DEMAG))) return rr;
+            const float dtb = s > 0 ? (float)(dt * bb[s - 1]) : 0.f;
+            const float cdt = s > 0 ? (float)(cc[s] * dt) : 0.f;
+            CK(h, launch_adj_combine(Y[s], lB, Dl, gd, lp, nl, lk, h->mat, dtb, cdt, h->P.nx, h->P.ny, h->P.nz, B,
+                                     grad_ms ? gms : nullptr, dlX, h->Bf.ip, h->Bf.prof[0], h->stream));
+            CK(h, launch_adj_scalar_vjp(S, part, nblk, h->Bf.ip, dlX, s, dt, hbar, B, h->stream));
+        }
+        CK(h, launch_adj_end_step(S, B, h->stream));
+        // lambda of step q is what the stages accumulated
+        CK(h, cudaMemcpyAsync(lam, nl, sv, cudaMemcpyDeviceToDevice, h->stream));
+        CK(h, launch_adj_next(cur, h->stream));
+        return MMCQ_OK;
+    };
+    StepGraph step_graph;
     for (int64_t c0 = (nck - 1) * K; c0 >= 0; c0 -= K) {
         const int64_t c1 = std::min(c0 + K, nsteps);
         // recompute the states of steps c0 .. c1 - 1 from checkpoint c0 (the state
@@ -1083,45 +1169,14 @@ int mmcq_adjoint_rk4(mmcq_t* h, int64_t nsteps, double dt, const mmcq_objective*
         }
         CK(h, cudaMemcpyAsync(segst + (c1 - c0) * B, c1 < nsteps ? ckst + (c1 / K) * B : stfin,
                               sizeof(InstState) * B, cudaMemcpyDeviceToDevice, h->stream));
+        CK(h, launch_adj_set_cursor(cur, c1 - 1 - c0, c0, h->stream));
         for (int64_t q = c1 - 1; q >= c0; q--) {
-            // the averaged photon number sees alpha at step q + 1
-            if (q + 1 >= nsteps - window + 1) CK(h, launch_adj_window(S, segst + (q + 1 - c0) * B, cav, B, h->stream));
-            const float4* Y1 = seg + (q - c0) * BN;
-            CK(h, launch_adj_begin_step(S, adst, segst + (q - c0) * B, B, h->stream));
-            CK(h, cudaMemcpyAsync(Y[0], Y1, sv, cudaMemcpyDeviceToDevice, h->stream));
-            for (int s = 0; s < 4; s++) {
-                Buffers Bq = h->Bf;
-                Bq.m[0] = Bq.m[1] = Y[s];
-                Bq.st = adst;
-                Bq.fout = Bs[s];
-                r = adj_field(h, Bq, MMCQ_TERM_ALL);
+            if (!step_graph.exec && !step_graph.failed) {
+                r = step_graph.capture(h, back_step);
                 if (r) return r;
-                CK(h, launch_coupling_sum(Bq, N, vc, 0, B, 0, dX, h->stream));
-                CK(h, launch_adj_alpha_stage(S, adst, h->Bf.ip, dX, s, dt, hbar, B, h->stream));
-                CK(h, launch_adj_torque(Y[s], Bs[s], Y1, Kb[s], s < 3 ? Y[s + 1] : nullptr,
-                                        (float)(cc[s < 3 ? s + 1 : 0] * dt), h->mat.pre, h->mat.alpha, BN,
-                                        h->stream));
             }
-            // renormalisation and the stage cotangents
-            CK(h, launch_adj_norm(Y1, Kb, lam, lp, nl, lk, (float)dt, BN, h->stream));
-            CK(h, launch_adj_begin_vjp(S, h->Bf.ip, dlX, dt, hbar, B, h->stream));
-            for (int s = 3; s >= 0; s--) {
-                CK(h, launch_adj_local(Y[s], Bs[s], lk, dlX, h->Bf.ip, h->Bf.prof[0], lB, gd, part, h->mat.pre,
-                                       h->mat.alpha, vc, N, B, h->stream));
-                Buffers Bq = h->Bf;
-                Bq.m[0] = Bq.m[1] = lB;
-                Bq.st = adst;
-                Bq.fout = Dl;
-                r = adj_field(h, Bq, MMCQ_TERM_DEMAG);
-                if (r) return r;
-                const float dtb = s > 0 ? (float)(dt * bb[s - 1]) : 0.f;
-                const float cdt = s > 0 ? (float)(cc[s] * dt) : 0.f;
-                CK(h, launch_adj_combine(Y[s], lB, Dl, gd, lp, nl, lk, h->mat, dtb, cdt, h->P.nx, h->P.ny, h->P.nz,
-                                         B, grad_ms ? gms : nullptr, dlX, h->Bf.ip, h->Bf.prof[0], h->stream));
-                CK(h, launch_adj_scalar_vjp(S, part, nblk, h->Bf.ip, dlX, s, dt, hbar, B, h->stream));
-            }
-            CK(h, launch_adj_end_step(S, B, h->stream));
-            std::swap(lam, nl);
+            if (step_graph.exec) CK(h, cudaGraphLaunch(step_graph.exec, h->stream));
+            else if ((r = back_step())) return r;
         }
     }
     {
