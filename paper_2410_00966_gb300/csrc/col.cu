@@ -671,8 +671,15 @@ cudaError_t launch_conv_part(const Plan& P, const Buffers& Bf, const StageArgs& 
         if (zconv_applies(P)) {
             C.G = zconv_groups(P);
             if (P.pz == 32) {
-                C.G = zsplit_groups(P);
-                return launch_z2<32>(P, Bf, A, C, nb, s);
+                // k_zconv2's two halves must be whole warps: its inverse hands
+                // rows between the halves through shared memory, between block
+                // barriers that each half reaches in its own branch (W = 96 for
+                // every grid with 32 or more kx x ky columns per block)
+                const int G2 = zsplit_groups(P);
+                if ((3 * G2 * P.TX) % 32 == 0) {
+                    C.G = G2;
+                    return launch_z2<32>(P, Bf, A, C, nb, s);
+                }
             }
             switch (P.pz) {
                 case 2: return launch_z<2>(P, Bf, A, C, nb, s);

@@ -33,6 +33,8 @@ GRIDS = [
     # the x passes; 256 x 40 x 16 also takes the fixed y (P = 128) and z
     # (pz = 32, 4 ky per block) shapes
     (256, 40, 16, (5e-9, 5e-9, 5e-9)),
+    # pz = 32 with one ky column: the one-thread z pass (k_zconv<32>)
+    (12, 1, 12, (4e-9, 4e-9, 4e-9)),
     (512, 8, 2, (4e-9, 4e-9, 4e-9)),
     (1024, 2, 2, (4e-9, 4e-9, 4e-9)),
 ]
