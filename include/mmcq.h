@@ -98,6 +98,8 @@ typedef struct {
     double X;              /* V_c sum_i Ms_i m_i . B_rms,i at the current m (J) */
     double dt;             /* next trial step (DP45) or last step (RK4) */
     int64_t accepted, rejected;
+    double err;            /* DP45: error estimate max_i |m5_i - m4_i| of the last attempt, the value
+                              the step controller used (FP32 on the device, widened); 0 for RK4 */
 } mmcq_cavity;
 
 typedef struct {
@@ -323,13 +325,13 @@ int mmcq_eval_field(mmcq_t* h, int inst, int terms, float* out, int where);
  *   m, brms: device arrays of n x 3 floats; ms: device array of n floats;
  *   vc: cell volume (m^3); out: host pointer receiving X (J).
  *   stream: cudaStream_t to run on (NULL = the default stream); the call
- *   waits for its own work on that stream before returning.
+ *   waits for its own work on that stream and copies X to the host before
+ *   returning, so it must not be made while that stream is capturing.
  * Limits and behaviour:
  *   - n <= 16,777,216 cells (4096 chunks of 4096); larger n returns
  *     MMCQ_ERR_UNSUPPORTED without touching the GPU.
  *   - The first call on each device looks up the array's device address
- *     (with that device current); make that first call before any stream
- *     capture begins.
+ *     (with that device current).
  *   - Every call shares the one array, so calls whose work overlaps on the GPU
  *     (different streams, threads or processes sharing the context) race and
  *     may return wrong sums; serialise them.

@@ -53,7 +53,7 @@ class mmcq_opts(ctypes.Structure):
 class mmcq_cavity(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in
                 ("t", "t_cav", "re_alpha", "im_alpha", "n_photon", "Gamma", "S", "C", "X", "dt")] + \
-               [("accepted", ctypes.c_int64), ("rejected", ctypes.c_int64)]
+               [("accepted", ctypes.c_int64), ("rejected", ctypes.c_int64), ("err", ctypes.c_double)]
 
 
 class mmcq_info(ctypes.Structure):

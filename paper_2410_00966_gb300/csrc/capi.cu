@@ -228,9 +228,11 @@ double launch_bytes(const mmcq_t* h, int cls, const StageArgs& A, int nb) {
     const Plan& P = h->P;
     const double N = (double)P.N;
     const double cplx = 8.0;
-    const double xrow = (double)P.nrows * P.NT * P.TX * 3 * cplx;      // one instance's x half-spectrum
-    const double yrow = (double)P.nz * P.py * P.NT * P.TX * 3 * cplx;  // after the y transform
-    const double kern = (double)P.hzk * P.hyk * P.NT * P.TX * 6 * 4;
+    // spectra and kernel count the px/2 + 1 half-spectrum columns the method
+    // needs, not the tile padding beyond them
+    const double xrow = (double)P.nrows * P.hx * 3 * cplx;      // one instance's x half-spectrum
+    const double yrow = (double)P.nz * P.py * P.hx * 3 * cplx;  // after the y transform
+    const double kern = (double)P.hzk * P.hyk * P.hx * 6 * 4;
     static const int dp_kreads[7] = {0, 1, 2, 3, 4, 5, 5};
     const int s = A.stage;
     double per = 0.0;
@@ -246,7 +248,7 @@ double launch_bytes(const mmcq_t* h, int cls, const StageArgs& A, int nb) {
         case CLS_ZCONV: return nb * 2.0 * yrow + kern;
         case CLS_YINV: per = yrow + xrow; break;
         case CLS_XINV: {
-            double spec = (double)P.nrows * (P.L + 1) * 3 * cplx;
+            double spec = xrow;
             double cells = 16.0;                         // stage input m_s
             if (A.field_only) cells += 16.0;             // field out
             else if (A.kind == KIND_RK4 && s == 3) cells += 16.0 * 5;  // m0, k1..k3 in, m out
@@ -733,6 +735,7 @@ void fill_cavity(const mmcq_t* h, const InstState* st, const double* X, int b0, 
         o.dt = s.dt;
         o.accepted = s.nacc;
         o.rejected = s.nrej;
+        o.err = s.err;
     }
 }
 }  // namespace

@@ -253,10 +253,17 @@ __device__ __forceinline__ void zsplit_forward(const ColArgs& C, float2* sm, int
     for (int m = 0; m < H; m++) sm[(2 * m + J) * W + col] = v[m];
 }
 
-template <int P, int J, bool FULL, typename S>
-__device__ __forceinline__ void zsplit_inverse(const ColArgs& C, float2* sm, int W, int col, float2* out, S rs) {
-    constexpr int H = P / 2, Q = H / 2;
-    float2 v[H];
+// The inverse runs in three phases with the block barriers between them in
+// the kernel body, where every thread of the block reaches the same barrier
+// instruction; each phase is a branch-free function of one half J:
+//   zinv_transform: the half's H frequencies from shared memory, inverse
+//     H-point DFT, and (J = 1) the twiddle W_P^{-n};
+//   zinv_handoff: the rows the other half will write out (J = 0 hands over
+//     rows Q..H-1, J = 1 rows 0..Q-1) go to shared memory;
+//   zinv_finish: the half's own Q rows plus the other half's part, written out.
+template <int P, int J>
+__device__ __forceinline__ void zinv_transform(const float2* sm, int W, int col, float2 (&v)[P / 2]) {
+    constexpr int H = P / 2;
 #pragma unroll
     for (int m = 0; m < H; m++) v[m] = sm[(2 * m + J) * W + col];
     fft_reg<H, true>(v);
@@ -268,10 +275,19 @@ __device__ __forceinline__ void zsplit_inverse(const ColArgs& C, float2* sm, int
             else { float2 w = c_tw32[e]; w.y = -w.y; v[n] = cmul(v[n], w); }
         }
     }
-    __syncthreads();                              // both halves have read the product
+}
+
+template <int P, int J>
+__device__ __forceinline__ void zinv_handoff(float2* sm, int W, int col, const float2 (&v)[P / 2]) {
+    constexpr int Q = P / 4;
 #pragma unroll
     for (int n = 0; n < Q; n++) sm[((J == 0 ? Q : 0) + n) * W + col] = v[(J == 0 ? Q : 0) + n];
-    __syncthreads();
+}
+
+template <int P, int J, bool FULL, typename S>
+__device__ __forceinline__ void zinv_finish(const ColArgs& C, const float2* sm, int W, int col,
+                                            const float2 (&v)[P / 2], float2* out, S rs) {
+    constexpr int Q = P / 4;
 #pragma unroll
     for (int n = 0; n < Q; n++) {
         const int r = (J == 0 ? 0 : Q) + n;
@@ -353,12 +369,19 @@ __global__ void __launch_bounds__(192, 6) k_zconv2(Plan Pl, Buffers Bf, StageArg
         }
     }
     __syncthreads();
+    float2 v[P / 2];
+    if (half == 0) zinv_transform<P, 0>(sm, W, col, v);
+    else zinv_transform<P, 1>(sm, W, col, v);
+    __syncthreads();                              // both halves have read the product
+    if (half == 0) zinv_handoff<P, 0>(sm, W, col, v);
+    else zinv_handoff<P, 1>(sm, W, col, v);
+    __syncthreads();
     if (FIXED) {
-        if (half == 0) zsplit_inverse<P, 0, true>(C, sm, W, col, C.out + off_out, (int)C.out_r);
-        else zsplit_inverse<P, 1, true>(C, sm, W, col, C.out + off_out, (int)C.out_r);
+        if (half == 0) zinv_finish<P, 0, true>(C, sm, W, col, v, C.out + off_out, (int)C.out_r);
+        else zinv_finish<P, 1, true>(C, sm, W, col, v, C.out + off_out, (int)C.out_r);
     } else {
-        if (half == 0) zsplit_inverse<P, 0, false>(C, sm, W, col, C.out + off_out, C.out_r);
-        else zsplit_inverse<P, 1, false>(C, sm, W, col, C.out + off_out, C.out_r);
+        if (half == 0) zinv_finish<P, 0, false>(C, sm, W, col, v, C.out + off_out, C.out_r);
+        else zinv_finish<P, 1, false>(C, sm, W, col, v, C.out + off_out, C.out_r);
     }
 }
 
@@ -671,10 +694,10 @@ cudaError_t launch_conv_part(const Plan& P, const Buffers& Bf, const StageArgs& 
         if (zconv_applies(P)) {
             C.G = zconv_groups(P);
             if (P.pz == 32) {
-                // k_zconv2's two halves must be whole warps: its inverse hands
-                // rows between the halves through shared memory, between block
-                // barriers that each half reaches in its own branch (W = 96 for
-                // every grid with 32 or more kx x ky columns per block)
+                // k_zconv2's halves are kept whole warps (W = 96 for every grid
+                // with 32 or more kx x ky columns per block), so that no warp
+                // diverges on the half; its barriers sit outside the per-half
+                // branches either way
                 const int G2 = zsplit_groups(P);
                 if ((3 * G2 * P.TX) % 32 == 0) {
                     C.G = G2;
