@@ -94,9 +94,9 @@ __global__ void __launch_bounds__(512) k_col_reg(Plan Pl, Buffers Bf, StageArgs 
     constexpr bool FIXED = WC > 0;
     extern __shared__ float2 sm[];
     const int ncomp = FIXED ? 3 : C.ncomp;
-    const int bz = blockIdx.z;
-    const int b = A.inst0 + (ncomp == 3 ? bz : bz / 3);
-    const int c0 = ncomp == 3 ? 0 : bz % 3;
+    const int b = A.inst0 + blockIdx.z;
+    const int c0 = ncomp == 3 ? 0 : blockIdx.x % 3;
+    const int bx = ncomp == 3 ? blockIdx.x : blockIdx.x / 3;
     if (stage_skips(Bf.st[b], A)) return;
     const int TX = FIXED ? WC / 3 : Pl.TX;
     const int lt = FIXED ? ilog2<(FIXED ? WC / 3 : 1)>() : Pl.lt;
@@ -108,8 +108,8 @@ __global__ void __launch_bounds__(512) k_col_reg(Plan Pl, Buffers Bf, StageArgs 
     const int j = threadIdx.x / W;
     const int g = ncomp == 3 ? (col >> lt) / 3 : (col >> lt);
     const int e = col - g * rw;
-    const int t0 = C.group_tiles ? blockIdx.x * G : blockIdx.y;
-    const int o0 = C.group_tiles ? blockIdx.y : blockIdx.x * G;
+    const int t0 = C.group_tiles ? bx * G : blockIdx.y;
+    const int o0 = C.group_tiles ? blockIdx.y : bx * G;
     const int t = C.group_tiles ? t0 + g : t0;
     const int o = C.group_tiles ? o0 : o0 + g;
     const bool valid = t < Pl.NT && o < C.nouter;
@@ -396,15 +396,21 @@ __global__ void __launch_bounds__(192, 6) k_zconv2(Plan Pl, Buffers Bf, StageArg
 // thread, so the read-back is the thread's own store).
 // FIXED: one component of one 8-column tile per block (G = 1), rows 24 apart
 // in both spectra, at compile time.
+// F3 (FIXED with PH = 1024): the three-factor transform, 16 points per
+// thread and 64 threads per column (512 threads for the 8 columns), so that
+// two blocks of 16 warps fit an SM; the last factor runs across the lanes
+// 8 apart (the same rows of the 8 columns are consecutive threads).
 template <int PH, bool FIXED>
-__global__ void __launch_bounds__(512) k_col_split(Plan Pl, Buffers Bf, StageArgs A, ColArgs C) {
-    constexpr int NPT = ColShape<PH>::NPT, N1 = ColShape<PH>::N1;
+__global__ void __launch_bounds__(512, (FIXED && PH == 1024) ? 2 : 1) k_col_split(Plan Pl, Buffers Bf, StageArgs A,
+                                                                                   ColArgs C) {
+    constexpr bool F3 = FIXED && PH == 1024;
+    constexpr int NPT = F3 ? 16 : ColShape<PH>::NPT, N1 = F3 ? ColShape3<PH>::N1 : ColShape<PH>::N1;
     constexpr int P = 2 * PH;
     extern __shared__ float2 sm[];
     const int ncomp = FIXED ? 1 : C.ncomp;
-    const int bz = blockIdx.z;
-    const int b = A.inst0 + (ncomp == 3 ? bz : bz / 3);
-    const int c0 = ncomp == 3 ? 0 : bz % 3;
+    const int b = A.inst0 + blockIdx.z;
+    const int c0 = ncomp == 3 ? 0 : blockIdx.x % 3;
+    const int bx = ncomp == 3 ? blockIdx.x : blockIdx.x / 3;
     if (stage_skips(Bf.st[b], A)) return;
     const int TX = FIXED ? 8 : Pl.TX, lt = FIXED ? 3 : Pl.lt;
     const int G = FIXED ? 1 : C.G;
@@ -415,13 +421,23 @@ __global__ void __launch_bounds__(512) k_col_split(Plan Pl, Buffers Bf, StageArg
     const int j = threadIdx.x / W;
     const int g = ncomp == 3 ? (col >> lt) / 3 : (col >> lt);
     const int e = col - g * rw;
-    const int t = blockIdx.x * G + g, o = blockIdx.y;          // tiles are the groups here
+    const int t = bx * G + g, o = blockIdx.y;                  // tiles are the groups here
     const bool valid = t < Pl.NT && o < C.nouter;
     const float2* in = C.in + b * C.in_b + o * C.in_o + t * C.in_t + c0 * TX + e;
     float2* out = C.out + b * C.out_b + o * C.out_o + t * C.out_t + c0 * TX + e;
     // exp(-2 pi i e / P), e < P, after the transform buffer: the odd-half
     // twiddles W_P^r and the four-step twiddles W_PH^{j k2} = W_P^{2 j k2}
     float2* stw = sm + PH * W;
+    auto fft = [&](float2 (&v)[NPT], bool inv) {
+        if constexpr (F3) {
+            if (inv) col_fft3<PH, true, true, 0, 8>(v, sm, W, col, j, stw, P);
+            else col_fft3<PH, false, true, 0, 8>(v, sm, W, col, j, stw, P);
+        } else {
+            if (inv) col_fft<PH, true, true>(v, sm, W, col, j, stw, P);
+            else col_fft<PH, false, true>(v, sm, W, col, j, stw, P);
+        }
+    };
+    auto out_row = [&](int i) { return F3 ? col3_out_row<PH>(j, i) : col_out_row<PH>(j, i); };
     {
         const int tstep = Pl.twn / P;
         for (int q = threadIdx.x; q < P; q += blockDim.x) stw[q] = __ldg(Bf.tw + q * tstep);
@@ -438,10 +454,10 @@ __global__ void __launch_bounds__(512) k_col_split(Plan Pl, Buffers Bf, StageArg
                 if (J == 1) x = cmul(x, stw[r]);
                 v[n2] = x;
             }
-            col_fft<PH, false, true>(v, sm, W, col, j, stw, P);
+            fft(v, false);
             if (valid) {
 #pragma unroll
-                for (int i = 0; i < NPT; i++) out[(2 * col_out_row<PH>(j, i) + J) * out_r] = v[i];
+                for (int i = 0; i < NPT; i++) out[(2 * out_row(i) + J) * out_r] = v[i];
             }
         } else {
 #pragma unroll
@@ -449,11 +465,11 @@ __global__ void __launch_bounds__(512) k_col_split(Plan Pl, Buffers Bf, StageArg
                 const int r = 2 * (j + N1 * n2) + J;
                 v[n2] = (valid && r < C.n_in) ? in[r * in_r] : make_float2(0.f, 0.f);
             }
-            col_fft<PH, true, true>(v, sm, W, col, j, stw, P);
+            fft(v, true);
             if (valid) {
 #pragma unroll
                 for (int i = 0; i < NPT; i++) {
-                    const int k = col_out_row<PH>(j, i);
+                    const int k = out_row(i);
                     if (k >= C.n_out) continue;
                     float2* q = out + k * out_r;
                     if (J == 0) {
@@ -473,16 +489,16 @@ __global__ void __launch_bounds__(512) k_col_split(Plan Pl, Buffers Bf, StageArg
 template <int SLOTS>
 __global__ void __launch_bounds__(MAX_THREADS) k_col_gen(Plan P, Buffers Bf, StageArgs A, ColArgs C) {
     extern __shared__ float2 sm[];
-    const int bz = blockIdx.z;
-    const int b = A.inst0 + (C.ncomp == 3 ? bz : bz / 3);
-    const int c0 = C.ncomp == 3 ? 0 : bz % 3;
+    const int b = A.inst0 + blockIdx.z;
+    const int c0 = C.ncomp == 3 ? 0 : blockIdx.x % 3;
+    const int bx = C.ncomp == 3 ? blockIdx.x : blockIdx.x / 3;
     if (stage_skips(Bf.st[b], A)) return;
     const int TX = P.TX;
     const int rw = C.ncomp * TX;
     const int G = C.G;
     const int W = G * rw;
-    const int t0 = C.group_tiles ? blockIdx.x * G : blockIdx.y;
-    const int o0 = C.group_tiles ? blockIdx.y : blockIdx.x * G;
+    const int t0 = C.group_tiles ? bx * G : blockIdx.y;
+    const int o0 = C.group_tiles ? blockIdx.y : bx * G;
     const float2* in = C.in + b * C.in_b + c0 * TX;
     float2* out = C.out + b * C.out_b + c0 * TX;
     for (int i = threadIdx.x; i < C.P * W; i += blockDim.x) {
@@ -570,11 +586,15 @@ static cudaError_t launch_split(const Plan& Pl, const Buffers& Bf, const StageAr
                                 cudaStream_t s) {
     constexpr int N1 = ColShape<PH>::N1;
     const int W = C.G * C.ncomp * Pl.TX;
-    dim3 grid((Pl.NT + C.G - 1) / C.G, C.nouter, nb * (C.ncomp == 3 ? 1 : 3));
+    dim3 grid(((Pl.NT + C.G - 1) / C.G) * (C.ncomp == 3 ? 1 : 3), C.nouter, nb);
     const bool fixed = Pl.TX == 8 && C.ncomp == 1 && C.G == 1 && C.in_r == 24 && C.out_r == 24;
     const size_t smem = ((size_t)PH * W + 2 * PH) * sizeof(float2);   // transform buffer + twiddle table
-    if (fixed) k_col_split<PH, true><<<grid, W * N1, smem, s>>>(Pl, Bf, A, C);
-    else k_col_split<PH, false><<<grid, W * N1, smem, s>>>(Pl, Bf, A, C);
+    if (fixed) {
+        const int n1 = PH == 1024 ? ColShape3<PH>::N1 : N1;   // three-factor shape (see k_col_split)
+        k_col_split<PH, true><<<grid, W * n1, smem, s>>>(Pl, Bf, A, C);
+    } else {
+        k_col_split<PH, false><<<grid, W * N1, smem, s>>>(Pl, Bf, A, C);
+    }
     return cudaGetLastError();
 }
 
@@ -599,8 +619,12 @@ static cudaError_t launch_col(const Plan& P, const Buffers& Bf, const StageArgs&
                               cudaStream_t s) {
     const int W = C.G * C.ncomp * P.TX;
     dim3 grid;
-    if (C.group_tiles) grid = dim3((P.NT + C.G - 1) / C.G, C.nouter, nb * (C.ncomp == 3 ? 1 : 3));
-    else grid = dim3((C.nouter + C.G - 1) / C.G, P.NT, nb * (C.ncomp == 3 ? 1 : 3));
+    // one component per block: the three component blocks of a tile are
+    // consecutive in x, so they run together and share the L2 lines of the
+    // tile rows (each component is a third of a row)
+    const int nc = C.ncomp == 3 ? 1 : 3;
+    if (C.group_tiles) grid = dim3(((P.NT + C.G - 1) / C.G) * nc, C.nouter, nb);
+    else grid = dim3(((C.nouter + C.G - 1) / C.G) * nc, P.NT, nb);
     switch (C.P) {
         case 1: return launch_reg<1>(P, Bf, A, C, grid, W, s);
         case 2: return launch_reg<2>(P, Bf, A, C, grid, W, s);

@@ -142,4 +142,90 @@ __device__ __forceinline__ void col_fft(float2* v, float2* buf, int ld, int col,
     __syncthreads();   // the buffer may be reused by the caller right after
 }
 
+// ---------------------------------------------------------------------------
+// Three-factor transform for the long lines (P = 256 N3, N3 = 2, 4 or 8): 16
+// points per thread, so that a line of P points takes N1 = P / 16 threads
+// with half the registers of the 32-point four-step above.
+//   P = 16 x N1 and N1 = 16 x N3.  Input: thread j (< N1) holds
+//   v[n2] = x[j + N1 n2].
+//   1. 16-point DFT over n2, twiddle W_P^{j k2}, transpose through `buf`.
+//   2. Thread j' = N3 a + q takes A[q + N3 n, a] (the twiddled stage-1 value
+//      of thread q + N3 n at k2 = a) for n < 16: 16-point DFT over n, twiddle
+//      W_N1^{q k'}.
+//   3. The N3-point DFT over q runs across the N3 lanes of the group by
+//      butterfly exchanges (decimation in frequency, lanes LS apart); lane q
+//      ends with output index bitrev(q).
+//   Element i of thread j' = (a, q) is then frequency a + 16 (i + 16 br(q)).
+// The transpose buffer rows are swizzled: row r at r + PADS (r / N1), so that
+// the stage-2 reads of lanes with different a spread over the banks (PADS = 4
+// for three lines per pitch, 0 when a warp reads whole 8-column rows); `buf`
+// needs P + 16 PADS rows.  Lanes q of a group must be LS apart inside one warp.
+template <int P>
+struct ColShape3 {
+    static constexpr int NPT = 16;
+    static constexpr int N1 = P / 16;     // threads per line
+    static constexpr int N3 = P / 256;    // last factor (across lanes)
+    static_assert(N3 == 2 || N3 == 4 || N3 == 8, "three-factor lengths are 512, 1024 and 2048");
+};
+
+template <int N3>
+__host__ __device__ constexpr int lane_bitrev(int q) {
+    return N3 == 2 ? q : (N3 == 4 ? ((q & 1) << 1) | (q >> 1) : ((q & 1) << 2) | (q & 2) | (q >> 2));
+}
+
+// Frequency held by element i of thread j (see above).
+template <int P>
+__device__ __forceinline__ int col3_out_row(int j, int i) {
+    constexpr int N3 = ColShape3<P>::N3;
+    return j / N3 + 16 * (i + 16 * lane_bitrev<N3>(j % N3));
+}
+
+template <int N1, int PADS>
+__device__ __forceinline__ int col3_swz(int r) { return r + PADS * (r / N1); }
+
+template <int P, bool INV, bool TW_SHARED, int PADS, int LS>
+__device__ __forceinline__ void col_fft3(float2* v, float2* buf, int ld, int col, int j, const float2* __restrict__ tw,
+                                         int twn) {
+    constexpr int N1 = ColShape3<P>::N1, N3 = ColShape3<P>::N3;
+    auto tw_at = [&](int k) {
+        float2 w = TW_SHARED ? tw[k] : __ldg(tw + k);
+        if (INV) w.y = -w.y;
+        return w;
+    };
+    // 1. 16 points at stride N1, twiddle W_P^{j k2}, transpose
+    fft_reg<16, INV>(v);
+    const int step = twn / P;
+#pragma unroll
+    for (int k2 = 1; k2 < 16; k2++) v[k2] = cmul(v[k2], tw_at(j * k2 * step));
+    __syncthreads();
+#pragma unroll
+    for (int k2 = 0; k2 < 16; k2++) buf[col3_swz<N1, PADS>(k2 * N1 + j) * ld + col] = v[k2];
+    __syncthreads();
+    // 2. thread (a, q): 16 points of column a at stride N3, twiddle W_N1^{q k'}
+    const int a = j / N3, q = j % N3;
+#pragma unroll
+    for (int n = 0; n < 16; n++) v[n] = buf[col3_swz<N1, PADS>(a * N1 + q + N3 * n) * ld + col];
+    fft_reg<16, INV>(v);
+    const int step2 = twn / N1;
+#pragma unroll
+    for (int k = 1; k < 16; k++) v[k] = cmul(v[k], tw_at(q * k * step2));
+    // 3. N3 points across the lanes of the group: at each level the lower lane
+    // of a pair keeps x_lo + x_hi, the upper lane (x_lo - x_hi) W_len^{p - half}
+#pragma unroll
+    for (int half = N3 / 2; half >= 1; half >>= 1) {
+        const int p = q & (2 * half - 1);
+        const bool upper = p >= half;
+        const float2 w = upper ? tw_at((p - half) * (twn / (2 * half))) : make_float2(1.f, 0.f);
+#pragma unroll
+        for (int e = 0; e < 16; e++) {
+            float2 o;
+            o.x = __shfl_xor_sync(0xffffffffu, v[e].x, half * LS);
+            o.y = __shfl_xor_sync(0xffffffffu, v[e].y, half * LS);
+            const float2 lo = upper ? o : v[e], hi = upper ? v[e] : o;
+            v[e] = upper ? cmul(csub(lo, hi), w) : cadd(lo, hi);
+        }
+    }
+    __syncthreads();   // the buffer may be reused by the caller right after
+}
+
 }  // namespace mq

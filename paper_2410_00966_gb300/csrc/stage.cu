@@ -30,7 +30,8 @@ namespace mq {
 // FX: the fixed shape of the large grids (see xpass_fixed) at compile time.
 template <int L, bool FX>
 __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xfwd(Plan P, Buffers Bf, StageArgs A) {
-    constexpr int NPT = ColShape<L>::NPT, N1 = ColShape<L>::N1;
+    constexpr bool F3 = xpass_f3(L);
+    constexpr int NPT = F3 ? 16 : ColShape<L>::NPT, N1 = xpass_line_threads(L);
     constexpr int RF = xpass_rows(L);
     extern __shared__ float2 sm[];
     const int b = A.inst0 + blockIdx.y;
@@ -55,7 +56,7 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xfwd(Pla
         si.prefetch(Bf, bytes);
     }
     float2* zs = sm;
-    float2* stw = sm + L * ld;                 // exp(-2 pi i e / px), e < px
+    float2* stw = sm + xpass_fft_rows(L) * ld; // exp(-2 pi i e / px), e < px
     const int tws = P.twn / px;
     for (int e = threadIdx.x; e < px; e += nthr) stw[e] = __ldg(Bf.tw + e * tws);
     // rows nx/2.. of the packed line are zero padding (rows below are all written)
@@ -75,14 +76,23 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xfwd(Pla
     }
     __syncthreads();
     {
+        // three-factor: a line's 64 threads are consecutive (lane groups of
+        // the last factor inside one warp); otherwise lines are fastest
         const int nl = 3 * Rb;
-        const int line = threadIdx.x % nl, j = threadIdx.x / nl;
+        const int line = F3 ? threadIdx.x / N1 : threadIdx.x % nl;
+        const int j = F3 ? threadIdx.x % N1 : threadIdx.x / nl;
         float2 v[NPT];
 #pragma unroll
         for (int n2 = 0; n2 < NPT; n2++) v[n2] = zs[(j + N1 * n2) * ld + line];
-        col_fft<L, false, true>(v, zs, ld, line, j, stw, px);
+        if constexpr (F3) {
+            col_fft3<L, false, true, XPASS_F3_PADS, 1>(v, zs, ld, line, j, stw, px);
 #pragma unroll
-        for (int i = 0; i < NPT; i++) zs[col_out_row<L>(j, i) * ld + line] = v[i];
+            for (int i = 0; i < NPT; i++) zs[col3_out_row<L>(j, i) * ld + line] = v[i];
+        } else {
+            col_fft<L, false, true>(v, zs, ld, line, j, stw, px);
+#pragma unroll
+            for (int i = 0; i < NPT; i++) zs[col_out_row<L>(j, i) * ld + line] = v[i];
+        }
     }
     __syncthreads();
 
@@ -273,7 +283,7 @@ __global__ void k_set_dt(InstState* st, int B, double dt) {
 // Rows per x-pass block: R lines of 3 components times N1 = L / 32 threads
 // each, aiming at ~192 threads per block.
 int rows_per_block(int L, int nrows) {
-    int n1 = col_threads_per_column(L);
+    int n1 = xpass_line_threads(L);
     int R = 64 / n1;
     if (R < 1) R = 1;
     if (R > nrows) R = nrows;
@@ -282,7 +292,7 @@ int rows_per_block(int L, int nrows) {
 
 
 // shared memory of the x forward: the packed lines and the px-entry twiddle table
-size_t xfwd_smem(const Plan& P) { return ((size_t)P.L * xpass_ld(P.R) + P.px) * sizeof(float2); }
+size_t xfwd_smem(const Plan& P) { return ((size_t)xpass_fft_rows(P.L) * xpass_ld(P.R) + P.px) * sizeof(float2); }
 
 
 bool x_fits(const Plan& P) { return P.L <= 1024 && xthreads(P) <= 512 && xinv_smem(P) <= 200 * 1024; }

@@ -29,7 +29,8 @@ namespace mq {
 // rows per block with none left over, tiles of 8 kx columns) at compile time.
 template <int L, bool REC, int NM, bool FX>
 __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Plan P, Material mat, Buffers Bf, StageArgs A) {
-    constexpr int NPT = ColShape<L>::NPT, N1 = ColShape<L>::N1;
+    constexpr bool F3 = xpass_f3(L);
+    constexpr int NPT = F3 ? 16 : ColShape<L>::NPT, N1 = xpass_line_threads(L);
     constexpr int RF = xpass_rows(L);
     extern __shared__ float2 sm[];
     __shared__ double s_red[32];
@@ -149,14 +150,23 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
     }
     __syncthreads();
     {
+        // three-factor: a line's 64 threads are consecutive (lane groups of
+        // the last factor inside one warp); otherwise lines are fastest
         const int nl = 3 * Rb;
-        const int line = threadIdx.x % nl, j = threadIdx.x / nl;
+        const int line = F3 ? threadIdx.x / N1 : threadIdx.x % nl;
+        const int j = F3 ? threadIdx.x % N1 : threadIdx.x / nl;
         float2 v[NPT];
 #pragma unroll
         for (int n2 = 0; n2 < NPT; n2++) v[n2] = xs[(j + N1 * n2) * ld + line];
-        col_fft<L, true>(v, xs, ld, line, j, Bf.tw, P.twn);
+        if constexpr (F3) {
+            col_fft3<L, true, false, XPASS_F3_PADS, 1>(v, xs, ld, line, j, Bf.tw, P.twn);
 #pragma unroll
-        for (int i = 0; i < NPT; i++) xs[col_out_row<L>(j, i) * ld + line] = v[i];
+            for (int i = 0; i < NPT; i++) xs[col3_out_row<L>(j, i) * ld + line] = v[i];
+        } else {
+            col_fft<L, true>(v, xs, ld, line, j, Bf.tw, P.twn);
+#pragma unroll
+            for (int i = 0; i < NPT; i++) xs[col_out_row<L>(j, i) * ld + line] = v[i];
+        }
     }
     __syncthreads();
 
