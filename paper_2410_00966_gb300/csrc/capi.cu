@@ -10,6 +10,9 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "adjoint.cuh"
 #include "common.cuh"
 #include "mmcq.h"
@@ -17,7 +20,8 @@
 namespace mq {
 cudaError_t set_smem_limits();
 cudaError_t launch_xfwd(const Plan&, const Buffers&, const StageArgs&, int, cudaStream_t);
-cudaError_t launch_xinv(const Plan&, const Material&, const Buffers&, const StageArgs&, int, cudaStream_t);
+cudaError_t launch_xinv(const Plan&, const Material&, const Buffers&, const StageArgs&, int, cudaStream_t,
+                        const SpecMap*);
 cudaError_t launch_convolution(const Plan&, const Buffers&, const StageArgs&, int, cudaStream_t);
 cudaError_t launch_conv_part(const Plan&, const Buffers&, const StageArgs&, int, cudaStream_t, int);
 int convolution_launches(const Plan&);
@@ -103,6 +107,7 @@ struct mmcq {
     struct Post { void* host = nullptr; cudaEvent_t ev = nullptr; };
     std::vector<Post> posts;
     int post_head = 0, post_count = 0;
+    SpecMap spec_map{};     // TMA map of the x-half-spectrum (pipelined x inverse)
 };
 
 enum { CLS_XFWD = 0, CLS_CONV2D, CLS_YFWD, CLS_ZCONV, CLS_YINV, CLS_XINV, NCLS };
@@ -275,7 +280,7 @@ int launch_timed(mmcq_t* h, int cls, const StageArgs& A, int nb, int part) {
         CK(h, cudaEventRecord(h->events[ev], h->stream));
     }
     if (cls == CLS_XFWD) CK(h, launch_xfwd(h->P, h->Bf, A, nb, h->stream));
-    else if (cls == CLS_XINV) CK(h, launch_xinv(h->P, h->mat, h->Bf, A, nb, h->stream));
+    else if (cls == CLS_XINV) CK(h, launch_xinv(h->P, h->mat, h->Bf, A, nb, h->stream, &h->spec_map));
     else CK(h, launch_conv_part(h->P, h->Bf, A, nb, h->stream, part));
     h->launches++;
     if (h->profiling) {
@@ -302,6 +307,9 @@ int check_flags(mmcq_t* h) {
     int f = 0;
     CK(h, cudaStreamSynchronize(h->stream));
     CK(h, cudaMemcpy(&f, h->Bf.flags, sizeof(int), cudaMemcpyDeviceToHost));
+    if (f & FLAG_TIMEOUT)
+        return fail(h, MMCQ_ERR_TIMEOUT, "a bulk copy into shared memory did not complete within its wait limit; "
+                                         "the handle's state is undefined");
     if (f & (FLAG_NAN | FLAG_DT_UNDERFLOW)) {
         int z = 0;
         CK(h, cudaMemcpy(h->Bf.flags, &z, sizeof(int), cudaMemcpyHostToDevice));
@@ -333,6 +341,34 @@ int enqueue_steps(mmcq_t* h, int64_t n) {
             }
         }
     }
+    return MMCQ_OK;
+}
+
+// The 4-D tensor map of the x-half-spectrum [B nz][NT][ny][3 TX] (complex64
+// values copied as 8-byte elements), box = one row: 3 TX x 1 x NT x 1.  Only
+// for the shapes the pipelined x inverse takes; otherwise map.valid = false.
+int encode_spec_map(mmcq_t* h) {
+    const Plan& P = h->P;
+    h->spec_map.valid = false;
+    if (!(P.L == 1024 && P.TX == 8 && P.R == 1 && P.NT <= 256)) return MMCQ_OK;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return fail(h, MMCQ_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    const cuuint64_t row = 3ull * P.TX;
+    cuuint64_t dims[4] = {row, (cuuint64_t)P.ny, (cuuint64_t)P.NT, (cuuint64_t)P.B * P.nz};
+    cuuint64_t strides[3] = {row * 8, row * 8 * P.ny, row * 8 * P.ny * P.NT};   // bytes, dims 1..3
+    cuuint32_t box[4] = {(cuuint32_t)row, 1, (cuuint32_t)P.NT, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    static_assert(sizeof(CUtensorMap) == sizeof(TensorMap), "tensor map size");
+    CUresult r = encode(reinterpret_cast<CUtensorMap*>(&h->spec_map.map), CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
+                        h->Bf.spec, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(h, MMCQ_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    h->spec_map.base = h->Bf.spec;
+    h->spec_map.valid = true;
     return MMCQ_OK;
 }
 
@@ -442,6 +478,7 @@ int mmcq_create(mmcq_t** out, const mmcq_grid* g, double Ms, double Aex, double 
     if (!ok) { h->err = "device allocation failed"; return bail(MMCQ_ERR_CUDA); }
 
     if (set_smem_limits() != cudaSuccess) return bail(MMCQ_ERR_CUDA);
+    if (encode_spec_map(h) != MMCQ_OK) return bail(MMCQ_ERR_CUDA);
     {
         std::vector<float2> t(P.twn);
         for (int k = 0; k < P.twn; k++) {
@@ -799,7 +836,7 @@ int mmcq_take_cavity(mmcq_t* h, mmcq_cavity* out) {
     int f = 0;
     std::memcpy(&f, p + sizeof(InstState) * B + sizeof(double) * B, sizeof(int));
     fill_cavity(h, st, X, 0, B, 0, out);
-    if (f & (FLAG_NAN | FLAG_DT_UNDERFLOW)) return check_flags(h);
+    if (f & (FLAG_NAN | FLAG_DT_UNDERFLOW | FLAG_TIMEOUT)) return check_flags(h);
     return MMCQ_OK;
 }
 
@@ -950,7 +987,7 @@ int adj_field(mmcq_t* h, const Buffers& Bq, int terms) {
     const int B = h->P.B;
     CK(h, launch_xfwd(h->P, Bq, A, B, h->stream));
     CK(h, launch_convolution(h->P, Bq, A, B, h->stream));
-    CK(h, launch_xinv(h->P, h->mat, Bq, A, B, h->stream));
+    CK(h, launch_xinv(h->P, h->mat, Bq, A, B, h->stream, &h->spec_map));
     return MMCQ_OK;
 }
 

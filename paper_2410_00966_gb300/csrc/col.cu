@@ -467,17 +467,31 @@ __global__ void __launch_bounds__(512, (FIXED && PH == 1024) ? 2 : 1) k_col_spli
             }
             fft(v, true);
             if (valid) {
+                if (J == 0) {
 #pragma unroll
-                for (int i = 0; i < NPT; i++) {
-                    const int k = out_row(i);
-                    if (k >= C.n_out) continue;
-                    float2* q = out + k * out_r;
-                    if (J == 0) {
-                        *q = v[i];
-                    } else {
-                        const float2 y = cmul(v[i], conjf2(stw[k]));
-                        const float2 a = *q;
-                        *q = make_float2(a.x + y.x, a.y + y.y);
+                    for (int i = 0; i < NPT; i++) {
+                        const int k = out_row(i);
+                        if (k < C.n_out) out[k * out_r] = v[i];
+                    }
+                } else {
+                    // the even half's rows come back in groups of 4 loads in
+                    // flight at once (a store between two loads of the same
+                    // array would otherwise order every load after the
+                    // previous store)
+#pragma unroll
+                    for (int i0 = 0; i0 < NPT; i0 += 4) {
+                        float2 a[4];
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            const int k = out_row(i0 + u);
+                            a[u] = k < C.n_out ? out[k * out_r] : make_float2(0.f, 0.f);
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            const int k = out_row(i0 + u);
+                            const float2 y = cmul(v[i0 + u], conjf2(stw[k]));
+                            if (k < C.n_out) out[k * out_r] = make_float2(a[u].x + y.x, a[u].y + y.y);
+                        }
                     }
                 }
             }

@@ -14,7 +14,21 @@ constexpr int XINV_THREADS = 768;  // register budget of the torque kernel (85 p
 
 enum Kind { KIND_RK4 = 0, KIND_DP45 = 1 };
 enum CavMode { CAV_E = 0, CAV_P = 1 };
-enum Flag { FLAG_NAN = 1, FLAG_DT_UNDERFLOW = 2, FLAG_HIST_FULL = 4 };
+enum Flag { FLAG_NAN = 1, FLAG_DT_UNDERFLOW = 2, FLAG_HIST_FULL = 4, FLAG_TIMEOUT = 8 };
+
+// A TMA tensor map (the driver's 128-byte CUtensorMap, opaque here), passed to
+// kernels by value as a __grid_constant__ parameter.
+struct alignas(64) TensorMap {
+    unsigned long long v[16];
+};
+
+// The tensor map of a handle's x-half-spectrum (4-D: 3 TX values of a tile
+// row, y, tile, plane), encoded on the host for the spectrum at `base`.
+struct SpecMap {
+    TensorMap map;
+    const void* base;
+    bool valid;
+};
 
 // x / d for 0 <= x < 2^31 by multiply-high (Granlund & Montgomery 1994):
 // s = ceil(log2 d), m = floor(2^32 (2^s - d) / d) + 1, q = (mulhi(x, m) + x) >> s.

@@ -36,6 +36,55 @@ __device__ __forceinline__ void prefetch_l2(const void* src, unsigned bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"(bytes) : "memory");
 }
 
+// ---- bulk tensor copies (TMA) completing on an mbarrier --------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// Order this thread's earlier shared-memory accesses (generic proxy) before
+// later bulk copies (async proxy) into the same memory, and make an mbarrier
+// initialisation visible to them.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// Arrive on `bar` expecting `bytes` from bulk copies, then copy the box at
+// coordinates (c0, c1, c2, c3) (innermost first) of the 4-D tensor map into
+// shared memory at `dst` (128-byte aligned); the copy completes on `bar`.
+__device__ __forceinline__ void tma_load_4d(void* dst, const TensorMap* map, int c0, int c1, int c2, int c3,
+                                            unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;\n" : "=l"(t));
+    return t;
+}
+
+// Wait until the phase of `bar` with the given parity has completed, for at
+// most `limit_ns` nanoseconds; false if the wait gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, unsigned long long limit_ns) {
+    const unsigned a = smem_u32(bar);
+    unsigned long long t0 = 0;
+    for (int it = 0;; it++) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (it == 0) t0 = global_ns();
+        else if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+
 // DP45: stage 1 lives in k1slot (first-same-as-last swap between buffers 0 and 6)
 __device__ __forceinline__ int k_slot(const InstState& s, int j) { return j == 0 ? s.k1slot : j; }
 

@@ -302,7 +302,7 @@ struct CellUpdate {
     float G[NM], bs[NM];
     bool on[NM];
     float dt, bex, bey, bez, D;
-    bool want_anis, want_zee, want_cav, field_only;
+    bool want_demag, want_exch, want_anis, want_zee, want_cav, field_only;
     int K, s, mode, nm;
     long long cb, fb;    // first cell of this instance; of the launch's first instance (field output)
     float4* kout;
@@ -322,6 +322,7 @@ struct CellUpdate {
         D = drive;
         dt = (float)st.dt;
         bex = (float)ip.bext[0]; bey = (float)ip.bext[1]; bez = (float)ip.bext[2];
+        want_demag = A.terms & 1; want_exch = A.terms & 2;
         want_anis = A.terms & 4; want_zee = A.terms & 8; want_cav = A.terms & 16;
         field_only = A.field_only != 0;
         K = A.kind; s = A.stage; mode = A.mode;
