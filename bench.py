@@ -1,20 +1,26 @@
 """Benchmark of the LLG + cavity hot path on GB300.
 
-Default workload: the YIG-wire omega_c sweep -- 21 instances of a 256x64x16
-grid of 5 nm cells (Ms 1.4e5 A/m, A 3.65e-12 J/m, alpha 1e-4, Ku 1e3 J/m^3
-along the wire, bias 100 mT), cavity frequencies spread over the uniform mode,
-g/2pi = 50 MHz, kappa/2pi = 10 MHz, Dormand-Prince tol 1e-6 -- integrated as one
-batch.  One step = one Dormand-Prince attempt of every instance.
+Default workload: the largest grid -- a CPW-like Permalloy film of 1024 x 1024
+x 8 cells of 4 nm (8.4 M cells; Ms 8e5 A/m, A 1.3e-11 J/m, alpha 0.01, bias
+30 mT along x), coupled to the cavity through a Lorentzian profile
+g(x) = g0 / (1 + (x / 500 nm)^2), g0/2pi = 20 MHz, omega_c at the uniform
+mode, kappa/2pi = 10 MHz, integrated by Dormand-Prince (tol 1e-6).  One step =
+one Dormand-Prince attempt.  Other workloads: --workload yig_wire (the 21-value
+omega_c sweep of a 256x64x16 YIG wire, one batch), batched (64 mixed-grid
+instances, CUDA graphs), adjoint (forward + discrete adjoint), film.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload ...]
 
 Prints one JSON line.  `value` counts accepted cell-steps (cells x accepted
 steps, summed over instances and ranks) per second of device time; the
 roofline object reports the dominant kernel's algorithmic bytes per launch over
-its event-timed duration, against the measured HBM copy bandwidth.
-Multi-GPU (torchrun): every rank integrates its own sweep (independent
-instances, no data exchange; weak scaling).  The reference arm times the FP64
-CPU oracle on a bounded sample of the same workload.
+its event-timed duration, against the measured HBM copy bandwidth.  `parity`
+gives the error against the FP64 oracle, which replays the accepted steps of
+the first two (warm-up) attempts of instance 0 from the same initial state;
+the time of that replay is the CPU baseline.
+Multi-GPU (torchrun): every rank integrates its own instances (independent,
+no data exchange; weak scaling).  The reference arm times the FP64 CPU oracle
+on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -147,59 +153,97 @@ def reduce_over_ranks(dist, device, ms: float, cell_steps: float):
     return float(t.item()), float(c.item())
 
 
-def cpu_oracle_sample(w, attempts: int):
-    """Time the FP64 oracle on instance 0 of the workload for `attempts` steps."""
+def oracle_for(I, w):
+    """The FP64 oracle set up like instance I of workload w (E-mode cavity)."""
     import numpy as np
     import oracle
-    I = w.instances[0]
     o = oracle.Oracle(I.nx, I.ny, I.nz, I.d, I.d, I.d, I.Ms, I.Aex, I.alpha, Ku=I.Ku, axis=I.axis)
     o.set_m(I.m0().astype(np.float64))
     o.set_bias(I.bias)
     prof = I.coupling_profile()
     o.set_cavity(I.omega_c, I.kappa, I.g, profile=None if prof is None else prof.astype(np.float64))
     o.set_integrator(oracle.DP45 if w.integrator == "dp45" else oracle.RK4, w.tol, oracle.CAV_E)
+    return o
+
+
+def cpu_oracle_sample(w, attempts: int):
+    """Time the FP64 oracle on instance 0 of the workload for `attempts` steps
+    (then on until about 10 s of CPU work)."""
+    o = oracle_for(w.instances[0], w)
     o.step(1, w.dt)   # first attempt outside the timing (sets the trial step)
     t0 = time.perf_counter()
     acc = 0
     done = 0
-    # at least `attempts`, then on until about 10 s of CPU work
     while done < attempts or (time.perf_counter() - t0 < 10.0 and done < 50 * attempts):
         acc += o.step(1, 0.0 if w.integrator == "dp45" else w.dt)
         done += 1
     dt = time.perf_counter() - t0
-    return acc * I.n / dt, dt, acc
+    return acc * w.instances[0].n / dt, dt, acc
+
+
+def oracle_replay_parity(w, prefix):
+    """Replay the GPU's accepted steps of the prefix (instance 0) in the oracle
+    from the same initial state; returns the error figures and the replay's
+    CPU throughput (the CPU baseline of the large workload)."""
+    import numpy as np
+    import oracle
+    I = w.instances[0]
+    t_setup = time.perf_counter()
+    o = oracle_for(I, w)
+    t_setup = time.perf_counter() - t_setup
+    hist = prefix["dt_history"]
+    t0 = time.perf_counter()
+    if w.integrator == "dp45":
+        o.replay(hist)
+    else:
+        o.step(len(hist), w.dt)
+    el = time.perf_counter() - t0
+    m_o = o.get_m()
+    dm = float(np.abs(prefix["m"].astype(np.float64) - m_o).max())
+    oc = o.cavity()
+    c = prefix["cavity"]
+    a_o = complex(oc["re_alpha"], oc["im_alpha"])
+    a_g = complex(c["re_alpha"], c["im_alpha"])
+    return {"max_dm": dm, "alpha_rel_err": abs(a_g - a_o) / abs(a_o) if a_o != 0 else None,
+            "alpha_gpu": [a_g.real, a_g.imag], "alpha_oracle": [a_o.real, a_o.imag],
+            "steps_replayed": len(hist), "t_replayed": float(np.sum(hist)), "instance": 0,
+            "oracle_setup_s": t_setup, "oracle_replay_s": el,
+            "bar": "max|dm| <= 1e-5 per component"}, len(hist) * I.n / el, el
 
 
 def run_reference(args):
+    """The FP64 oracle on instance 0 of the workload, one attempt (step) at a
+    time on the host cores; the number of timed steps is capped so that the
+    run ends within a few minutes (one attempt of the largest grid takes tens
+    of seconds)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    import numpy as np
     import oracle
     oracle.build()
     w = workload_instances(args.workload, 0)
     I = w.instances[0]
-    o = oracle.Oracle(I.nx, I.ny, I.nz, I.d, I.d, I.d, I.Ms, I.Aex, I.alpha, Ku=I.Ku, axis=I.axis)
-    o.set_m(I.m0().astype(np.float64))
-    o.set_bias(I.bias)
-    prof = I.coupling_profile()
-    o.set_cavity(I.omega_c, I.kappa, I.g, profile=None if prof is None else prof.astype(np.float64))
     dp = w.integrator == "dp45"
-    o.set_integrator(oracle.DP45 if dp else oracle.RK4, w.tol, oracle.CAV_E)
+    o = oracle_for(I, w)
+    budget_s = 60.0 if args.workload == "large" else 240.0
+    warm = 1 if args.workload == "large" else args.warmup
     o.step(1, w.dt)
-    for _ in range(args.warmup):
+    for _ in range(warm - 1):
         o.step(1, 0.0 if dp else w.dt)
     t0 = time.perf_counter()
     acc = 0
-    for _ in range(args.steps):
+    steps = 0
+    while steps < args.steps and (steps == 0 or time.perf_counter() - t0 < budget_s):
         acc += o.step(1, 0.0 if dp else w.dt)
+        steps += 1
     el = time.perf_counter() - t0
     value = acc * I.n / el
-    cores = os.cpu_count()
-    sample = f"instance 0 of the workload ({I.nx}x{I.ny}x{I.nz} cells), one {w.integrator} attempt per step"
+    cores = oracle.set_threads(0)
+    sample = (f"instance 0 of the workload ({I.nx}x{I.ny}x{I.nz} cells), {steps} {w.integrator} attempts "
+              f"({acc} accepted) after {warm} untimed, {el:.1f} s; steps capped by a {budget_s:.0f} s budget")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "steps": steps, "steps_requested": args.steps, "warmup": warm, "ms_per_step": 1e3 * el / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "instances_timed": 1, "cells_per_instance": I.n, "integrator": w.integrator},
         "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": cores, "kind": "oracle", "sample": sample},
@@ -246,9 +290,14 @@ def run_ours(args):
         if dp:
             sim.set_horizon(w.horizon)
         info = sim.info()
-        # warm-up
+        # warm-up; the state of instance 0 after the first two attempts is
+        # kept for the parity check against the oracle (after the timing)
         sim.step(1, w.dt)
-        sim.step(max(args.warmup - 1, 0), 0.0 if dp else w.dt)
+        sim.step(1, 0.0 if dp else w.dt)
+        prefix = None
+        if rank == 0 and not args.no_cpu_baseline:
+            prefix = {"m": sim.get_m(0), "cavity": sim.cavity(0), "dt_history": sim.dt_history(0)}
+        sim.step(max(args.warmup - 2, 0), 0.0 if dp else w.dt)
         sim.sync()
         acc0 = sum(c["accepted"] for c in sim.cavity(-1))
         launches0 = sim.launch_count()
@@ -338,19 +387,30 @@ def run_ours(args):
         sim.close()
 
     cpu = None
+    parity = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        attempts = 3 if args.workload == "yig_wire" else 20
         cores = oracle.set_threads(0)
-        v, el, acc = cpu_oracle_sample(w, attempts)
-        oracle.set_threads(1)
-        v1, el1, acc_1 = cpu_oracle_sample(w, 1)
-        oracle.set_threads(0)
-        cpu = {"value": v, "unit": "cell-steps/s", "cores": cores, "kind": "oracle",
-               "sample": f"{acc} accepted {w.integrator} steps of instance 0 ({I0.nx}x{I0.ny}x{I0.nz} cells), "
-                         f"{el:.1f} s",
-               "single_thread": {"value": v1, "sample": f"{acc_1} accepted steps, {el1:.1f} s"}}
+        if args.workload == "large":
+            # the replay of the warm-up prefix is both the parity check and the
+            # CPU baseline (one attempt of this grid is tens of seconds of CPU)
+            parity, v, el = oracle_replay_parity(w, prefix)
+            cpu = {"value": v, "unit": "cell-steps/s", "cores": cores, "kind": "oracle",
+                   "sample": f"FP64 replay of the {parity['steps_replayed']} accepted {w.integrator} steps of the "
+                             f"first two attempts of instance 0 ({I0.nx}x{I0.ny}x{I0.nz} cells), {el:.1f} s"}
+        else:
+            attempts = 3 if args.workload == "yig_wire" else 20
+            v, el, acc = cpu_oracle_sample(w, attempts)
+            oracle.set_threads(1)
+            v1, el1, acc_1 = cpu_oracle_sample(w, 1)
+            oracle.set_threads(0)
+            cpu = {"value": v, "unit": "cell-steps/s", "cores": cores, "kind": "oracle",
+                   "sample": f"{acc} accepted {w.integrator} steps of instance 0 ({I0.nx}x{I0.ny}x{I0.nz} cells), "
+                             f"{el:.1f} s",
+                   "single_thread": {"value": v1, "sample": f"{acc_1} accepted steps, {el1:.1f} s"}}
+            if prefix is not None:
+                parity, _, _ = oracle_replay_parity(w, prefix)
 
     if rank == 0:
         line = {
@@ -368,6 +428,7 @@ def run_ours(args):
                        "step_model_efficiency": (step_bytes / args.steps) / (ms_max / args.steps / 1e3) / 1e9 / peak},
             "roofline": roof,
             "cpu_baseline": cpu,
+            "parity": parity,
             "e2e": e2e,
             "clocks": clk,
             "gpu_launches": launches,
@@ -548,7 +609,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="yig_wire", choices=["yig_wire", "film", "large", "batched", "adjoint"])
+    ap.add_argument("--workload", default="large", choices=["large", "yig_wire", "film", "batched", "adjoint"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--instances", type=int, default=0, help="use only the first N instances (profiling)")

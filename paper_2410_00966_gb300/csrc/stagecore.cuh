@@ -336,7 +336,7 @@ struct CellUpdate {
     // (Bx, By, Bz) holds demag + exchange on entry
     template <bool REC>
     __device__ __forceinline__ void run(const Material& mat, const Buffers& Bf, long long i, float4 m, float Bx,
-                                        float By, float Bz, float (&xacc)[NM], double (&macc)[REC ? 3 : 1],
+                                        float By, float Bz, double (&xacc)[NM], double (&macc)[REC ? 3 : 1],
                                         float& emax, bool& bad) const {
         const float Ms = m.w;
         float px_[NM], py_[NM], pz_[NM];
@@ -407,13 +407,11 @@ struct CellUpdate {
                 emax = fmaxf(emax, en);
             }
         }
-        // per-cell products, and a thread's partial over its few cells, in
-        // FP32; the caller widens the partial to FP64 for the block and
-        // instance sums (the sum over all cells is the quantity that needs the
-        // range, and FP64 issues at a small fraction of the FP32 rate here)
+        // the coupling sums: each cell's product in FP32, promoted and
+        // accumulated in FP64 (thread, block and instance sums)
 #pragma unroll
         for (int q = 0; q < NM; q++)
-            if (on[q]) xacc[q] += Ms * (mx.x * px_[q] + mx.y * py_[q] + mx.z * pz_[q]);
+            if (on[q]) xacc[q] += (double)(Ms * (mx.x * px_[q] + mx.y * py_[q] + mx.z * pz_[q]));
         if constexpr (REC) {
             if (Ms > 0.f) { macc[0] += mrec.x; macc[1] += mrec.y; macc[2] += mrec.z; }
         }

@@ -3,8 +3,8 @@
 // giving B_demag, then exchange + anisotropy + Zeeman (with the Appendix C
 // excitation) + cavity sum_k B_rms,k Gamma_k (Sec. 2.1 field terms, Eq. bcav),
 // the LLG torque (Eq. llg), the RK bookkeeping, and block partials of the
-// coupling sums X_k = V_c sum_i Ms_i m_i . B_rms,k,i (Eq. gammafinal): FP32
-// over a thread's few cells, FP64 over the block.  The last block of each
+// coupling sums X_k = V_c sum_i Ms_i m_i . B_rms,k,i (Eq. gammafinal): each
+// cell's FP32 product promoted and added in FP64.  The last block of each
 // instance to finish reduces the partials in a fixed order and advances the
 // cavity amplitudes and the step-size controller in FP64.
 #include <math.h>
@@ -25,7 +25,7 @@ template <int NM, bool REC>
 __device__ __forceinline__ void xinv_cells(const Plan& P, const Material& mat, const Buffers& Bf,
                                            const CellUpdate<NM>& cu, const float2* xs, int ld, const float4* msrc,
                                            long long base, int nx, int nr, int nthr, const int2* s_yz,
-                                           float (&xacc)[NM], double (&macc)[REC ? 3 : 1], float& emax, bool& bad) {
+                                           double (&xacc)[NM], double (&macc)[REC ? 3 : 1], float& emax, bool& bad) {
     const bool want_demag = cu.want_demag, want_exch = cu.want_exch;
     const int pl = nx * P.ny;
     // cell ii = r nx + x of the block; (x, r) advance by the block size
@@ -231,18 +231,15 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
 
     CellUpdate<NM> cu;
     cu.init(Bf, A, st, ip, s_gamma, s_drive, cb, (long long)A.inst0 * P.N);
-    float xacc[NM];
+    double xacc[NM];
 #pragma unroll
-    for (int q = 0; q < NM; q++) xacc[q] = 0.f;
+    for (int q = 0; q < NM; q++) xacc[q] = 0.0;
     double macc[REC ? 3 : 1] = {};
     float emax = 0.f;
     bool bad = false;
     xinv_cells<NM, REC>(P, mat, Bf, cu, xs, ld, msrc, base, nx, nr, nthr, s_yz, xacc, macc, emax, bad);
     if (A.field_only) return;
-    double xd[NM];
-#pragma unroll
-    for (int q = 0; q < NM; q++) xd[q] = (double)xacc[q];
-    stage_epilogue<REC, NM>(P, mat, Bf, A, b, blockIdx.x, P.nblk, xd, emax, bad, s_red, s_redf, &s_last, macc);
+    stage_epilogue<REC, NM>(P, mat, Bf, A, b, blockIdx.x, P.nblk, xacc, emax, bad, s_red, s_redf, &s_last, macc);
 }
 
 // ---------------------------------------------------------------------------
@@ -318,9 +315,9 @@ __global__ void __launch_bounds__(XPASS_THREADS, XPIPE_BLOCKS) k_xinv_pipe(Plan 
 
     CellUpdate<NM> cu;
     cu.init(Bf, A, st, ip, s_gamma, s_drive, cb, (long long)A.inst0 * P.N);
-    float xacc[NM];
+    double xacc[NM];
 #pragma unroll
-    for (int q = 0; q < NM; q++) xacc[q] = 0.f;
+    for (int q = 0; q < NM; q++) xacc[q] = 0.0;
     double macc[REC ? 3 : 1] = {};
     float emax = 0.f;
     bool bad = false;
@@ -384,10 +381,7 @@ __global__ void __launch_bounds__(XPASS_THREADS, XPIPE_BLOCKS) k_xinv_pipe(Plan 
         __syncthreads();   // buffer q and s_yz are rewritten by the next rows
     }
     if (A.field_only) return;
-    double xd[NM];
-#pragma unroll
-    for (int q = 0; q < NM; q++) xd[q] = (double)xacc[q];
-    stage_epilogue<REC, NM>(P, mat, Bf, A, b, blockIdx.x, gridDim.x, xd, emax, bad, s_red, s_redf, &s_last, macc);
+    stage_epilogue<REC, NM>(P, mat, Bf, A, b, blockIdx.x, gridDim.x, xacc, emax, bad, s_red, s_redf, &s_last, macc);
 }
 
 // Whether the pipelined row kernel applies (see k_xinv_pipe) with this map.
