@@ -161,6 +161,37 @@ def test_kittel_single_prism_cell(oracle_mod):
     assert abs(measured / w - 1) < 1e-6
 
 
+def _zero_crossing_frequency(ts, ys):
+    cross = [ts[i] - ys[i] * (ts[i + 1] - ts[i]) / (ys[i + 1] - ys[i]) for i in range(len(ys) - 1)
+             if ys[i] < 0 <= ys[i + 1]]
+    return 2 * math.pi / np.mean(np.diff(cross))
+
+
+def test_kittel_multicell_element_approaches_macrospin(oracle_mod):
+    # several cells, so the FFT demag convolution, exchange and Zeeman all act:
+    # an element below the exchange length (5.7 nm for Permalloy) stays close
+    # to uniform and precesses near Kittel's frequency with the element's
+    # prism factors; the deviation (non-uniform demag field) grows with size
+    Ms, B = 8e5, 0.1
+    dev = []
+    for nx, ny, nz in [(6, 4, 2), (12, 8, 4)]:
+        d = 2e-9
+        o = oracle_mod.Oracle(nx, ny, nz, d, d, d, Ms, 1.3e-11, 0.0)
+        th = 1e-3
+        o.set_m(np.tile([math.cos(th), math.sin(th), 0.0], (nx * ny * nz, 1)))
+        o.set_bias([B, 0, 0])
+        D = _prism_factors(oracle_mod, nx * d, ny * d, nz * d)
+        w = oracle_mod.GAMMA_LL * math.sqrt((B + (D[1] - D[0]) * oracle_mod.MU0 * Ms) *
+                                            (B + (D[2] - D[0]) * oracle_mod.MU0 * Ms))
+        dt = 2 * math.pi / w / 2000      # resolves the exchange modes of 2 nm cells
+        o.set_recording(True)
+        o.step(12000, dt)
+        h = o.mavg_history()
+        dev.append(_zero_crossing_frequency(h[:, 0], h[:, 2]) / w - 1)
+    assert abs(dev[0]) < 5e-3
+    assert abs(dev[1]) > abs(dev[0])
+
+
 # ---------------------------------------------------------------------------
 # cavity: Dicke-model benchmarks (Sec. 4) and the memory term
 # ---------------------------------------------------------------------------
