@@ -290,6 +290,7 @@ def run_ours(args):
         if dp:
             sim.set_horizon(w.horizon)
         info = sim.info()
+        tuning = sim.autotune(reps=7)   # launch parameters of this grid, chosen by timing
         # warm-up; the state of instance 0 after the first two attempts is
         # kept for the parity check against the oracle (after the timing)
         sim.step(1, w.dt)
@@ -422,7 +423,7 @@ def run_ours(args):
                        "cavity_mode": "E", "parallelism": "independent instances per rank",
                        "accepted_steps": acc1 - acc0, "rejected_steps": rej,
                        "l2": f"inputs larger than L2 ({info['device_bytes'] / 1e9:.2f} GB resident)",
-                       "padded": [info["px"], info["py"], info["pz"]], "tile": info["tile"],
+                       "padded": [info["px"], info["py"], info["pz"]], "tile": info["tile"], "tuning": tuning,
                        "algorithmic_bytes_per_step": step_bytes / args.steps,
                        "field_evals_per_s": B * (6 if dp else 4) * args.steps / (ms_max / 1e3),
                        "step_model_efficiency": (step_bytes / args.steps) / (ms_max / args.steps / 1e3) / 1e9 / peak},
@@ -443,8 +444,10 @@ def run_ours(args):
 def run_batched(args):
     """The batched anticrossing map: 64 Permalloy instances on four grid sizes
     (32x32x1, 64x64x2, 128x128x2, 256x256x4), one batched handle per grid
-    size, all stepped together as one CUDA graph per chunk of RK4 steps
-    (mmcq_group_*).  A step advances every instance by one RK4 step."""
+    size, each with launch parameters chosen by mmcq_autotune, all stepped
+    together as one CUDA graph per chunk of RK4 steps (mmcq_group_*).  A step
+    advances every instance by one RK4 step.  The line also gives the same
+    graphs under the fixed launch rules."""
     import torch
 
     import paper_2410_00966_gb300 as pkg
@@ -471,6 +474,8 @@ def run_batched(args):
             sim.set_integrator(pkg.MMCQ_RK4, w.tol, pkg.MMCQ_CAVITY_E)
             sims.append(sim)
         cells = sum(s.n * s.batch for s in sims)
+        # launch parameters per grid shape, chosen by timing (mmcq_autotune)
+        tuning = {"x".join(map(str, s.shape[::-1])): s.autotune(reps=7) for s in sims}
         g = pkg.Group(sims, chunk=chunk)
         steps = max(chunk, (args.steps // chunk) * chunk)
 
@@ -500,6 +505,15 @@ def run_batched(args):
             for s in sims:
                 s.step(steps, w.dt)
         ms_eager = timed(eager)
+        # the same graphs with the fixed launch rules instead of the tuned plans
+        g.close()
+        for s in sims:
+            s.set_tuning(None)
+        g = pkg.Group(sims, chunk=chunk)
+        g.step(chunk, w.dt)
+        ms_rules = timed(lambda: g.step(steps, w.dt))
+        for s, (_, t) in zip(sims, tuning.items()):
+            s.set_tuning(t)
         for s in sims:
             s.profile(True)
         ms_prof = timed(lambda: [s.step(chunk, w.dt) for s in sims])
@@ -526,6 +540,8 @@ def run_batched(args):
                    "grids": {f"{a}x{b}x{c}": len(v) for (a, b, c), v in sorted(shapes.items())},
                    "cells_per_step": cells, "integrator": "rk4", "dt": w.dt, "graph_chunk": chunk,
                    "eager_value": cells * steps / (ms_eager / 1e3),
+                   "fixed_rules_value": cells * steps / (ms_rules / 1e3),
+                   "tuning": tuning,
                    "l2": "working set below L2 (small grids; latency and launch bound)"},
         "roofline": {"bound": "hbm", "kernel": top_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,

@@ -363,6 +363,44 @@ int64_t mmcq_group_replays(const mmcq_group_t* g);
 void mmcq_group_destroy(mmcq_group_t* g);
 const char* mmcq_group_last_error(const mmcq_group_t* g);
 
+/* ---- autotuning of the launch parameters --------------------------------
+ * The paper runs Mumax3's fixed kernels; here the launch shape of each pass of
+ * the field evaluation is chosen per grid by timing.  The knobs change no data
+ * layout and no arithmetic, so every plan computes the same field:
+ *   x_rows         cells rows per block of the x passes (1 .. the rule's count);
+ *   col_groups[k]  kx tiles (y passes) or ky columns (z pass) per block of the
+ *                  column passes: k = 0 the 2-D convolution, 1 the forward y,
+ *                  2 the z pass, 3 the inverse y (0: not launched for this
+ *                  grid); a power of two up to the rule's (largest) count;
+ *   z_split        pz = 32: 1 the split z kernel (two threads per column), 0 one
+ *                  thread per column; -1: no choice for this grid;
+ *   x_pipe         rows of L = 1024 points: 1 the persistent x inverse fed by
+ *                  bulk tensor copies, 0 one row per block; -1: no choice.
+ * mmcq_autotune times one field evaluation of the whole batch at the current
+ *   state (the state does not change) under the fixed rules and under each
+ *   candidate, one knob at a time with the others at their best so far, takes
+ *   the median of `reps` timings per candidate, and keeps the fastest plan for
+ *   the later steps of the handle.  The choice is also cached for the process
+ *   (per device, grid and batch size): a later handle of the same shape gets it
+ *   without timing (out->candidates = 0).  Allocates B x N x 16 bytes of scratch
+ *   for the duration of the call.  Synchronises.
+ * mmcq_set_tuning applies a plan (MMCQ_ERR_ARG, nothing changed, if it is not
+ *   one of this grid's choices); NULL restores the fixed rules.  A group
+ *   holding the handle captures its graph again at its next step. 
+ * mmcq_get_tuning reports the plan in use (eval_ms, rule_ms, candidates 0). */
+typedef struct {
+    int x_rows;
+    int col_groups[4];
+    int z_split;
+    int x_pipe;
+    double eval_ms;        /* median time of one field evaluation of the batch with this plan */
+    double rule_ms;        /* the same with the fixed rules */
+    int candidates;        /* plans timed (0: taken from the cache) */
+} mmcq_tuning;
+int mmcq_autotune(mmcq_t* h, int reps, mmcq_tuning* out);
+int mmcq_set_tuning(mmcq_t* h, const mmcq_tuning* t);
+int mmcq_get_tuning(mmcq_t* h, mmcq_tuning* out);
+
 /* ---- measurement -------------------------------------------------------
  * Per-kernel-class timing of the launches mmcq_step enqueues.  While enabled,
  * each launch is bracketed by two CUDA events on the handle's stream; the

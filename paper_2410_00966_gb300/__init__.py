@@ -67,6 +67,12 @@ class mmcq_objective(ctypes.Structure):
                 ("window", ctypes.c_int64)]
 
 
+class mmcq_tuning(ctypes.Structure):
+    _fields_ = [("x_rows", ctypes.c_int), ("col_groups", ctypes.c_int * 4), ("z_split", ctypes.c_int),
+                ("x_pipe", ctypes.c_int), ("eval_ms", ctypes.c_double), ("rule_ms", ctypes.c_double),
+                ("candidates", ctypes.c_int)]
+
+
 class mmcq_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
                 ("bytes", ctypes.c_double)]
@@ -122,6 +128,9 @@ PROTOTYPES = {
     "mmcq_profile_read": (ctypes.c_int, [_H, ctypes.POINTER(mmcq_kernel_stat), ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int)]),
     "mmcq_launch_count": (ctypes.c_int64, [_H]),
+    "mmcq_autotune": (ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(mmcq_tuning)]),
+    "mmcq_set_tuning": (ctypes.c_int, [_H, ctypes.POINTER(mmcq_tuning)]),
+    "mmcq_get_tuning": (ctypes.c_int, [_H, ctypes.POINTER(mmcq_tuning)]),
     "mmcq_coupling_sum_noalloc": (ctypes.c_int, [_FP, _FP, _FP, ctypes.c_int64, ctypes.c_double, _DP,
                                                  ctypes.c_void_p]),
 }
@@ -337,6 +346,35 @@ class Sim:
 
     def profile(self, enable=True):
         self._ck(self._lib.mmcq_profile(self._h, int(bool(enable))))
+
+    @staticmethod
+    def _tuning_dict(t) -> dict:
+        return {"x_rows": t.x_rows, "col_groups": list(t.col_groups), "z_split": t.z_split, "x_pipe": t.x_pipe,
+                "eval_ms": t.eval_ms, "rule_ms": t.rule_ms, "candidates": t.candidates}
+
+    def autotune(self, reps=5) -> dict:
+        """Time the launch-parameter candidates of this grid and keep the fastest (mmcq_autotune)."""
+        t = mmcq_tuning()
+        self._ck(self._lib.mmcq_autotune(self._h, int(reps), ctypes.byref(t)))
+        return self._tuning_dict(t)
+
+    def tuning(self) -> dict:
+        t = mmcq_tuning()
+        self._ck(self._lib.mmcq_get_tuning(self._h, ctypes.byref(t)))
+        return self._tuning_dict(t)
+
+    def set_tuning(self, plan=None):
+        """Apply a plan (dict as returned by tuning()/autotune()); None restores the fixed rules."""
+        if plan is None:
+            self._ck(self._lib.mmcq_set_tuning(self._h, None))
+            return
+        t = mmcq_tuning()
+        t.x_rows = int(plan["x_rows"])
+        for k in range(4):
+            t.col_groups[k] = int(plan["col_groups"][k])
+        t.z_split = int(plan["z_split"])
+        t.x_pipe = int(plan["x_pipe"])
+        self._ck(self._lib.mmcq_set_tuning(self._h, ctypes.byref(t)))
 
     def profile_read(self) -> list:
         arr = (mmcq_kernel_stat * 16)()

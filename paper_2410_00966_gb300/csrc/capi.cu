@@ -6,7 +6,10 @@
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <functional>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -21,9 +24,10 @@ namespace mq {
 cudaError_t set_smem_limits();
 cudaError_t launch_xfwd(const Plan&, const Buffers&, const StageArgs&, int, cudaStream_t);
 cudaError_t launch_xinv(const Plan&, const Material&, const Buffers&, const StageArgs&, int, cudaStream_t,
-                        const SpecMap*);
-cudaError_t launch_convolution(const Plan&, const Buffers&, const StageArgs&, int, cudaStream_t);
-cudaError_t launch_conv_part(const Plan&, const Buffers&, const StageArgs&, int, cudaStream_t, int);
+                        const SpecMap*, const Tune*);
+cudaError_t launch_convolution(const Plan&, const Buffers&, const StageArgs&, int, cudaStream_t, const Tune*);
+cudaError_t launch_conv_part(const Plan&, const Buffers&, const StageArgs&, int, cudaStream_t, int, const Tune*);
+void conv_tunables(const Plan&, int*, int*);
 int convolution_launches(const Plan&);
 bool col_fits(const Plan&);
 bool fft_fits(int, int);
@@ -108,6 +112,9 @@ struct mmcq {
     std::vector<Post> posts;
     int post_head = 0, post_count = 0;
     SpecMap spec_map{};     // TMA map of the x-half-spectrum (pipelined x inverse)
+    Tune tune{{0, 0, 0, 0}, -1, -1};   // launch parameters chosen by mmcq_autotune (default: the fixed rules)
+    int rows_rule = 1;      // x-pass rows per block of the fixed rule
+    int64_t tune_epoch = 0; // bumped when the launch parameters change (groups capture again)
 };
 
 enum { CLS_XFWD = 0, CLS_CONV2D, CLS_YFWD, CLS_ZCONV, CLS_YINV, CLS_XINV, NCLS };
@@ -280,8 +287,8 @@ int launch_timed(mmcq_t* h, int cls, const StageArgs& A, int nb, int part) {
         CK(h, cudaEventRecord(h->events[ev], h->stream));
     }
     if (cls == CLS_XFWD) CK(h, launch_xfwd(h->P, h->Bf, A, nb, h->stream));
-    else if (cls == CLS_XINV) CK(h, launch_xinv(h->P, h->mat, h->Bf, A, nb, h->stream, &h->spec_map));
-    else CK(h, launch_conv_part(h->P, h->Bf, A, nb, h->stream, part));
+    else if (cls == CLS_XINV) CK(h, launch_xinv(h->P, h->mat, h->Bf, A, nb, h->stream, &h->spec_map, &h->tune));
+    else CK(h, launch_conv_part(h->P, h->Bf, A, nb, h->stream, part, &h->tune));
     h->launches++;
     if (h->profiling) {
         CK(h, cudaEventRecord(h->events[ev + 1], h->stream));
@@ -423,6 +430,7 @@ int mmcq_create(mmcq_t** out, const mmcq_grid* g, double Ms, double Aex, double 
     while ((1 << P.lt) < P.TX) P.lt++;
     P.R = rows_per_block(P.L, P.nrows);
     P.nblk = (P.nrows + P.R - 1) / P.R;
+    h->rows_rule = P.R;
     if (!x_fits(P)) return bail(MMCQ_ERR_UNSUPPORTED);
     P.fd_nx = make_fastdiv((unsigned)P.nx);
     P.fd_ny = make_fastdiv((unsigned)P.ny);
@@ -459,10 +467,11 @@ int mmcq_create(mmcq_t** out, const mmcq_grid* g, double Ms, double Aex, double 
     for (int k = 0; k < MAX_MODES; k++) Bf.prof[k] = nullptr;
     Bf.ip = (InstParams*)A(sizeof(InstParams) * P.B);
     Bf.st = (InstState*)A(sizeof(InstState) * P.B);
-    Bf.xpart = (double*)A(sizeof(double) * MAX_MODES * (long long)P.B * P.nblk);
-    Bf.mpart = (double*)A(sizeof(double) * 3LL * P.B * P.nblk);
+    // block partials: room for one row per block (the autotuner may lower P.R)
+    Bf.xpart = (double*)A(sizeof(double) * MAX_MODES * (long long)P.B * P.nrows);
+    Bf.mpart = (double*)A(sizeof(double) * 3LL * P.B * P.nrows);
     Bf.mhist = nullptr;   // allocated by mmcq_set_recording
-    Bf.epart = (float*)A(sizeof(float) * (long long)P.B * P.nblk);
+    Bf.epart = (float*)A(sizeof(float) * (long long)P.B * P.nrows);
     Bf.counter = (unsigned*)A(sizeof(unsigned) * P.B);
     Bf.hcap = 1 << 16;
     Bf.hist = (double*)A(sizeof(double) * (long long)P.B * Bf.hcap);
@@ -975,6 +984,185 @@ int mmcq_spectrum(mmcq_t* h, int inst, int comp, const double* omega, int nw, do
     return MMCQ_OK;
 }
 
+// ---- autotuning of the launch parameters -------------------------------------------
+namespace {
+
+// Choices found per device and shape, reused by later handles of the process.
+std::mutex g_tune_mu;
+std::map<std::string, mmcq_tuning> g_tune_cache;
+
+std::string tune_key(const mmcq_t* h) {
+    const Plan& P = h->P;
+    return std::to_string(h->device) + ":" + std::to_string(P.nx) + "x" + std::to_string(P.ny) + "x" +
+           std::to_string(P.nz) + "b" + std::to_string(P.B) + "t" + std::to_string(P.TX);
+}
+
+void tune_read(const mmcq_t* h, mmcq_tuning* t) {
+    int gmax[4], zc;
+    conv_tunables(h->P, gmax, &zc);
+    t->x_rows = h->P.R;
+    for (int k = 0; k < 4; k++) t->col_groups[k] = gmax[k] ? (h->tune.col_g[k] > 0 ? h->tune.col_g[k] : gmax[k]) : 0;
+    t->z_split = zc ? (h->tune.z_split < 0 ? 1 : h->tune.z_split) : -1;
+    t->x_pipe = h->spec_map.valid ? (h->tune.x_pipe < 0 ? 1 : h->tune.x_pipe) : -1;
+}
+
+// Apply a plan; false (nothing changed) if it is not one of this grid's choices.
+bool tune_apply(mmcq_t* h, const mmcq_tuning* t) {
+    int gmax[4], zc;
+    conv_tunables(h->P, gmax, &zc);
+    if (!t) {
+        h->tune = Tune{{0, 0, 0, 0}, -1, -1};
+        h->P.R = h->rows_rule;
+    } else {
+        if (t->x_rows < 1 || t->x_rows > h->rows_rule) return false;
+        for (int k = 0; k < 4; k++)
+            if (t->col_groups[k] < 0 || (gmax[k] == 0 && t->col_groups[k] != 0) || t->col_groups[k] > gmax[k])
+                return false;
+        if (t->z_split < -1 || t->z_split > 1 || (!zc && t->z_split == 1)) return false;
+        if (t->x_pipe < -1 || t->x_pipe > 1 || (!h->spec_map.valid && t->x_pipe == 1)) return false;
+        for (int k = 0; k < 4; k++) h->tune.col_g[k] = t->col_groups[k];
+        h->tune.z_split = t->z_split;
+        h->tune.x_pipe = t->x_pipe;
+        h->P.R = t->x_rows;
+    }
+    h->P.nblk = (h->P.nrows + h->P.R - 1) / h->P.R;
+    h->tune_epoch++;
+    return true;
+}
+
+}  // namespace
+
+int mmcq_set_tuning(mmcq_t* h, const mmcq_tuning* t) {
+    if (!h) return MMCQ_ERR_ARG;
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (!tune_apply(h, t)) return fail(h, MMCQ_ERR_ARG, "set_tuning: not a plan of this grid");
+    return MMCQ_OK;
+}
+
+int mmcq_get_tuning(mmcq_t* h, mmcq_tuning* out) {
+    if (!h || !out) return MMCQ_ERR_ARG;
+    std::memset(out, 0, sizeof(*out));
+    tune_read(h, out);
+    return MMCQ_OK;
+}
+
+int mmcq_autotune(mmcq_t* h, int reps, mmcq_tuning* out) {
+    if (!h || !out || reps < 1) return MMCQ_ERR_ARG;
+    const std::string key = tune_key(h);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            mmcq_tuning t = it->second;
+            if (!tune_apply(h, &t)) return fail(h, MMCQ_ERR_STATE, "autotune: cached plan does not fit");
+            *out = t;
+            out->candidates = 0;
+            return MMCQ_OK;
+        }
+    }
+    int r = check_flags(h);
+    if (r) return r;
+    const Plan& P = h->P;
+    const int B = P.B;
+    // field evaluations of the whole batch at the current m, written to a
+    // scratch field buffer: the state does not change
+    float4* fout = (float4*)dev_alloc(h, sizeof(float4) * (size_t)B * P.N);
+    if (!fout) return fail(h, MMCQ_ERR_CUDA, "autotune: scratch allocation failed");
+    Buffers Bq = h->Bf;
+    Bq.fout = fout;
+    StageArgs A = step_args(h);
+    A.field_only = 1; A.terms = MMCQ_TERM_ALL; A.inst0 = 0; A.stage = 0; A.record = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int err = MMCQ_OK;
+    auto cleanup = [&]() {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        dev_free_now(h, fout);
+    };
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cleanup();
+        return fail(h, MMCQ_ERR_CUDA, "autotune: event creation failed");
+    }
+    int ncand = 0;
+    auto eval = [&]() -> cudaError_t {
+        cudaError_t e;
+        if ((e = launch_xfwd(h->P, Bq, A, B, h->stream)) != cudaSuccess) return e;
+        if ((e = launch_convolution(h->P, Bq, A, B, h->stream, &h->tune)) != cudaSuccess) return e;
+        return launch_xinv(h->P, h->mat, Bq, A, B, h->stream, &h->spec_map, &h->tune);
+    };
+    // median time of one evaluation over `reps`, after one untimed
+    auto measure = [&](double* ms) -> int {
+        std::vector<float> t(reps);
+        if (eval() != cudaSuccess) return MMCQ_ERR_CUDA;
+        for (int q = 0; q < reps; q++) {
+            if (cudaEventRecord(e0, h->stream) != cudaSuccess || eval() != cudaSuccess ||
+                cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&t[q], e0, e1) != cudaSuccess)
+                return MMCQ_ERR_CUDA;
+        }
+        std::sort(t.begin(), t.end());
+        *ms = t[reps / 2];
+        ncand++;
+        return MMCQ_OK;
+    };
+    mmcq_tuning best{};
+    tune_apply(h, nullptr);
+    tune_read(h, &best);
+    double rule_ms = 0, best_ms = 0;
+    if ((err = measure(&rule_ms))) { cleanup(); return fail(h, err, "autotune: timing failed"); }
+    best_ms = rule_ms;
+    // one knob at a time, the others at their best so far
+    auto trial = [&](const mmcq_tuning& c) -> int {
+        mmcq_tuning t = c;
+        if (!tune_apply(h, &t)) return MMCQ_OK;
+        double ms = 0;
+        int e = measure(&ms);
+        if (e) return e;
+        if (ms < best_ms) { best_ms = ms; best = t; }
+        tune_apply(h, &best);
+        return MMCQ_OK;
+    };
+    for (int R = h->rows_rule / 2; R >= 1 && R >= h->rows_rule / 4 && !err; R /= 2) {
+        mmcq_tuning c = best;
+        c.x_rows = R;
+        err = trial(c);
+    }
+    int gmax[4], zc;
+    conv_tunables(P, gmax, &zc);
+    if (zc && !err) {
+        mmcq_tuning c = best;
+        c.z_split = 0;
+        err = trial(c);
+    }
+    for (int k = 0; k < 4 && !err; k++) {
+        for (int G = 1; G < gmax[k] && !err; G *= 2) {
+            mmcq_tuning c = best;
+            c.col_groups[k] = G;
+            err = trial(c);
+        }
+    }
+    if (h->spec_map.valid && !err) {
+        mmcq_tuning c = best;
+        c.x_pipe = 0;
+        err = trial(c);
+    }
+    cleanup();
+    if (err) {
+        tune_apply(h, nullptr);
+        return fail(h, err, "autotune: timing failed");
+    }
+    tune_apply(h, &best);
+    best.eval_ms = best_ms;
+    best.rule_ms = rule_ms;
+    best.candidates = ncand;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    *out = best;
+    return MMCQ_OK;
+}
+
 // ---- discrete adjoint of the RK4 path ---------------------------------------------
 namespace {
 
@@ -986,8 +1174,8 @@ int adj_field(mmcq_t* h, const Buffers& Bq, int terms) {
     A.record = 0; A.nmodes = 1;
     const int B = h->P.B;
     CK(h, launch_xfwd(h->P, Bq, A, B, h->stream));
-    CK(h, launch_convolution(h->P, Bq, A, B, h->stream));
-    CK(h, launch_xinv(h->P, h->mat, Bq, A, B, h->stream, &h->spec_map));
+    CK(h, launch_convolution(h->P, Bq, A, B, h->stream, &h->tune));
+    CK(h, launch_xinv(h->P, h->mat, Bq, A, B, h->stream, &h->spec_map, &h->tune));
     return MMCQ_OK;
 }
 
@@ -1352,6 +1540,7 @@ struct mmcq_group {
     std::vector<cudaEvent_t> join, in;
     cudaGraphExec_t exec = nullptr;
     std::vector<int> cap_kind, cap_mode, cap_record, cap_nmodes;
+    std::vector<int64_t> cap_epoch;         // tuning epoch of each handle at the capture
     std::vector<double> cap_tol;
     std::vector<int64_t> cap_launches;      // kernel launches per replay, per handle
     int64_t replays = 0;
@@ -1377,7 +1566,7 @@ bool group_stale(const mmcq_group_t* g) {
     for (size_t i = 0; i < g->hs.size(); i++) {
         const mmcq_t* h = g->hs[i];
         if (h->kind != g->cap_kind[i] || h->mode != g->cap_mode[i] || h->tol != g->cap_tol[i] ||
-            h->record != g->cap_record[i] || h->nmodes != g->cap_nmodes[i])
+            h->record != g->cap_record[i] || h->nmodes != g->cap_nmodes[i] || h->tune_epoch != g->cap_epoch[i])
             return true;
     }
     return false;
@@ -1417,6 +1606,7 @@ int group_capture(mmcq_group_t* g) {
         g->cap_tol[i] = g->hs[i]->tol;
         g->cap_record[i] = g->hs[i]->record;
         g->cap_nmodes[i] = g->hs[i]->nmodes;
+        g->cap_epoch[i] = g->hs[i]->tune_epoch;
     }
     if (r != MMCQ_OK) {
         if (graph) cudaGraphDestroy(graph);
@@ -1456,6 +1646,7 @@ int mmcq_group_create(mmcq_group_t** out, mmcq_t* const* handles, int n, int chu
     g->cap_kind.assign(n, -1);
     g->cap_mode.assign(n, -1);
     g->cap_tol.assign(n, -1.0);
+    g->cap_epoch.assign(n, -1);
     g->cap_record.assign(n, -1);
     g->cap_nmodes.assign(n, -1);
     g->cap_launches.assign(n, 0);

@@ -691,7 +691,17 @@ static const int COL_MAX_THREADS = 256;
 
 // One launch of the demag convolution: part 0 = 2-D (fwd y, product, inv y);
 // 3-D: part 1 = forward y, 2 = z forward / product / z inverse, 3 = inverse y.
-cudaError_t launch_conv_part(const Plan& P, const Buffers& Bf, const StageArgs& A, int nb, cudaStream_t s, int part) {
+// Groups per block of a column part as the tuning asks, within the rule's
+// (largest feasible) count; a count of 0 keeps the rule.
+static int tuned_groups(const Tune* T, int part, int rule) {
+    if (!T || T->col_g[part] <= 0) return rule;
+    int G = 1;
+    while (G * 2 <= T->col_g[part] && G * 2 <= rule) G *= 2;
+    return G;
+}
+
+cudaError_t launch_conv_part(const Plan& P, const Buffers& Bf, const StageArgs& A, int nb, cudaStream_t s, int part,
+                             const Tune* T) {
     long long sb, sz, st, sr, tb, tz, tt, tr;
     spec_strides(P, P.ny, sb, sz, st, sr);
     spec_strides(P, P.py, tb, tz, tt, tr);
@@ -702,7 +712,7 @@ cudaError_t launch_conv_part(const Plan& P, const Buffers& Bf, const StageArgs& 
         C.P = P.py; C.n_in = P.ny; C.n_out = P.ny;
         C.fwd = 1; C.mult = 1; C.inv = 1; C.ncomp = 3; C.ky_is_row = 1;
         C.group_tiles = 1; C.nouter = 1;
-        C.G = pick_groups(3 * P.TX, P.py, P.NT, COL_MAX_THREADS, COL_SMEM_CAP);
+        C.G = tuned_groups(T, 0, pick_groups(3 * P.TX, P.py, P.NT, COL_MAX_THREADS, COL_SMEM_CAP));
     } else if (part == 1 || part == 3) {
         bool fwd = part == 1;
         C.in = fwd ? Bf.spec : Bf.spec2;
@@ -715,12 +725,12 @@ cudaError_t launch_conv_part(const Plan& P, const Buffers& Bf, const StageArgs& 
                                   : fft_fits(3 * P.TX, P.py) && (size_t)P.py * 3 * P.TX * 8 <= COL_SMEM_CAP;
         C.ncomp = three ? 3 : 1;
         C.group_tiles = 1; C.nouter = P.nz;
-        C.G = pick_groups(C.ncomp * P.TX, P.py, P.NT, COL_MAX_THREADS, COL_SMEM_CAP);
+        C.G = tuned_groups(T, part, pick_groups(C.ncomp * P.TX, P.py, P.NT, COL_MAX_THREADS, COL_SMEM_CAP));
         if (P.py == 2048 && 2 * P.ny <= P.py) {
             // two register transforms of 1024 per column (split of the padded length)
             const bool three = reg_threads(1024, 3 * P.TX) <= 512 && (size_t)1024 * 3 * P.TX * 8 <= 96 * 1024;
             C.ncomp = three ? 3 : 1;
-            C.G = pick_groups(C.ncomp * P.TX, 1024, P.NT, 512, 96 * 1024);
+            C.G = tuned_groups(T, part, pick_groups(C.ncomp * P.TX, 1024, P.NT, 512, 96 * 1024));
             return launch_split<1024>(P, Bf, A, C, nb, s);
         }
     } else {
@@ -728,15 +738,15 @@ cudaError_t launch_conv_part(const Plan& P, const Buffers& Bf, const StageArgs& 
         C.in_b = C.out_b = tb; C.in_o = C.out_o = tr; C.in_t = C.out_t = tt; C.in_r = C.out_r = tz;
         C.P = P.pz; C.n_in = P.nz; C.n_out = P.nz; C.fwd = 1; C.mult = 1; C.inv = 1; C.ncomp = 3; C.ky_is_row = 0;
         C.group_tiles = 0; C.nouter = P.py;
-        C.G = pick_groups(3 * P.TX, P.pz, P.py, COL_MAX_THREADS, COL_SMEM_CAP);
+        C.G = tuned_groups(T, 2, pick_groups(3 * P.TX, P.pz, P.py, COL_MAX_THREADS, COL_SMEM_CAP));
         if (zconv_applies(P)) {
-            C.G = zconv_groups(P);
-            if (P.pz == 32) {
+            C.G = tuned_groups(T, 2, zconv_groups(P));
+            if (P.pz == 32 && (!T || T->z_split != 0)) {
                 // k_zconv2's halves are kept whole warps (W = 96 for every grid
                 // with 32 or more kx x ky columns per block), so that no warp
                 // diverges on the half; its barriers sit outside the per-half
                 // branches either way
-                const int G2 = zsplit_groups(P);
+                const int G2 = tuned_groups(T, 2, zsplit_groups(P));
                 if ((3 * G2 * P.TX) % 32 == 0) {
                     C.G = G2;
                     return launch_z2<32>(P, Bf, A, C, nb, s);
@@ -755,12 +765,40 @@ cudaError_t launch_conv_part(const Plan& P, const Buffers& Bf, const StageArgs& 
     return launch_col(P, Bf, A, C, nb, s);
 }
 
-cudaError_t launch_convolution(const Plan& P, const Buffers& Bf, const StageArgs& A, int nb, cudaStream_t s) {
-    if (P.nz == 1) return launch_conv_part(P, Bf, A, nb, s, 0);
+cudaError_t launch_convolution(const Plan& P, const Buffers& Bf, const StageArgs& A, int nb, cudaStream_t s,
+                               const Tune* T) {
+    if (P.nz == 1) return launch_conv_part(P, Bf, A, nb, s, 0, T);
     cudaError_t e;
     for (int part = 1; part <= 3; part++)
-        if ((e = launch_conv_part(P, Bf, A, nb, s, part)) != cudaSuccess) return e;
+        if ((e = launch_conv_part(P, Bf, A, nb, s, part, T)) != cudaSuccess) return e;
     return cudaSuccess;
+}
+
+// The tunable choices of a plan's column passes: the rule's (largest) group
+// count of each part present (0 where the part is not launched), and whether
+// the split z kernel is an alternative.
+void conv_tunables(const Plan& P, int gmax[4], int* z_split_choice) {
+    for (int k = 0; k < 4; k++) gmax[k] = 0;
+    *z_split_choice = 0;
+    if (P.nz == 1) {
+        gmax[0] = pick_groups(3 * P.TX, P.py, P.NT, COL_MAX_THREADS, COL_SMEM_CAP);
+        return;
+    }
+    for (int part = 1; part <= 3; part += 2) {
+        bool three = P.py <= 1024 ? reg_threads(P.py, 3 * P.TX) <= 512 && (size_t)P.py * 3 * P.TX * 8 <= COL_SMEM_CAP
+                                  : fft_fits(3 * P.TX, P.py) && (size_t)P.py * 3 * P.TX * 8 <= COL_SMEM_CAP;
+        int nc = three ? 3 : 1;
+        gmax[part] = pick_groups(nc * P.TX, P.py, P.NT, COL_MAX_THREADS, COL_SMEM_CAP);
+        if (P.py == 2048 && 2 * P.ny <= P.py) {
+            const bool t3 = reg_threads(1024, 3 * P.TX) <= 512 && (size_t)1024 * 3 * P.TX * 8 <= 96 * 1024;
+            gmax[part] = pick_groups((t3 ? 3 : 1) * P.TX, 1024, P.NT, 512, 96 * 1024);
+        }
+    }
+    gmax[2] = pick_groups(3 * P.TX, P.pz, P.py, COL_MAX_THREADS, COL_SMEM_CAP);
+    if (zconv_applies(P)) {
+        gmax[2] = zconv_groups(P);
+        if (P.pz == 32 && (3 * zsplit_groups(P) * P.TX) % 32 == 0) *z_split_choice = 1;
+    }
 }
 
 int convolution_launches(const Plan& P) { return P.nz == 1 ? 1 : 3; }

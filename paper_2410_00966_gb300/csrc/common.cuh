@@ -106,6 +106,14 @@ struct InstState {
     int poison;             // DP45: a stage of the current attempt was not finite
 };
 
+// Launch parameters the autotuner may override (0 / -1: the fixed rules).
+// None of them changes a data layout, so every choice computes the same thing.
+struct Tune {
+    int col_g[4];   // groups per block of each column part (2-D, y forward, z, y inverse); 0 = rule
+    int z_split;    // pz = 32: 1 the split z kernel, 0 one thread per column; -1 = rule
+    int x_pipe;     // L = 1024: 1 the pipelined x inverse, 0 the per-row kernel; -1 = rule
+};
+
 // Device buffers of one handle.
 struct Buffers {
     float4* m[2];     // [B][N] (x, y, z, Ms); m[mcur] is the accepted state

@@ -404,13 +404,13 @@ static void launch_xpipe(const Plan& P, const Material& mat, const Buffers& Bf, 
 }
 
 cudaError_t launch_xinv(const Plan& P, const Material& mat, const Buffers& Bf, const StageArgs& A, int nb,
-                        cudaStream_t s, const SpecMap* map) {
+                        cudaStream_t s, const SpecMap* map, const Tune* T) {
     dim3 grid(P.nblk, nb);
     const int th = xthreads(P);
     const size_t sm = xinv_smem(P);
     const bool rec = A.record > 0 && !A.field_only && A.stage == (A.kind == KIND_RK4 ? 3 : 6);
     const bool multi = A.nmodes > 1;
-    if (xpipe_applies(P, Bf, map)) {
+    if (xpipe_applies(P, Bf, map) && (!T || T->x_pipe != 0)) {
         if (multi) {
             if (rec) launch_xpipe<true, MAX_MODES>(P, mat, Bf, A, nb, map, s);
             else launch_xpipe<false, MAX_MODES>(P, mat, Bf, A, nb, map, s);
