@@ -376,14 +376,16 @@ const char* mmcq_group_last_error(const mmcq_group_t* g);
  *                  thread per column; -1: no choice for this grid;
  *   x_pipe         rows of L = 1024 points: 1 the persistent x inverse fed by
  *                  bulk tensor copies, 0 one row per block; -1: no choice.
- * mmcq_autotune times one field evaluation of the whole batch at the current
- *   state (the state does not change) under the fixed rules and under each
- *   candidate, one knob at a time with the others at their best so far, takes
- *   the median of `reps` timings per candidate, and keeps the fastest plan for
- *   the later steps of the handle.  The choice is also cached for the process
- *   (per device, grid and batch size): a later handle of the same shape gets it
- *   without timing (out->candidates = 0).  Allocates B x N x 16 bytes of scratch
- *   for the duration of the call.  Synchronises.
+ * mmcq_autotune times one middle Runge-Kutta stage of the whole batch (stage
+ *   input, transforms, field, torque, coupling sums, per-instance finish) at
+ *   the current state under the fixed rules and under each candidate, one knob
+ *   at a time with the others at their best so far, takes the median of `reps`
+ *   timings per candidate, and keeps the fastest plan for the later steps of
+ *   the handle.  Only that stage's scratch buffers are written and the
+ *   instance states are restored, so the integration is unchanged.  The choice
+ *   is also cached for the process (per device, grid and batch size): a later
+ *   handle of the same shape gets it without timing (out->candidates = 0).
+ *   Synchronises.
  * mmcq_set_tuning applies a plan (MMCQ_ERR_ARG, nothing changed, if it is not
  *   one of this grid's choices); NULL restores the fixed rules.  A group
  *   holding the handle captures its graph again at its next step. 
@@ -393,7 +395,7 @@ typedef struct {
     int col_groups[4];
     int z_split;
     int x_pipe;
-    double eval_ms;        /* median time of one field evaluation of the batch with this plan */
+    double eval_ms;        /* median time of one stage of the batch with this plan */
     double rule_ms;        /* the same with the fixed rules */
     int candidates;        /* plans timed (0: taken from the cache) */
 } mmcq_tuning;

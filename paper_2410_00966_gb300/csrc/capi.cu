@@ -1064,20 +1064,25 @@ int mmcq_autotune(mmcq_t* h, int reps, mmcq_tuning* out) {
     if (r) return r;
     const Plan& P = h->P;
     const int B = P.B;
-    // field evaluations of the whole batch at the current m, written to a
-    // scratch field buffer: the state does not change
-    float4* fout = (float4*)dev_alloc(h, sizeof(float4) * (size_t)B * P.N);
-    if (!fout) return fail(h, MMCQ_ERR_CUDA, "autotune: scratch allocation failed");
-    Buffers Bq = h->Bf;
-    Bq.fout = fout;
+    // timed: one middle Runge-Kutta stage of the whole batch (stage input,
+    // transforms, field, torque, coupling sums and the per-instance finish),
+    // which writes only that stage's scratch buffers and the instance states;
+    // the states are put back afterwards, so the integration is unchanged
+    std::vector<InstState> saved(B);
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpy(saved.data(), h->Bf.st, sizeof(InstState) * B, cudaMemcpyDeviceToHost));
     StageArgs A = step_args(h);
-    A.field_only = 1; A.terms = MMCQ_TERM_ALL; A.inst0 = 0; A.stage = 0; A.record = 0;
+    A.stage = h->kind == KIND_RK4 ? 1 : 3;
+    A.record = 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     int err = MMCQ_OK;
-    auto cleanup = [&]() {
+    auto cleanup = [&]() -> int {
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
-        dev_free_now(h, fout);
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess ||
+            cudaMemcpy(h->Bf.st, saved.data(), sizeof(InstState) * B, cudaMemcpyHostToDevice) != cudaSuccess)
+            return MMCQ_ERR_CUDA;
+        return MMCQ_OK;
     };
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         cleanup();
@@ -1086,9 +1091,9 @@ int mmcq_autotune(mmcq_t* h, int reps, mmcq_tuning* out) {
     int ncand = 0;
     auto eval = [&]() -> cudaError_t {
         cudaError_t e;
-        if ((e = launch_xfwd(h->P, Bq, A, B, h->stream)) != cudaSuccess) return e;
-        if ((e = launch_convolution(h->P, Bq, A, B, h->stream, &h->tune)) != cudaSuccess) return e;
-        return launch_xinv(h->P, h->mat, Bq, A, B, h->stream, &h->spec_map, &h->tune);
+        if ((e = launch_xfwd(h->P, h->Bf, A, B, h->stream)) != cudaSuccess) return e;
+        if ((e = launch_convolution(h->P, h->Bf, A, B, h->stream, &h->tune)) != cudaSuccess) return e;
+        return launch_xinv(h->P, h->mat, h->Bf, A, B, h->stream, &h->spec_map, &h->tune);
     };
     // median time of one evaluation over `reps`, after one untimed
     auto measure = [&](double* ms) -> int {
@@ -1109,7 +1114,10 @@ int mmcq_autotune(mmcq_t* h, int reps, mmcq_tuning* out) {
     tune_apply(h, nullptr);
     tune_read(h, &best);
     double rule_ms = 0, best_ms = 0;
-    if ((err = measure(&rule_ms))) { cleanup(); return fail(h, err, "autotune: timing failed"); }
+    if ((err = measure(&rule_ms))) {
+        cleanup();
+        return fail(h, err, "autotune: timing failed");
+    }
     best_ms = rule_ms;
     // one knob at a time, the others at their best so far
     auto trial = [&](const mmcq_tuning& c) -> int {
@@ -1146,7 +1154,7 @@ int mmcq_autotune(mmcq_t* h, int reps, mmcq_tuning* out) {
         c.x_pipe = 0;
         err = trial(c);
     }
-    cleanup();
+    if (cleanup() != MMCQ_OK) err = MMCQ_ERR_CUDA;
     if (err) {
         tune_apply(h, nullptr);
         return fail(h, err, "autotune: timing failed");

@@ -447,11 +447,15 @@ __global__ void __launch_bounds__(512, (FIXED && PH == 1024) ? 2 : 1) k_col_spli
     for (int J = 0; J < 2; J++) {
         float2 v[NPT];
         if (C.fwd) {
+            // odd half: x_r W_P^r with r = j + N1 n2; for the three-factor
+            // shape W_P^r = W_P^j W_32^{n2} (N1 = P / 32), one table value
+            // per thread and constant-bank factors
+            const float2 wj = stw[j];
 #pragma unroll
             for (int n2 = 0; n2 < NPT; n2++) {
                 const int r = j + N1 * n2;
                 float2 x = (valid && r < C.n_in) ? in[r * in_r] : make_float2(0.f, 0.f);
-                if (J == 1) x = cmul(x, stw[r]);
+                if (J == 1) x = F3 ? cmul(x, n2 == 0 ? wj : cmul(wj, c_tw32[n2])) : cmul(x, stw[r]);
                 v[n2] = x;
             }
             fft(v, false);

@@ -183,6 +183,26 @@ __device__ __forceinline__ int col3_out_row(int j, int i) {
 template <int N1, int PADS>
 __device__ __forceinline__ int col3_swz(int r) { return r + PADS * (r / N1); }
 
+// v[k] *= w^k for k = 1..15, w = table[b]: six table values (w^1..3 and
+// w^4, w^8, w^12) and one product for each of the other nine powers, so that
+// every factor carries at most one rounding beyond the table's.
+template <bool INV, bool TW_SHARED>
+__device__ __forceinline__ void twiddle15(float2* v, const float2* __restrict__ tw, int b) {
+    auto at = [&](int k) {
+        float2 w = TW_SHARED ? tw[k] : __ldg(tw + k);
+        if (INV) w.y = -w.y;
+        return w;
+    };
+    const float2 lo[4] = {make_float2(1.f, 0.f), at(b), at(2 * b), at(3 * b)};
+    const float2 hi[4] = {make_float2(1.f, 0.f), at(4 * b), at(8 * b), at(12 * b)};
+#pragma unroll
+    for (int k = 1; k < 16; k++) {
+        const int a = k & 3, c = k >> 2;
+        const float2 w = a == 0 ? hi[c] : (c == 0 ? lo[a] : cmul(lo[a], hi[c]));
+        v[k] = cmul(v[k], w);
+    }
+}
+
 template <int P, bool INV, bool TW_SHARED, int PADS, int LS>
 __device__ __forceinline__ void col_fft3(float2* v, float2* buf, int ld, int col, int j, const float2* __restrict__ tw,
                                          int twn) {
@@ -195,8 +215,7 @@ __device__ __forceinline__ void col_fft3(float2* v, float2* buf, int ld, int col
     // 1. 16 points at stride N1, twiddle W_P^{j k2}, transpose
     fft_reg<16, INV>(v);
     const int step = twn / P;
-#pragma unroll
-    for (int k2 = 1; k2 < 16; k2++) v[k2] = cmul(v[k2], tw_at(j * k2 * step));
+    twiddle15<INV, TW_SHARED>(v, tw, j * step);
     __syncthreads();
 #pragma unroll
     for (int k2 = 0; k2 < 16; k2++) buf[col3_swz<N1, PADS>(k2 * N1 + j) * ld + col] = v[k2];
@@ -207,8 +226,7 @@ __device__ __forceinline__ void col_fft3(float2* v, float2* buf, int ld, int col
     for (int n = 0; n < 16; n++) v[n] = buf[col3_swz<N1, PADS>(a * N1 + q + N3 * n) * ld + col];
     fft_reg<16, INV>(v);
     const int step2 = twn / N1;
-#pragma unroll
-    for (int k = 1; k < 16; k++) v[k] = cmul(v[k], tw_at(q * k * step2));
+    twiddle15<INV, TW_SHARED>(v, tw, q * step2);
     // 3. N3 points across the lanes of the group: at each level the lower lane
     // of a pair keeps x_lo + x_hi, the upper lane (x_lo - x_hi) W_len^{p - half}
 #pragma unroll

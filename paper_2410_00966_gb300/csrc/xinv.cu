@@ -257,6 +257,7 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
 constexpr int XPIPE_BUF = (1024 + 16 * XPASS_F3_PADS) * 3;   // float2 per buffer (>= 129 * 24)
 constexpr int XPIPE_BLOCKS = 4;                              // resident blocks per SM
 constexpr unsigned long long XPIPE_WAIT_NS = 1000000000ull;
+static int g_sms = 0;                                        // SMs of the device (set by xinv_init)
 
 __device__ __forceinline__ int xpipe_land(int k, int c) { return 24 * (k >> 3) + 8 * c + (k & 7); }
 
@@ -388,8 +389,6 @@ __global__ void __launch_bounds__(XPASS_THREADS, XPIPE_BLOCKS) k_xinv_pipe(Plan 
 static bool xpipe_applies(const Plan& P, const Buffers& Bf, const SpecMap* map) {
     return map && map->valid && map->base == Bf.spec && P.L == 1024 && P.TX == 8 && P.R == 1 && P.NT <= 256;
 }
-
-static int g_sms = 0;
 
 template <bool REC, int NM>
 static void launch_xpipe(const Plan& P, const Material& mat, const Buffers& Bf, const StageArgs& A, int nb,

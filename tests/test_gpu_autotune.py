@@ -118,8 +118,14 @@ def test_tuned_plan_steps_the_oracle_trajectory_and_is_cached():
     sim.step(8, 1e-13)
     o.replay(sim.dt_history())
     assert np.abs(sim.get_m().astype(np.float64) - o.get_m()).max() <= 1e-5
-    # the tuner's choice, then a second handle of the same shape takes it from the cache
+    # the tuner times real stages but puts the instance states back: stepping
+    # on from here continues the same trajectory
     first = sim.autotune(reps=3)
+    done = len(sim.dt_history())
+    sim.step(4, 0.0)
+    o.replay(sim.dt_history()[done:])
+    assert np.abs(sim.get_m().astype(np.float64) - o.get_m()).max() <= 1e-5
+    # a second handle of the same shape takes the tuner's choice from the cache
     other = pkg.Sim(nx, ny, nz, d, d, d, 1.4e5, 3.65e-12, 1e-3, Ku=1e3)
     again = other.autotune(reps=3)
     assert again["candidates"] == 0
