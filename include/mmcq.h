@@ -372,16 +372,19 @@ const char* mmcq_group_last_error(const mmcq_group_t* g);
  *                  column passes: k = 0 the 2-D convolution, 1 the forward y,
  *                  2 the z pass, 3 the inverse y (0: not launched for this
  *                  grid); a power of two up to the rule's (largest) count;
- *   z_split        pz = 32: 1 the split z kernel (two threads per column), 0 one
- *                  thread per column; -1: no choice for this grid;
+ *   z_split        pz = 16 or 32: 1 the split z kernel (two threads per
+ *                  column), 0 one thread per column (the rule: split for 32,
+ *                  one thread for 16); -1: no choice for this grid;
  *   x_pipe         rows of L = 1024 points: 1 the persistent x inverse fed by
  *                  bulk tensor copies, 0 one row per block; -1: no choice.
  * mmcq_autotune times one middle Runge-Kutta stage of the whole batch (stage
  *   input, transforms, field, torque, coupling sums, per-instance finish) at
  *   the current state under the fixed rules and under each candidate, one knob
- *   at a time with the others at their best so far, takes the median of `reps`
- *   timings per candidate, and keeps the fastest plan for the later steps of
- *   the handle.  Only that stage's scratch buffers are written and the
+ *   at a time with the others at their best so far, with events around every
+ *   pass: a candidate is kept when the passes its knob changes (both x passes
+ *   for x_rows, the column part for col_groups, the z pass for z_split, the x
+ *   inverse for x_pipe) take less time, by the median of `reps` stages.  The
+ *   fastest plan stays in use for the later steps of the handle.  Only that stage's scratch buffers are written and the
  *   instance states are restored, so the integration is unchanged.  The choice
  *   is also cached for the process (per device, grid and batch size): a later
  *   handle of the same shape gets it without timing (out->candidates = 0).
@@ -395,7 +398,7 @@ typedef struct {
     int col_groups[4];
     int z_split;
     int x_pipe;
-    double eval_ms;        /* median time of one stage of the batch with this plan */
+    double eval_ms;        /* one stage of the batch with this plan: sum of the passes' median times */
     double rule_ms;        /* the same with the fixed rules */
     int candidates;        /* plans timed (0: taken from the cache) */
 } mmcq_tuning;

@@ -27,7 +27,7 @@ cudaError_t launch_xinv(const Plan&, const Material&, const Buffers&, const Stag
                         const SpecMap*, const Tune*);
 cudaError_t launch_convolution(const Plan&, const Buffers&, const StageArgs&, int, cudaStream_t, const Tune*);
 cudaError_t launch_conv_part(const Plan&, const Buffers&, const StageArgs&, int, cudaStream_t, int, const Tune*);
-void conv_tunables(const Plan&, int*, int*);
+void conv_tunables(const Plan&, int*, int*, int*);
 int convolution_launches(const Plan&);
 bool col_fits(const Plan&);
 bool fft_fits(int, int);
@@ -998,18 +998,18 @@ std::string tune_key(const mmcq_t* h) {
 }
 
 void tune_read(const mmcq_t* h, mmcq_tuning* t) {
-    int gmax[4], zc;
-    conv_tunables(h->P, gmax, &zc);
+    int gmax[4], zc, zr;
+    conv_tunables(h->P, gmax, &zc, &zr);
     t->x_rows = h->P.R;
     for (int k = 0; k < 4; k++) t->col_groups[k] = gmax[k] ? (h->tune.col_g[k] > 0 ? h->tune.col_g[k] : gmax[k]) : 0;
-    t->z_split = zc ? (h->tune.z_split < 0 ? 1 : h->tune.z_split) : -1;
+    t->z_split = zc ? (h->tune.z_split < 0 ? zr : h->tune.z_split) : -1;
     t->x_pipe = h->spec_map.valid ? (h->tune.x_pipe < 0 ? 1 : h->tune.x_pipe) : -1;
 }
 
 // Apply a plan; false (nothing changed) if it is not one of this grid's choices.
 bool tune_apply(mmcq_t* h, const mmcq_tuning* t) {
-    int gmax[4], zc;
-    conv_tunables(h->P, gmax, &zc);
+    int gmax[4], zc, zr;
+    conv_tunables(h->P, gmax, &zc, &zr);
     if (!t) {
         h->tune = Tune{{0, 0, 0, 0}, -1, -1};
         h->P.R = h->rows_rule;
@@ -1074,86 +1074,115 @@ int mmcq_autotune(mmcq_t* h, int reps, mmcq_tuning* out) {
     StageArgs A = step_args(h);
     A.stage = h->kind == KIND_RK4 ? 1 : 3;
     A.record = 0;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    // passes of one stage: 0 = x forward, 1..4 = column parts 0..3, 5 = x inverse;
+    // events bracket each pass so that a knob is judged on the passes it changes
+    const int parts0 = P.nz == 1 ? 0 : 1, parts1 = P.nz == 1 ? 0 : 3;
+    std::vector<cudaEvent_t> ev;
     int err = MMCQ_OK;
     auto cleanup = [&]() -> int {
-        if (e0) cudaEventDestroy(e0);
-        if (e1) cudaEventDestroy(e1);
+        for (auto e : ev) cudaEventDestroy(e);
         if (cudaStreamSynchronize(h->stream) != cudaSuccess ||
             cudaMemcpy(h->Bf.st, saved.data(), sizeof(InstState) * B, cudaMemcpyHostToDevice) != cudaSuccess)
             return MMCQ_ERR_CUDA;
         return MMCQ_OK;
     };
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
-        cleanup();
-        return fail(h, MMCQ_ERR_CUDA, "autotune: event creation failed");
+    const int nev = 2 + (parts1 - parts0 + 1) + 1;    // start, after x forward, after each part, after x inverse
+    for (int q = 0; q < nev; q++) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cleanup();
+            return fail(h, MMCQ_ERR_CUDA, "autotune: event creation failed");
+        }
+        ev.push_back(e);
     }
     int ncand = 0;
-    auto eval = [&]() -> cudaError_t {
+    auto eval = [&](bool timed) -> cudaError_t {
         cudaError_t e;
+        int q = 0;
+        if (timed && (e = cudaEventRecord(ev[q++], h->stream)) != cudaSuccess) return e;
         if ((e = launch_xfwd(h->P, h->Bf, A, B, h->stream)) != cudaSuccess) return e;
-        if ((e = launch_convolution(h->P, h->Bf, A, B, h->stream, &h->tune)) != cudaSuccess) return e;
-        return launch_xinv(h->P, h->mat, h->Bf, A, B, h->stream, &h->spec_map, &h->tune);
-    };
-    // median time of one evaluation over `reps`, after one untimed
-    auto measure = [&](double* ms) -> int {
-        std::vector<float> t(reps);
-        if (eval() != cudaSuccess) return MMCQ_ERR_CUDA;
-        for (int q = 0; q < reps; q++) {
-            if (cudaEventRecord(e0, h->stream) != cudaSuccess || eval() != cudaSuccess ||
-                cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                cudaEventElapsedTime(&t[q], e0, e1) != cudaSuccess)
-                return MMCQ_ERR_CUDA;
+        if (timed && (e = cudaEventRecord(ev[q++], h->stream)) != cudaSuccess) return e;
+        for (int part = parts0; part <= parts1; part++) {
+            if ((e = launch_conv_part(h->P, h->Bf, A, B, h->stream, part, &h->tune)) != cudaSuccess) return e;
+            if (timed && (e = cudaEventRecord(ev[q++], h->stream)) != cudaSuccess) return e;
         }
-        std::sort(t.begin(), t.end());
-        *ms = t[reps / 2];
+        if ((e = launch_xinv(h->P, h->mat, h->Bf, A, B, h->stream, &h->spec_map, &h->tune)) != cudaSuccess) return e;
+        if (timed && (e = cudaEventRecord(ev[q++], h->stream)) != cudaSuccess) return e;
+        return cudaSuccess;
+    };
+    // median time per pass over `reps` stages, after one untimed; pass k is
+    // slot 0 (x forward), 1 + part, or 5 (x inverse)
+    auto measure = [&](double (&ms)[6]) -> int {
+        std::vector<std::vector<float>> t(6, std::vector<float>(reps, 0.f));
+        if (eval(false) != cudaSuccess) return MMCQ_ERR_CUDA;
+        for (int q = 0; q < reps; q++) {
+            if (eval(true) != cudaSuccess || cudaEventSynchronize(ev[nev - 1]) != cudaSuccess) return MMCQ_ERR_CUDA;
+            std::vector<int> slot;
+            slot.push_back(0);
+            for (int part = parts0; part <= parts1; part++) slot.push_back(1 + part);
+            slot.push_back(5);
+            for (size_t k = 0; k < slot.size(); k++)
+                if (cudaEventElapsedTime(&t[slot[k]][q], ev[k], ev[k + 1]) != cudaSuccess) return MMCQ_ERR_CUDA;
+        }
+        for (int k = 0; k < 6; k++) {
+            std::sort(t[k].begin(), t[k].end());
+            ms[k] = t[k][reps / 2];
+        }
         ncand++;
         return MMCQ_OK;
     };
+    auto total = [](const double (&ms)[6]) { return ms[0] + ms[1] + ms[2] + ms[3] + ms[4] + ms[5]; };
     mmcq_tuning best{};
     tune_apply(h, nullptr);
     tune_read(h, &best);
-    double rule_ms = 0, best_ms = 0;
-    if ((err = measure(&rule_ms))) {
+    double rule[6], cur[6];
+    if ((err = measure(rule))) {
         cleanup();
         return fail(h, err, "autotune: timing failed");
     }
-    best_ms = rule_ms;
-    // one knob at a time, the others at their best so far
-    auto trial = [&](const mmcq_tuning& c) -> int {
+    std::copy(rule, rule + 6, cur);
+    // one knob at a time, the others at their best so far, judged on the
+    // passes that knob changes (slots)
+    auto trial = [&](const mmcq_tuning& c, std::initializer_list<int> slots) -> int {
         mmcq_tuning t = c;
         if (!tune_apply(h, &t)) return MMCQ_OK;
-        double ms = 0;
-        int e = measure(&ms);
+        double ms[6];
+        int e = measure(ms);
         if (e) return e;
-        if (ms < best_ms) { best_ms = ms; best = t; }
+        double a = 0, b = 0;
+        for (int k : slots) { a += ms[k]; b += cur[k]; }
+        if (a < b) {
+            best = t;
+            for (int k : slots) cur[k] = ms[k];
+        }
         tune_apply(h, &best);
         return MMCQ_OK;
     };
     for (int R = h->rows_rule / 2; R >= 1 && R >= h->rows_rule / 4 && !err; R /= 2) {
         mmcq_tuning c = best;
         c.x_rows = R;
-        err = trial(c);
+        err = trial(c, {0, 5});
     }
-    int gmax[4], zc;
-    conv_tunables(P, gmax, &zc);
+    int gmax[4], zc, zr;
+    conv_tunables(P, gmax, &zc, &zr);
     if (zc && !err) {
         mmcq_tuning c = best;
-        c.z_split = 0;
-        err = trial(c);
+        c.z_split = 1 - zr;
+        err = trial(c, {3});
     }
     for (int k = 0; k < 4 && !err; k++) {
         for (int G = 1; G < gmax[k] && !err; G *= 2) {
             mmcq_tuning c = best;
             c.col_groups[k] = G;
-            err = trial(c);
+            err = trial(c, {1 + k});
         }
     }
     if (h->spec_map.valid && !err) {
         mmcq_tuning c = best;
         c.x_pipe = 0;
-        err = trial(c);
+        err = trial(c, {5});
     }
+    const double rule_ms = total(rule), best_ms = total(cur);
     if (cleanup() != MMCQ_OK) err = MMCQ_ERR_CUDA;
     if (err) {
         tune_apply(h, nullptr);

@@ -9,8 +9,9 @@
 //   a thread group owns one column and loads its strided rows straight from
 //   global memory (consecutive threads = consecutive columns = contiguous
 //   memory).  WC > 0: the common tile shape fixed at compile time.
-// k_zconv<P> / k_zconv2<P, TXC, GC>: the z pass (pz <= 16 / pz = 32) with the
-//   demag product between the forward and the inverse z transform.
+// k_zconv<P> / k_zconv2<P, TXC, GC>: the z pass (pz <= 32, one thread per
+//   column / pz = 16 or 32, two threads per column) with the demag product
+//   between the forward and the inverse z transform.
 // k_col_split<PH, FIXED>: y passes whose padded length 2 PH exceeds the
 //   register path, as two PH-point register transforms per column.
 // k_col_gen: any power-of-two length, shared-memory Stockham (fft.cuh); the
@@ -745,7 +746,9 @@ cudaError_t launch_conv_part(const Plan& P, const Buffers& Bf, const StageArgs& 
         C.G = tuned_groups(T, 2, pick_groups(3 * P.TX, P.pz, P.py, COL_MAX_THREADS, COL_SMEM_CAP));
         if (zconv_applies(P)) {
             C.G = tuned_groups(T, 2, zconv_groups(P));
-            if (P.pz == 32 && (!T || T->z_split != 0)) {
+            // the split kernel: the rule for pz = 32, a tuning choice for pz = 16
+            const bool split = P.pz == 32 ? (!T || T->z_split != 0) : (P.pz == 16 && T && T->z_split == 1);
+            if (split) {
                 // k_zconv2's halves are kept whole warps (W = 96 for every grid
                 // with 32 or more kx x ky columns per block), so that no warp
                 // diverges on the half; its barriers sit outside the per-half
@@ -753,7 +756,7 @@ cudaError_t launch_conv_part(const Plan& P, const Buffers& Bf, const StageArgs& 
                 const int G2 = tuned_groups(T, 2, zsplit_groups(P));
                 if ((3 * G2 * P.TX) % 32 == 0) {
                     C.G = G2;
-                    return launch_z2<32>(P, Bf, A, C, nb, s);
+                    return P.pz == 32 ? launch_z2<32>(P, Bf, A, C, nb, s) : launch_z2<16>(P, Bf, A, C, nb, s);
                 }
             }
             switch (P.pz) {
@@ -781,9 +784,10 @@ cudaError_t launch_convolution(const Plan& P, const Buffers& Bf, const StageArgs
 // The tunable choices of a plan's column passes: the rule's (largest) group
 // count of each part present (0 where the part is not launched), and whether
 // the split z kernel is an alternative.
-void conv_tunables(const Plan& P, int gmax[4], int* z_split_choice) {
+void conv_tunables(const Plan& P, int gmax[4], int* z_split_choice, int* z_split_rule) {
     for (int k = 0; k < 4; k++) gmax[k] = 0;
     *z_split_choice = 0;
+    *z_split_rule = 0;
     if (P.nz == 1) {
         gmax[0] = pick_groups(3 * P.TX, P.py, P.NT, COL_MAX_THREADS, COL_SMEM_CAP);
         return;
@@ -801,7 +805,10 @@ void conv_tunables(const Plan& P, int gmax[4], int* z_split_choice) {
     gmax[2] = pick_groups(3 * P.TX, P.pz, P.py, COL_MAX_THREADS, COL_SMEM_CAP);
     if (zconv_applies(P)) {
         gmax[2] = zconv_groups(P);
-        if (P.pz == 32 && (3 * zsplit_groups(P) * P.TX) % 32 == 0) *z_split_choice = 1;
+        if ((P.pz == 32 || P.pz == 16) && (3 * zsplit_groups(P) * P.TX) % 32 == 0) {
+            *z_split_choice = 1;
+            *z_split_rule = P.pz == 32 ? 1 : 0;
+        }
     }
 }
 
@@ -847,6 +854,10 @@ cudaError_t col_init() {
         return e;
     if ((e = cudaFuncSetAttribute(k_col_split<1024, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) !=
         cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_zconv2<16, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_zconv2<16, 8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
         return e;
     if ((e = cudaFuncSetAttribute(k_zconv2<32, 0, 0>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
         return e;

@@ -24,6 +24,7 @@ GRIDS = [
     (64, 64, 2, 4e-9),       # 3-D, pz = 4 (batched-map members)
     (128, 128, 2, 4e-9),
     (64, 24, 16, 5e-9),      # pz = 32: split or one-thread z
+    (48, 40, 8, 4e-9),       # pz = 16: one-thread or split z
     (1024, 4, 2, 4e-9),      # rows of L = 1024: pipelined or per-row x inverse
 ]
 
@@ -42,8 +43,8 @@ def _candidates(plan):
             cg[k] = g
             out.append(dict(plan, col_groups=cg))
             g *= 2
-    if plan["z_split"] == 1:
-        out.append(dict(plan, z_split=0))
+    if plan["z_split"] in (0, 1):
+        out.append(dict(plan, z_split=1 - plan["z_split"]))
     if plan["x_pipe"] == 1:
         out.append(dict(plan, x_pipe=0))
     return out
