@@ -434,6 +434,7 @@ int mmcq_create(mmcq_t** out, const mmcq_grid* g, double Ms, double Aex, double 
     if (!x_fits(P)) return bail(MMCQ_ERR_UNSUPPORTED);
     P.fd_nx = make_fastdiv((unsigned)P.nx);
     P.fd_ny = make_fastdiv((unsigned)P.ny);
+    P.fd_nz = make_fastdiv((unsigned)P.nz);
     P.fd_L1 = make_fastdiv((unsigned)(P.L + 1));
     P.fd_half = make_fastdiv((unsigned)(P.L / 2 + 1));
 

@@ -61,7 +61,7 @@ struct Plan {
     int R;            // x rows per block in the x passes
     int nblk;         // x-pass blocks per instance: ceil(nrows / R)
     int lt;           // log2(TX)
-    FastDiv fd_nx, fd_ny, fd_L1, fd_half;   // divisions by nx, ny, L + 1, L / 2 + 1
+    FastDiv fd_nx, fd_ny, fd_nz, fd_L1, fd_half;   // divisions by nx, ny, nz, L + 1, L / 2 + 1
     int twn;          // twiddle table length (power of two >= every FFT length)
 };
 

@@ -21,6 +21,16 @@ namespace mq {
 // demag field of those rows is in xs (x_2n = Re, x_2n+1 = Im of row x / 2,
 // pitch ld, line 3 r + comp): exchange, then CellUpdate (local fields,
 // torque, RK bookkeeping, the cell's share of the coupling sums and error).
+// Row of flat index i when blocks of one row are ordered z fastest: the rows
+// that run at the same time are whole runs of z for consecutive y, so each
+// row's six neighbour rows (y +- 1, z +- 1) are being read by blocks running
+// alongside it and are found in L2 (in y-major order a z neighbour is a whole
+// plane of the grid away and has left L2 by the time it is needed).
+__device__ __forceinline__ int zfast_row(const Plan& P, int i) {
+    const int y = (int)fdiv((unsigned)i, P.fd_nz);
+    return (i - y * P.nz) * P.ny + y;
+}
+
 template <int NM, bool REC>
 __device__ __forceinline__ void xinv_cells(const Plan& P, const Material& mat, const Buffers& Bf,
                                            const CellUpdate<NM>& cu, const float2* xs, int ld, const float4* msrc,
@@ -106,7 +116,7 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
     const int TX = FX ? 8 : P.TX, nx = FX ? L : P.nx, lt = FX ? 3 : P.lt;
     const int NT = FX ? L / 8 + 1 : P.NT;
     const int nthr = FX ? 3 * RF * N1 : (int)blockDim.x;
-    const int row0 = blockIdx.x * Rb;
+    const int row0 = F3 ? zfast_row(P, blockIdx.x) : blockIdx.x * Rb;   // F3: one row per block
     const int nr = FX ? RF : min(P.R, P.nrows - row0);
     const int ld = xpass_ld(Rb);
     const long long cb = (long long)b * P.N;
@@ -245,7 +255,8 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
 // ---------------------------------------------------------------------------
 // The same stage for rows of L = 1024 (8-column tiles, one row per pass),
 // persistent and pipelined: each block takes rows blockIdx.x, + gridDim.x, ...
-// of its instance, and while it transforms and updates one row, the
+// of its instance in z-fastest order (zfast_row), and while it transforms and
+// updates one row, the
 // half-spectrum row after it is already on its way into the other of two
 // shared-memory buffers by one bulk tensor copy (TMA: the 129 tiles x 24
 // values of the row as one box of the 4-D map [plane][tile][y][24]),
@@ -312,7 +323,7 @@ __global__ void __launch_bounds__(XPASS_THREADS, XPIPE_BLOCKS) k_xinv_pipe(Plan 
         s_drive = (float)drive_factor(A, ip, st);
     }
     __syncthreads();
-    if (threadIdx.x == 0 && (int)blockIdx.x < P.nrows) issue(blockIdx.x, 0);
+    if (threadIdx.x == 0 && (int)blockIdx.x < P.nrows) issue(zfast_row(P, blockIdx.x), 0);
 
     CellUpdate<NM> cu;
     cu.init(Bf, A, st, ip, s_gamma, s_drive, cb, (long long)A.inst0 * P.N);
@@ -325,11 +336,12 @@ __global__ void __launch_bounds__(XPASS_THREADS, XPIPE_BLOCKS) k_xinv_pipe(Plan 
     const int line = threadIdx.x / N1, j = threadIdx.x % N1;
     const int twstep = P.twn / P.px;
     int it = 0;
-    for (int row = blockIdx.x; row < P.nrows; row += gridDim.x, it++) {
+    for (int flat = blockIdx.x; flat < P.nrows; flat += gridDim.x, it++) {
         const int q = it & 1;
-        const int nxt = row + gridDim.x;
+        const int row = zfast_row(P, flat);
+        const int nxt = flat + gridDim.x;
         if (threadIdx.x == 0) {
-            if (nxt < P.nrows) issue(nxt, q ^ 1);
+            if (nxt < P.nrows) issue(zfast_row(P, nxt), q ^ 1);
             const int z = (int)fdiv((unsigned)row, P.fd_ny);
             s_yz[0] = make_int2(row - z * P.ny, z);
         }
