@@ -431,14 +431,14 @@ __global__ void __launch_bounds__(512, (FIXED && PH == 1024) ? 2 : 1) k_col_spli
     float2* stw = sm + PH * W;
     auto fft = [&](float2 (&v)[NPT], bool inv) {
         if constexpr (F3) {
-            if (inv) col_fft3<PH, true, true, 0, 8>(v, sm, W, col, j, stw, P);
-            else col_fft3<PH, false, true, 0, 8>(v, sm, W, col, j, stw, P);
+            if (inv) col_fft3<PH, true, true, 0, 8, true>(v, sm, W, col, j, stw, P);
+            else col_fft3<PH, false, true, 0, 8, true>(v, sm, W, col, j, stw, P);
         } else {
             if (inv) col_fft<PH, true, true>(v, sm, W, col, j, stw, P);
             else col_fft<PH, false, true>(v, sm, W, col, j, stw, P);
         }
     };
-    auto out_row = [&](int i) { return F3 ? col3_out_row<PH>(j, i) : col_out_row<PH>(j, i); };
+    auto out_row = [&](int i) { return F3 ? col3t_out_row<PH>(j, i) : col_out_row<PH>(j, i); };
     {
         const int tstep = Pl.twn / P;
         for (int q = threadIdx.x; q < P; q += blockDim.x) stw[q] = __ldg(Bf.tw + q * tstep);

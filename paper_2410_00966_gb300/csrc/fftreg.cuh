@@ -203,7 +203,28 @@ __device__ __forceinline__ void twiddle15(float2* v, const float2* __restrict__ 
     }
 }
 
-template <int P, bool INV, bool TW_SHARED, int PADS, int LS>
+// Variant of step 3 (T2): a second transpose instead of the lane exchange.
+// Thread (a, q) then takes k' = q (16 / N3) + qq, qq < 16 / N3, gathers the N3
+// values of each k' and runs N3-point register DFTs; element i = qq N3 + k''
+// is frequency a + 16 (k' + 16 k'').  The second transpose's rows are
+// swizzled so that the lane groups of a warp hit different banks both when
+// they write (rows a N1 + k' N3 + q) and when they read (rows a N1 + 16 q +
+// ...): with 8-column rows (PADS = 0) the low log2 N3 bits are XORed with the
+// bits above the 16-row group; with three-line rows (PADS > 0) the rows are
+// shifted by PADS per N1 group plus those bits.
+template <int P>
+__device__ __forceinline__ int col3t_out_row(int j, int i) {
+    constexpr int N3 = ColShape3<P>::N3, QK = 16 / N3;
+    const int a = j / N3, q = j % N3;
+    return a + 16 * (q * QK + i / N3 + 16 * (i % N3));
+}
+
+template <int N1, int N3, int PADS>
+__device__ __forceinline__ int col3t_swz(int r) {
+    return PADS == 0 ? (r ^ ((r >> 4) & (N3 - 1))) : r + PADS * (r / N1) + ((r >> 4) & (N3 - 1));
+}
+
+template <int P, bool INV, bool TW_SHARED, int PADS, int LS, bool T2 = false>
 __device__ __forceinline__ void col_fft3(float2* v, float2* buf, int ld, int col, int j, const float2* __restrict__ tw,
                                          int twn) {
     constexpr int N1 = ColShape3<P>::N1, N3 = ColShape3<P>::N3;
@@ -227,6 +248,26 @@ __device__ __forceinline__ void col_fft3(float2* v, float2* buf, int ld, int col
     fft_reg<16, INV>(v);
     const int step2 = twn / N1;
     twiddle15<INV, TW_SHARED>(v, tw, q * step2);
+    if constexpr (T2) {
+        // 3'. transpose and N3-point register DFTs
+        constexpr int QK = 16 / N3;
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; k++) buf[col3t_swz<N1, N3, PADS>(a * N1 + k * N3 + q) * ld + col] = v[k];
+        __syncthreads();
+#pragma unroll
+        for (int qq = 0; qq < QK; qq++) {
+            float2 u[N3];
+            const int kk = q * QK + qq;
+#pragma unroll
+            for (int r = 0; r < N3; r++) u[r] = buf[col3t_swz<N1, N3, PADS>(a * N1 + kk * N3 + r) * ld + col];
+            fft_reg<N3, INV>(u);
+#pragma unroll
+            for (int r = 0; r < N3; r++) v[qq * N3 + r] = u[r];
+        }
+        __syncthreads();   // the buffer may be reused by the caller right after
+        return;
+    }
     // 3. N3 points across the lanes of the group: at each level the lower lane
     // of a pair keeps x_lo + x_hi, the upper lane (x_lo - x_hi) W_len^{p - half}
 #pragma unroll
