@@ -273,6 +273,11 @@ def run_ours(args):
     w = workload_instances(args.workload, rank)
     if args.instances:
         w.instances = w.instances[:args.instances]
+    if args.grid:
+        # the same workload on another grid (profiling a smaller case of the same kernels)
+        import synthetic
+        nx, ny, nz = (int(v) for v in args.grid.lower().split("x"))
+        w.instances = [synthetic.scaled(I, nx, ny, nz) for I in w.instances]
     I0 = w.instances[0]
     B = len(w.instances)
     dp = w.integrator == "dp45"
@@ -290,7 +295,13 @@ def run_ours(args):
         if dp:
             sim.set_horizon(w.horizon)
         info = sim.info()
-        tuning = sim.autotune(reps=7)   # launch parameters of this grid, chosen by timing
+        if args.plan:
+            # a given launch plan (e.g. the one a plain run chose, to profile
+            # the same kernels under ncu, whose timings would mislead the tuner)
+            sim.set_tuning(json.loads(args.plan))
+            tuning = sim.tuning()
+        else:
+            tuning = sim.autotune(reps=7)   # launch parameters of this grid, chosen by timing
         # warm-up; the state of instance 0 after the first two attempts is
         # kept for the parity check against the oracle (after the timing)
         sim.step(1, w.dt)
@@ -629,6 +640,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--instances", type=int, default=0, help="use only the first N instances (profiling)")
+    ap.add_argument("--grid", default="", help="NXxNYxNZ: run the workload on this grid instead (profiling)")
+    ap.add_argument("--plan", default="", help="launch plan as JSON (x_rows, col_groups, z_split, x_pipe) "
+                                               "instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
