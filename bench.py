@@ -542,6 +542,11 @@ def run_batched(args):
     top_name = max(stats, key=lambda k: stats[k]["total_ms"])
     top = stats[top_name]
     achieved = top["bytes"] / (top["total_ms"] / 1e3) / 1e9
+    # every handle's algorithmic bytes of one step (the profiled pass ran
+    # `chunk` steps), over the graph's time per step: the whole map's share
+    # of the peak while its handles run side by side
+    step_bytes = sum(d["bytes"] for d in stats.values()) / chunk
+    step_eff = step_bytes / (ms_graph / steps / 1e3) / 1e9 / peak
     line = {
         "metric": "LLG cell-steps/s, batched anticrossing map (mixed grids, CUDA graph)", "value": value,
         "unit": "cell-steps/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup,
@@ -553,10 +558,12 @@ def run_batched(args):
                    "eager_value": cells * steps / (ms_eager / 1e3),
                    "fixed_rules_value": cells * steps / (ms_rules / 1e3),
                    "tuning": tuning,
+                   "algorithmic_bytes_per_step": step_bytes, "step_model_efficiency": step_eff,
                    "l2": "working set below L2 (small grids; latency and launch bound)"},
         "roofline": {"bound": "hbm", "kernel": top_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
-                     "note": "from an eager profiled pass (per-launch events)"},
+                     "note": "from an eager profiled pass (per-launch events, handles one after another); "
+                             "config.step_model_efficiency is the graph run with the handles side by side"},
         "clocks": clk, "gpu_launches": launches,
     }
     print(json.dumps(line), flush=True)

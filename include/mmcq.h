@@ -376,14 +376,19 @@ const char* mmcq_group_last_error(const mmcq_group_t* g);
  *                  column), 0 one thread per column (the rule: split for 32,
  *                  one thread for 16); -1: no choice for this grid;
  *   x_pipe         rows of L = 1024 points: 1 the persistent x inverse fed by
- *                  bulk tensor copies, 0 one row per block; -1: no choice.
+ *                  bulk tensor copies, 0 one row per block; -1: no choice;
+ *   y_split[k]     y padding 2048 with tiles of 8 columns (k = 0 the forward,
+ *                  1 the inverse y pass): 1 each half of the split transform
+ *                  in a block of its own (the inverse's two blocks a cluster
+ *                  exchanging terms through shared memory), 0 both halves in
+ *                  one block; -1: no choice.
  * mmcq_autotune times one middle Runge-Kutta stage of the whole batch (stage
  *   input, transforms, field, torque, coupling sums, per-instance finish) at
  *   the current state under the fixed rules and under each candidate, one knob
  *   at a time with the others at their best so far, with events around every
  *   pass: a candidate is kept when the passes its knob changes (both x passes
  *   for x_rows, the column part for col_groups, the z pass for z_split, the x
- *   inverse for x_pipe) take less time, by the median of `reps` stages.  The
+ *   inverse for x_pipe, the y pass for y_split) take less time, by the median of `reps` stages.  The
  *   fastest plan stays in use for the later steps of the handle.  Only that stage's scratch buffers are written and the
  *   instance states are restored, so the integration is unchanged.  The choice
  *   is also cached for the process (per device, grid and batch size): a later
@@ -398,6 +403,7 @@ typedef struct {
     int col_groups[4];
     int z_split;
     int x_pipe;
+    int y_split[2];
     double eval_ms;        /* one stage of the batch with this plan: sum of the passes' median times */
     double rule_ms;        /* the same with the fixed rules */
     int candidates;        /* plans timed (0: taken from the cache) */

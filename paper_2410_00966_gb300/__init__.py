@@ -69,8 +69,8 @@ class mmcq_objective(ctypes.Structure):
 
 class mmcq_tuning(ctypes.Structure):
     _fields_ = [("x_rows", ctypes.c_int), ("col_groups", ctypes.c_int * 4), ("z_split", ctypes.c_int),
-                ("x_pipe", ctypes.c_int), ("eval_ms", ctypes.c_double), ("rule_ms", ctypes.c_double),
-                ("candidates", ctypes.c_int)]
+                ("x_pipe", ctypes.c_int), ("y_split", ctypes.c_int * 2), ("eval_ms", ctypes.c_double),
+                ("rule_ms", ctypes.c_double), ("candidates", ctypes.c_int)]
 
 
 class mmcq_kernel_stat(ctypes.Structure):
@@ -350,7 +350,7 @@ class Sim:
     @staticmethod
     def _tuning_dict(t) -> dict:
         return {"x_rows": t.x_rows, "col_groups": list(t.col_groups), "z_split": t.z_split, "x_pipe": t.x_pipe,
-                "eval_ms": t.eval_ms, "rule_ms": t.rule_ms, "candidates": t.candidates}
+                "y_split": list(t.y_split), "eval_ms": t.eval_ms, "rule_ms": t.rule_ms, "candidates": t.candidates}
 
     def autotune(self, reps=5) -> dict:
         """Time the launch-parameter candidates of this grid and keep the fastest (mmcq_autotune)."""
@@ -374,6 +374,9 @@ class Sim:
             t.col_groups[k] = int(plan["col_groups"][k])
         t.z_split = int(plan["z_split"])
         t.x_pipe = int(plan["x_pipe"])
+        ys = plan.get("y_split", [-1, -1])
+        for k in range(2):
+            t.y_split[k] = int(ys[k])
         self._ck(self._lib.mmcq_set_tuning(self._h, ctypes.byref(t)))
 
     def profile_read(self) -> list:

@@ -28,8 +28,8 @@ def nvcc() -> str:
 
 
 def _flags():
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
-                   "-I", CSRC]
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--diag-error", "940",
+                   "-I", os.path.join(ROOT, "include"), "-I", CSRC]
 
 
 def _deps():

@@ -27,7 +27,7 @@ cudaError_t launch_xinv(const Plan&, const Material&, const Buffers&, const Stag
                         const SpecMap*, const Tune*);
 cudaError_t launch_convolution(const Plan&, const Buffers&, const StageArgs&, int, cudaStream_t, const Tune*);
 cudaError_t launch_conv_part(const Plan&, const Buffers&, const StageArgs&, int, cudaStream_t, int, const Tune*);
-void conv_tunables(const Plan&, int*, int*, int*);
+void conv_tunables(const Plan&, int*, int*, int*, int*, int*);
 int convolution_launches(const Plan&);
 bool col_fits(const Plan&);
 bool fft_fits(int, int);
@@ -112,7 +112,7 @@ struct mmcq {
     std::vector<Post> posts;
     int post_head = 0, post_count = 0;
     SpecMap spec_map{};     // TMA map of the x-half-spectrum (pipelined x inverse)
-    Tune tune{{0, 0, 0, 0}, -1, -1};   // launch parameters chosen by mmcq_autotune (default: the fixed rules)
+    Tune tune{{0, 0, 0, 0}, -1, -1, {-1, -1}};   // launch parameters chosen by mmcq_autotune (default: the fixed rules)
     int rows_rule = 1;      // x-pass rows per block of the fixed rule
     int64_t tune_epoch = 0; // bumped when the launch parameters change (groups capture again)
 };
@@ -999,20 +999,21 @@ std::string tune_key(const mmcq_t* h) {
 }
 
 void tune_read(const mmcq_t* h, mmcq_tuning* t) {
-    int gmax[4], zc, zr;
-    conv_tunables(h->P, gmax, &zc, &zr);
+    int gmax[4], zc, zr, yc, yr[2];
+    conv_tunables(h->P, gmax, &zc, &zr, &yc, yr);
     t->x_rows = h->P.R;
     for (int k = 0; k < 4; k++) t->col_groups[k] = gmax[k] ? (h->tune.col_g[k] > 0 ? h->tune.col_g[k] : gmax[k]) : 0;
     t->z_split = zc ? (h->tune.z_split < 0 ? zr : h->tune.z_split) : -1;
     t->x_pipe = h->spec_map.valid ? (h->tune.x_pipe < 0 ? 1 : h->tune.x_pipe) : -1;
+    for (int k = 0; k < 2; k++) t->y_split[k] = yc ? (h->tune.y_split[k] < 0 ? yr[k] : h->tune.y_split[k]) : -1;
 }
 
 // Apply a plan; false (nothing changed) if it is not one of this grid's choices.
 bool tune_apply(mmcq_t* h, const mmcq_tuning* t) {
-    int gmax[4], zc, zr;
-    conv_tunables(h->P, gmax, &zc, &zr);
+    int gmax[4], zc, zr, yc, yr[2];
+    conv_tunables(h->P, gmax, &zc, &zr, &yc, yr);
     if (!t) {
-        h->tune = Tune{{0, 0, 0, 0}, -1, -1};
+        h->tune = Tune{{0, 0, 0, 0}, -1, -1, {-1, -1}};
         h->P.R = h->rows_rule;
     } else {
         if (t->x_rows < 1 || t->x_rows > h->rows_rule) return false;
@@ -1021,7 +1022,10 @@ bool tune_apply(mmcq_t* h, const mmcq_tuning* t) {
                 return false;
         if (t->z_split < -1 || t->z_split > 1 || (!zc && t->z_split == 1)) return false;
         if (t->x_pipe < -1 || t->x_pipe > 1 || (!h->spec_map.valid && t->x_pipe == 1)) return false;
+        for (int k = 0; k < 2; k++)
+            if (t->y_split[k] < -1 || t->y_split[k] > 1 || (!yc && t->y_split[k] == 1)) return false;
         for (int k = 0; k < 4; k++) h->tune.col_g[k] = t->col_groups[k];
+        for (int k = 0; k < 2; k++) h->tune.y_split[k] = t->y_split[k];
         h->tune.z_split = t->z_split;
         h->tune.x_pipe = t->x_pipe;
         h->P.R = t->x_rows;
@@ -1164,12 +1168,17 @@ int mmcq_autotune(mmcq_t* h, int reps, mmcq_tuning* out) {
         c.x_rows = R;
         err = trial(c, {0, 5});
     }
-    int gmax[4], zc, zr;
-    conv_tunables(P, gmax, &zc, &zr);
+    int gmax[4], zc, zr, yc, yr[2];
+    conv_tunables(P, gmax, &zc, &zr, &yc, yr);
     if (zc && !err) {
         mmcq_tuning c = best;
         c.z_split = 1 - zr;
         err = trial(c, {3});
+    }
+    for (int k = 0; k < 2 && yc && !err; k++) {
+        mmcq_tuning c = best;
+        c.y_split[k] = 1 - yr[k];
+        err = trial(c, {k == 0 ? 2 : 4});
     }
     for (int k = 0; k < 4 && !err; k++) {
         for (int G = 1; G < gmax[k] && !err; G *= 2) {

@@ -399,19 +399,29 @@ __global__ void __launch_bounds__(192, 6) k_zconv2(Plan Pl, Buffers Bf, StageArg
 // in both spectra, at compile time.
 // F3 (FIXED with PH = 1024): the three-factor transform, 16 points per
 // thread and 64 threads per column (512 threads for the 8 columns), so that
-// two blocks of 16 warps fit an SM; the last factor runs across the lanes
-// 8 apart (the same rows of the 8 columns are consecutive threads).
-template <int PH, bool FIXED>
+// two blocks of 16 warps fit an SM; the last factor by a second transpose.
+// JS (F3 only): each half J in a block of its own (blockIdx.x = 2 (3 tile +
+// component) + J), twice the blocks with half the work each.  In the forward
+// the two blocks are independent.  The inverse is launched as clusters of the
+// two blocks: each keeps half of the output rows (J = 0 those below PH / 2,
+// J = 1 the others), hands the other half of its terms to the partner through
+// its shared memory, and adds the partner's terms for its own rows, so the
+// even half's rows never go to global memory and back.
+template <int PH, bool FIXED, bool JS = false>
 __global__ void __launch_bounds__(512, (FIXED && PH == 1024) ? 2 : 1) k_col_split(Plan Pl, Buffers Bf, StageArgs A,
                                                                                    ColArgs C) {
     constexpr bool F3 = FIXED && PH == 1024;
+    static_assert(!JS || F3, "one half per block is the three-factor shape only");
     constexpr int NPT = F3 ? 16 : ColShape<PH>::NPT, N1 = F3 ? ColShape3<PH>::N1 : ColShape<PH>::N1;
     constexpr int P = 2 * PH;
     extern __shared__ float2 sm[];
     const int ncomp = FIXED ? 1 : C.ncomp;
     const int b = A.inst0 + blockIdx.z;
-    const int c0 = ncomp == 3 ? 0 : blockIdx.x % 3;
-    const int bx = ncomp == 3 ? blockIdx.x : blockIdx.x / 3;
+    const int Jb = JS ? (int)(blockIdx.x & 1) : 0;            // the block's half (JS)
+    const int bxx = JS ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+    const int c0 = ncomp == 3 ? 0 : bxx % 3;
+    const int bx = ncomp == 3 ? bxx : bxx / 3;
+    // the same for both blocks of a cluster (same instance)
     if (stage_skips(Bf.st[b], A)) return;
     const int TX = FIXED ? 8 : Pl.TX, lt = FIXED ? 3 : Pl.lt;
     const int G = FIXED ? 1 : C.G;
@@ -444,8 +454,50 @@ __global__ void __launch_bounds__(512, (FIXED && PH == 1024) ? 2 : 1) k_col_spli
         for (int q = threadIdx.x; q < P; q += blockDim.x) stw[q] = __ldg(Bf.tw + q * tstep);
     }
     __syncthreads();
+    if constexpr (JS) {
+        if (!C.fwd) {
+            // inverse, one half per block: the block's PH-point inverse, and
+            // (J = 1) the twiddle W_P^{-k}, before the exchange
+            const int J = Jb;
+            float2 v[NPT];
+#pragma unroll
+            for (int n2 = 0; n2 < NPT; n2++) {
+                const int r = 2 * (j + N1 * n2) + J;
+                v[n2] = (valid && r < C.n_in) ? in[r * in_r] : make_float2(0.f, 0.f);
+            }
+            fft(v, true);
+            if (J == 1) {
+#pragma unroll
+                for (int i = 0; i < NPT; i++) v[i] = cmul(v[i], conjf2(stw[out_row(i)]));
+            }
+            // element i is row a + 16 (4 q + i / 4) + (PH / 4) (i % 4): below
+            // PH / 2 exactly when i % 4 < 2.  The 8 elements a block gives
+            // away go to slot 2 (i / 4) + i % 2 of its own buffer [8][threads];
+            // the partner thread of the same index holds the same rows.
+            const int nth = (int)blockDim.x;
+            float2* hand = sm;
+#pragma unroll
+            for (int i = 0; i < NPT; i++) {
+                const bool give = ((i & 3) >= 2) == (J == 0);
+                if (give) hand[(2 * (i >> 2) + (i & 1)) * nth + threadIdx.x] = v[i];
+            }
+            cluster_sync();
+            const unsigned rem = cluster_map(smem_u32(hand), (unsigned)(J ^ 1));
+#pragma unroll
+            for (int i = 0; i < NPT; i++) {
+                const bool give = ((i & 3) >= 2) == (J == 0);
+                if (!give) {
+                    const float2 u = ld_cluster_f2(rem + 8u * (unsigned)((2 * (i >> 2) + (i & 1)) * nth + threadIdx.x));
+                    const int k = out_row(i);
+                    if (valid && k < C.n_out) out[k * out_r] = cadd(v[i], u);
+                }
+            }
+            cluster_sync();   // the partner has read this block's buffer
+            return;
+        }
+    }
 #pragma unroll 1
-    for (int J = 0; J < 2; J++) {
+    for (int J = JS ? Jb : 0; J < (JS ? Jb + 1 : 2); J++) {
         float2 v[NPT];
         if (C.fwd) {
             // odd half: x_r W_P^r with r = j + N1 n2; for the three-factor
@@ -566,13 +618,11 @@ static cudaError_t launch_reg(const Plan& Pl, const Buffers& Bf, const StageArgs
                        C.out_r == 24;
     if constexpr (col_fixed_len(P)) {
         if (fixed) {
-            k_col_reg<P, 24><<<grid, W * N1, (size_t)P * W * sizeof(float2), s>>>(Pl, Bf, A, C);
-            return cudaGetLastError();
+            return launch_chain(k_col_reg<P, 24>, grid, W * N1, (size_t)P * W * sizeof(float2), s, Pl, Bf, A, C);
         }
     }
     (void)fixed;
-    k_col_reg<P, 0><<<grid, W * N1, (size_t)P * W * sizeof(float2), s>>>(Pl, Bf, A, C);
-    return cudaGetLastError();
+    return launch_chain(k_col_reg<P, 0>, grid, W * N1, (size_t)P * W * sizeof(float2), s, Pl, Bf, A, C);
 }
 
 template <int P>
@@ -580,8 +630,7 @@ static cudaError_t launch_z(const Plan& Pl, const Buffers& Bf, const StageArgs& 
                             cudaStream_t s) {
     const int W = C.G * 3 * Pl.TX;
     dim3 grid((Pl.py + C.G - 1) / C.G, Pl.NT, nb);
-    k_zconv<P><<<grid, W, (size_t)P * W * sizeof(float2), s>>>(Pl, Bf, A, C);
-    return cudaGetLastError();
+    return launch_chain(k_zconv<P>, grid, W, (size_t)P * W * sizeof(float2), s, Pl, Bf, A, C);
 }
 
 // The fixed-shape z pass: tiles of 8 kx columns, 4 ky per block, all pz / 2 rows data.
@@ -595,26 +644,38 @@ static cudaError_t launch_z2(const Plan& Pl, const Buffers& Bf, const StageArgs&
                              cudaStream_t s) {
     const int W = C.G * 3 * Pl.TX;
     dim3 grid((Pl.py + C.G - 1) / C.G, Pl.NT, nb);
-    if (z2_fixed(Pl, C, P)) k_zconv2<P, 8, 4><<<grid, 2 * W, (size_t)P * W * sizeof(float2), s>>>(Pl, Bf, A, C);
-    else k_zconv2<P, 0, 0><<<grid, 2 * W, (size_t)P * W * sizeof(float2), s>>>(Pl, Bf, A, C);
-    return cudaGetLastError();
+    if (z2_fixed(Pl, C, P))
+        return launch_chain(k_zconv2<P, 8, 4>, grid, 2 * W, (size_t)P * W * sizeof(float2), s, Pl, Bf, A, C);
+    return launch_chain(k_zconv2<P, 0, 0>, grid, 2 * W, (size_t)P * W * sizeof(float2), s, Pl, Bf, A, C);
+}
+
+// Whether a y pass of this plan runs the fixed three-factor split kernel
+// (k_col_split<1024, true>), the one with the choice of a half per block.
+static bool split_fixed(const Plan& Pl, const ColArgs& C) {
+    return Pl.TX == 8 && C.ncomp == 1 && C.G == 1 && C.in_r == 24 && C.out_r == 24;
 }
 
 template <int PH>
 static cudaError_t launch_split(const Plan& Pl, const Buffers& Bf, const StageArgs& A, const ColArgs& C, int nb,
-                                cudaStream_t s) {
+                                cudaStream_t s, bool js) {
     constexpr int N1 = ColShape<PH>::N1;
     const int W = C.G * C.ncomp * Pl.TX;
     dim3 grid(((Pl.NT + C.G - 1) / C.G) * (C.ncomp == 3 ? 1 : 3), C.nouter, nb);
-    const bool fixed = Pl.TX == 8 && C.ncomp == 1 && C.G == 1 && C.in_r == 24 && C.out_r == 24;
+    const bool fixed = split_fixed(Pl, C);
     const size_t smem = ((size_t)PH * W + 2 * PH) * sizeof(float2);   // transform buffer + twiddle table
     if (fixed) {
         const int n1 = PH == 1024 ? ColShape3<PH>::N1 : N1;   // three-factor shape (see k_col_split)
-        k_col_split<PH, true><<<grid, W * n1, smem, s>>>(Pl, Bf, A, C);
-    } else {
-        k_col_split<PH, false><<<grid, W * N1, smem, s>>>(Pl, Bf, A, C);
+        if constexpr (PH == 1024) {
+            if (js) {
+                // a half per block; the inverse's two blocks form a cluster
+                dim3 g2(grid.x * 2, grid.y, grid.z);
+                if (C.fwd) return launch_chain(k_col_split<PH, true, true>, g2, W * n1, smem, s, Pl, Bf, A, C);
+                return launch_chain_cl(k_col_split<PH, true, true>, g2, dim3(W * n1), smem, s, 2, Pl, Bf, A, C);
+            }
+        }
+        return launch_chain(k_col_split<PH, true>, grid, W * n1, smem, s, Pl, Bf, A, C);
     }
-    return cudaGetLastError();
+    return launch_chain(k_col_split<PH, false>, grid, W * N1, smem, s, Pl, Bf, A, C);
 }
 
 // z pass with one thread per column (pz <= 32); false if it does not apply.
@@ -661,9 +722,8 @@ static cudaError_t launch_col(const Plan& P, const Buffers& Bf, const StageArgs&
     int per;
     int th = gen_threads(W, C.P, &per);
     size_t sm = (size_t)C.P * W * sizeof(float2);
-    if (per == 2) k_col_gen<2><<<grid, th, sm, s>>>(P, Bf, A, C);
-    else k_col_gen<4><<<grid, th, sm, s>>>(P, Bf, A, C);
-    return cudaGetLastError();
+    if (per == 2) return launch_chain(k_col_gen<2>, grid, th, sm, s, P, Bf, A, C);
+    return launch_chain(k_col_gen<4>, grid, th, sm, s, P, Bf, A, C);
 }
 
 // Threads of a register-path block: W columns x N1 threads each.
@@ -693,6 +753,8 @@ static void spec_strides(const Plan& P, int rows, long long& sb, long long& sz, 
 
 static const size_t COL_SMEM_CAP = 48 * 1024;
 static const int COL_MAX_THREADS = 256;
+// A half per block in the fixed split y passes (forward, inverse) by default.
+static const bool Y_SPLIT_RULE[2] = {false, false};
 
 // One launch of the demag convolution: part 0 = 2-D (fwd y, product, inv y);
 // 3-D: part 1 = forward y, 2 = z forward / product / z inverse, 3 = inverse y.
@@ -736,7 +798,8 @@ cudaError_t launch_conv_part(const Plan& P, const Buffers& Bf, const StageArgs& 
             const bool three = reg_threads(1024, 3 * P.TX) <= 512 && (size_t)1024 * 3 * P.TX * 8 <= 96 * 1024;
             C.ncomp = three ? 3 : 1;
             C.G = tuned_groups(T, part, pick_groups(C.ncomp * P.TX, 1024, P.NT, 512, 96 * 1024));
-            return launch_split<1024>(P, Bf, A, C, nb, s);
+            const int ys = T ? T->y_split[part == 1 ? 0 : 1] : -1;
+            return launch_split<1024>(P, Bf, A, C, nb, s, ys > 0 || (ys < 0 && Y_SPLIT_RULE[part == 1 ? 0 : 1]));
         }
     } else {
         C.in = Bf.spec2; C.out = Bf.spec2;
@@ -784,10 +847,14 @@ cudaError_t launch_convolution(const Plan& P, const Buffers& Bf, const StageArgs
 // The tunable choices of a plan's column passes: the rule's (largest) group
 // count of each part present (0 where the part is not launched), and whether
 // the split z kernel is an alternative.
-void conv_tunables(const Plan& P, int gmax[4], int* z_split_choice, int* z_split_rule) {
+void conv_tunables(const Plan& P, int gmax[4], int* z_split_choice, int* z_split_rule, int* y_split_choice,
+                   int y_split_rule[2]) {
     for (int k = 0; k < 4; k++) gmax[k] = 0;
     *z_split_choice = 0;
     *z_split_rule = 0;
+    *y_split_choice = 0;
+    y_split_rule[0] = Y_SPLIT_RULE[0];
+    y_split_rule[1] = Y_SPLIT_RULE[1];
     if (P.nz == 1) {
         gmax[0] = pick_groups(3 * P.TX, P.py, P.NT, COL_MAX_THREADS, COL_SMEM_CAP);
         return;
@@ -800,6 +867,9 @@ void conv_tunables(const Plan& P, int gmax[4], int* z_split_choice, int* z_split
         if (P.py == 2048 && 2 * P.ny <= P.py) {
             const bool t3 = reg_threads(1024, 3 * P.TX) <= 512 && (size_t)1024 * 3 * P.TX * 8 <= 96 * 1024;
             gmax[part] = pick_groups((t3 ? 3 : 1) * P.TX, 1024, P.NT, 512, 96 * 1024);
+            // the fixed split kernel (tiles of 8, one component per block)
+            // runs at one group per block, the only count this shape allows
+            if (P.TX == 8 && !t3 && gmax[part] == 1) *y_split_choice = 1;
         }
     }
     gmax[2] = pick_groups(3 * P.TX, P.pz, P.py, COL_MAX_THREADS, COL_SMEM_CAP);
@@ -855,6 +925,10 @@ cudaError_t col_init() {
     if ((e = cudaFuncSetAttribute(k_col_split<1024, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) !=
         cudaSuccess)
         return e;
+    if ((e = cudaFuncSetAttribute(k_col_split<1024, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  lim)) != cudaSuccess)
+        return e;
+
     if ((e = cudaFuncSetAttribute(k_zconv2<16, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
         return e;
     if ((e = cudaFuncSetAttribute(k_zconv2<16, 8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)

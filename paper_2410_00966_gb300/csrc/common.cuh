@@ -112,6 +112,7 @@ struct Tune {
     int col_g[4];   // groups per block of each column part (2-D, y forward, z, y inverse); 0 = rule
     int z_split;    // pz = 32: 1 the split z kernel, 0 one thread per column; -1 = rule
     int x_pipe;     // L = 1024: 1 the pipelined x inverse, 0 the per-row kernel; -1 = rule
+    int y_split[2]; // fixed split y passes (forward, inverse): 1 a half per block, 0 both halves; -1 = rule
 };
 
 // Device buffers of one handle.

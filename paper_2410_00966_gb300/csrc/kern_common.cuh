@@ -5,6 +5,31 @@
 
 namespace mq {
 
+// Host side: launch a stage-chain kernel; cluster > 1 groups consecutive
+// blocks along x into clusters of that size.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_chain_cl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                   int cluster, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = cluster > 1 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_chain(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                Args... args) {
+    return launch_chain_cl(kernel, grid, block, smem, s, 1, args...);
+}
+
 // Whether this instance does nothing in this launch.
 __device__ __forceinline__ bool stage_skips(const InstState& s, const StageArgs& A) {
     if (A.field_only) return false;
@@ -83,6 +108,26 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
         if (it == 0) t0 = global_ns();
         else if (global_ns() - t0 > limit_ns) return false;
     }
+}
+
+// ---- thread-block clusters ----------------------------------------------------
+// Barrier over every thread of every block of the cluster (hardware barrier;
+// release / acquire order the shared-memory writes before it against the
+// reads after it, across the blocks).  All threads of a warp must reach it
+// together.
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+// The shared-window address `a` of this block mapped into block `rank` of the cluster.
+__device__ __forceinline__ unsigned cluster_map(unsigned a, unsigned rank) {
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ float2 ld_cluster_f2(unsigned a) {
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+    return v;
 }
 
 // DP45: stage 1 lives in k1slot (first-same-as-last swap between buffers 0 and 6)

@@ -304,19 +304,18 @@ cudaError_t launch_xfwd(const Plan& P, const Buffers& Bf, const StageArgs& A, in
     const size_t sm = xfwd_smem(P);
     if (xpass_fixed(P)) {
         switch (P.L) {
-#define MMCQ_CASE(Lv) case Lv: k_xfwd<Lv, true><<<grid, th, sm, s>>>(P, Bf, A); return cudaGetLastError();
+#define MMCQ_CASE(Lv) case Lv: return launch_chain(k_xfwd<Lv, true>, grid, th, sm, s, P, Bf, A);
             MMCQ_XFIXED(MMCQ_CASE)
 #undef MMCQ_CASE
             default: break;
         }
     }
     switch (P.L) {
-#define MMCQ_CASE(Lv) case Lv: k_xfwd<Lv, false><<<grid, th, sm, s>>>(P, Bf, A); break;
+#define MMCQ_CASE(Lv) case Lv: return launch_chain(k_xfwd<Lv, false>, grid, th, sm, s, P, Bf, A);
         MMCQ_XCASES(MMCQ_CASE)
 #undef MMCQ_CASE
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_spectrum(const double* mh, long long ns, int comp, const double* w, int nw, double* out,

@@ -403,15 +403,16 @@ static bool xpipe_applies(const Plan& P, const Buffers& Bf, const SpecMap* map) 
 }
 
 template <bool REC, int NM>
-static void launch_xpipe(const Plan& P, const Material& mat, const Buffers& Bf, const StageArgs& A, int nb,
+static cudaError_t launch_xpipe(const Plan& P, const Material& mat, const Buffers& Bf, const StageArgs& A, int nb,
                          const SpecMap* map, cudaStream_t s) {
     // persistent: XPIPE_BLOCKS per SM spread over the instances of the launch
     int per = (XPIPE_BLOCKS * g_sms + nb - 1) / nb;
     if (per > P.nrows) per = P.nrows;
     if (per < 1) per = 1;
     const size_t sm = 2 * XPIPE_BUF * sizeof(float2) + 128;   // + alignment slack
-    if (P.nx == 1024) k_xinv_pipe<REC, NM, true><<<dim3(per, nb), XPASS_THREADS, sm, s>>>(P, mat, Bf, A, map->map);
-    else k_xinv_pipe<REC, NM, false><<<dim3(per, nb), XPASS_THREADS, sm, s>>>(P, mat, Bf, A, map->map);
+    if (P.nx == 1024) return launch_chain(k_xinv_pipe<REC, NM, true>, dim3(per, nb), dim3(XPASS_THREADS), sm, s, P, mat, Bf, A,
+                                          map->map);
+    return launch_chain(k_xinv_pipe<REC, NM, false>, dim3(per, nb), dim3(XPASS_THREADS), sm, s, P, mat, Bf, A, map->map);
 }
 
 cudaError_t launch_xinv(const Plan& P, const Material& mat, const Buffers& Bf, const StageArgs& A, int nb,
@@ -423,41 +424,34 @@ cudaError_t launch_xinv(const Plan& P, const Material& mat, const Buffers& Bf, c
     const bool multi = A.nmodes > 1;
     if (xpipe_applies(P, Bf, map) && (!T || T->x_pipe != 0)) {
         if (multi) {
-            if (rec) launch_xpipe<true, MAX_MODES>(P, mat, Bf, A, nb, map, s);
-            else launch_xpipe<false, MAX_MODES>(P, mat, Bf, A, nb, map, s);
-        } else {
-            if (rec) launch_xpipe<true, 1>(P, mat, Bf, A, nb, map, s);
-            else launch_xpipe<false, 1>(P, mat, Bf, A, nb, map, s);
+            if (rec) return launch_xpipe<true, MAX_MODES>(P, mat, Bf, A, nb, map, s);
+            return launch_xpipe<false, MAX_MODES>(P, mat, Bf, A, nb, map, s);
         }
-        return cudaGetLastError();
+        if (rec) return launch_xpipe<true, 1>(P, mat, Bf, A, nb, map, s);
+        return launch_xpipe<false, 1>(P, mat, Bf, A, nb, map, s);
     }
     if (!multi && !rec && xpass_fixed(P)) {
         switch (P.L) {
-#define MMCQ_CASE(Lv)                                                          \
-    case Lv:                                                                   \
-        k_xinv<Lv, false, 1, true><<<grid, th, sm, s>>>(P, mat, Bf, A);        \
-        return cudaGetLastError();
+#define MMCQ_CASE(Lv) \
+    case Lv: return launch_chain(k_xinv<Lv, false, 1, true>, grid, th, sm, s, P, mat, Bf, A);
             MMCQ_XFIXED(MMCQ_CASE)
 #undef MMCQ_CASE
             default: break;
         }
     }
     switch (P.L) {
-#define MMCQ_CASE(Lv)                                                                          \
-    case Lv:                                                                                   \
-        if (multi) {                                                                           \
-            if (rec) k_xinv<Lv, true, MAX_MODES, false><<<grid, th, sm, s>>>(P, mat, Bf, A);   \
-            else k_xinv<Lv, false, MAX_MODES, false><<<grid, th, sm, s>>>(P, mat, Bf, A);      \
-        } else {                                                                               \
-            if (rec) k_xinv<Lv, true, 1, false><<<grid, th, sm, s>>>(P, mat, Bf, A);           \
-            else k_xinv<Lv, false, 1, false><<<grid, th, sm, s>>>(P, mat, Bf, A);              \
-        }                                                                                      \
-        break;
+#define MMCQ_CASE(Lv)                                                                                  \
+    case Lv:                                                                                           \
+        if (multi) {                                                                                   \
+            if (rec) return launch_chain(k_xinv<Lv, true, MAX_MODES, false>, grid, th, sm, s, P, mat, Bf, A); \
+            return launch_chain(k_xinv<Lv, false, MAX_MODES, false>, grid, th, sm, s, P, mat, Bf, A);         \
+        }                                                                                              \
+        if (rec) return launch_chain(k_xinv<Lv, true, 1, false>, grid, th, sm, s, P, mat, Bf, A);            \
+        return launch_chain(k_xinv<Lv, false, 1, false>, grid, th, sm, s, P, mat, Bf, A);
         MMCQ_XCASES(MMCQ_CASE)
 #undef MMCQ_CASE
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 template <typename K>
