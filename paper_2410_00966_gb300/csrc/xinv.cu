@@ -17,6 +17,20 @@
 
 namespace mq {
 
+// e^{+2 pi i k / px} for the point k = j + N1 n2 of a line of L = px / 2
+// complex points: with 16 points per thread (px = 32 N1) it is
+// e^{+2 pi i j / px} conj(W_32^{n2}), one table value per thread times a
+// constant-bank factor; otherwise one table value per point.
+template <int L, int N1>
+__device__ __forceinline__ float2 unpack_twiddle(const float2* __restrict__ tw, int twstep, int j, int n2) {
+    if constexpr (32 * N1 == 2 * L) {
+        const float2 wj = twiddle(tw, j * twstep, true);
+        return n2 == 0 ? wj : cmul(wj, conjf2(c_tw32[n2]));
+    } else {
+        return twiddle(tw, (j + N1 * n2) * twstep, true);
+    }
+}
+
 // The cells of nr rows (row r of the block at (y, z) = s_yz[r]) once the
 // demag field of those rows is in xs (x_2n = Re, x_2n+1 = Im of row x / 2,
 // pitch ld, line 3 r + comp): exchange, then CellUpdate (local fields,
@@ -196,37 +210,27 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xinv(Pla
     }
     cp_async_wait_all();
     __syncthreads();
-    // Z[k] = (X[k] + conj X[L-k]) + i e^{+2 pi i k / px} (X[k] - conj X[L-k]), in place by pairs
     const int twstep = P.twn / P.px;
-    constexpr int HALF = L / 2 + 1;
-    for (int idx = threadIdx.x; idx < 3 * nr * HALF; idx += nthr) {
-        const int line = idx / HALF, k = idx - line * HALF;
-        const int kk = L - k;
-        float2 a = xs[k * ld + line], bq = xs[kk * ld + line];
-        float2 ca = conjf2(bq);
-        float2 sum = cadd(a, ca), dif = csub(a, ca);
-        const float2 w = twiddle(Bf.tw, k * twstep, true);
-        float2 wd = cmul(w, dif);
-        float2 zk = make_float2(sum.x - wd.y, sum.y + wd.x);   // sum + i wd
-        if (k != 0 && kk != k) {
-            float2 cb2 = conjf2(a);
-            float2 sum2 = cadd(bq, cb2), dif2 = csub(bq, cb2);
-            // e^{2 pi i (L - k) / px} = -conj(e^{2 pi i k / px}) since px = 2 L
-            float2 wd2 = cmul(make_float2(-w.x, w.y), dif2);
-            xs[kk * ld + line] = make_float2(sum2.x - wd2.y, sum2.y + wd2.x);
-        }
-        xs[k * ld + line] = zk;
-    }
-    __syncthreads();
     {
         // three-factor: a line's 64 threads are consecutive (lane groups of
         // the last factor inside one warp); otherwise lines are fastest
         const int nl = 3 * Rb;
         const int line = F3 ? threadIdx.x / N1 : threadIdx.x % nl;
         const int j = F3 ? threadIdx.x % N1 : threadIdx.x / nl;
+        // the C2R unpack done as the transform loads its points (k = j + N1 n2):
+        // Z[k] = (X[k] + conj X[L-k]) + i e^{+2 pi i k / px} (X[k] - conj X[L-k]).
+        // Every thread reads before the transform's first barrier, and no
+        // thread stores into xs before it (with N1 = 1 a thread owns its line).
         float2 v[NPT];
 #pragma unroll
-        for (int n2 = 0; n2 < NPT; n2++) v[n2] = xs[(j + N1 * n2) * ld + line];
+        for (int n2 = 0; n2 < NPT; n2++) {
+            const int k = j + N1 * n2;
+            const float2 a = xs[k * ld + line], bq = xs[(L - k) * ld + line];
+            const float2 ca = conjf2(bq);
+            const float2 sum = cadd(a, ca), dif = csub(a, ca);
+            const float2 wd = cmul(unpack_twiddle<L, N1>(Bf.tw, twstep, j, n2), dif);
+            v[n2] = make_float2(sum.x - wd.y, sum.y + wd.x);   // sum + i wd
+        }
         if constexpr (F3) {
             col_fft3<L, true, false, XPASS_F3_PADS, 1>(v, xs, ld, line, j, Bf.tw, P.twn);
 #pragma unroll
@@ -358,32 +362,20 @@ __global__ void __launch_bounds__(XPASS_THREADS, XPIPE_BLOCKS) k_xinv_pipe(Plan 
             return;
         }
         float2* xs = sm + q * XPIPE_BUF;
-        // Z[k] = (X[k] + conj X[L-k]) + i e^{+2 pi i k / px} (X[k] - conj X[L-k]), in place by pairs
-        constexpr int HALF = L / 2 + 1;
-        for (int idx = threadIdx.x; idx < 3 * HALF; idx += nthr) {
-            const int c = idx / HALF, k = idx - c * HALF;
-            const int kk = L - k;
-            float2* pa = xs + xpipe_land(k, c);
-            float2* pb = xs + xpipe_land(kk, c);
-            const float2 a = *pa, bq = *pb;
-            const float2 ca = conjf2(bq);
-            const float2 sum = cadd(a, ca), dif = csub(a, ca);
-            const float2 w = twiddle(Bf.tw, k * twstep, true);
-            const float2 wd = cmul(w, dif);
-            const float2 zk = make_float2(sum.x - wd.y, sum.y + wd.x);
-            if (k != 0 && kk != k) {
-                const float2 cb2 = conjf2(a);
-                const float2 sum2 = cadd(bq, cb2), dif2 = csub(bq, cb2);
-                const float2 wd2 = cmul(make_float2(-w.x, w.y), dif2);
-                *pb = make_float2(sum2.x - wd2.y, sum2.y + wd2.x);
-            }
-            *pa = zk;
-        }
-        __syncthreads();
         {
+            // the C2R unpack done as the transform loads its points (see
+            // k_xinv), X[k] at xpipe_land(k, line)
             float2 v[NPT];
 #pragma unroll
-            for (int n2 = 0; n2 < NPT; n2++) v[n2] = xs[xpipe_land(j + N1 * n2, line)];
+            for (int n2 = 0; n2 < NPT; n2++) {
+                const int k = j + N1 * n2;
+                const float2 a = xs[xpipe_land(k, line)], bq = xs[xpipe_land(L - k, line)];
+                const float2 ca = conjf2(bq);
+                const float2 sum = cadd(a, ca), dif = csub(a, ca);
+                const float2 wd = cmul(unpack_twiddle<L, N1>(Bf.tw, twstep, j, n2), dif);
+                v[n2] = make_float2(sum.x - wd.y, sum.y + wd.x);
+            }
+            // (the transform's first barrier comes before its first store into xs)
             col_fft3<L, true, false, XPASS_F3_PADS, 1>(v, xs, ld, line, j, Bf.tw, P.twn);
 #pragma unroll
             for (int i = 0; i < NPT; i++) xs[col3_out_row<L>(j, i) * ld + line] = v[i];

@@ -7,7 +7,8 @@ FFT is not used:
 * Large CPW-like film (1024x1024x8, 8.4 M cells, Lorentzian coupling profile):
   the demag field at sampled cells by the direct sum (each sample a sum over
   all 8.4 M cells, no FFT on either side of the comparison), and the local
-  terms at the same cells in closed form.
+  terms at the same cells in closed form; the field of every launch plan of
+  the split y passes equal to the default one, bit for bit.
 """
 import numpy as np
 import pytest
@@ -58,4 +59,19 @@ def test_large_cpw_fields_at_sampled_cells():
     err_t = np.abs(Bt[cells] - expect).max()
     print(f"total field at sampled cells: max err {err_t:.3e} T of {np.abs(expect).max():.3e} T")
     assert err_t <= 2e-6 * scale + 2e-6 * np.abs(Bl).max()
+    # every launch plan of this grid's split y passes (one block for both
+    # halves, or a block per half with the inverse's pairs exchanging through
+    # cluster shared memory) gives the same field, bit for bit
+    sim.set_tuning(None)
+    rule = sim.tuning()
+    assert rule["y_split"] != [-1, -1]
+    fields = {}
+    for ys in ([0, 0], [1, 0], [0, 1], [1, 1]):
+        sim.set_tuning(dict(rule, y_split=ys))
+        fields[tuple(ys)] = sim.eval_field(pkg.MMCQ_TERM_DEMAG)
+    sim.set_tuning(None)
+    base = fields[(0, 0)]
+    assert np.array_equal(base.astype(np.float64), Bd)
+    for ys, f in fields.items():
+        assert np.array_equal(f, base), ys
     sim.close()
