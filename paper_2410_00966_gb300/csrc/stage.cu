@@ -56,11 +56,17 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xfwd(Pla
         si.prefetch(Bf, bytes);
     }
     float2* zs = sm;
-    float2* stw = sm + xpass_fft_rows(L) * ld; // exp(-2 pi i e / px), e < px
+    // exp(-2 pi i e / px), e < px: a shared copy for the four-step transform;
+    // the three-factor one (L = 1024) reads the global table through L1
+    float2* stw = sm + xpass_fft_rows(L) * ld;
     const int tws = P.twn / px;
-    for (int e = threadIdx.x; e < px; e += nthr) stw[e] = __ldg(Bf.tw + e * tws);
-    // rows nx/2.. of the packed line are zero padding (rows below are all written)
-    for (int i = (nx >> 1) * ld + threadIdx.x; i < L * ld; i += nthr) zs[i] = make_float2(0.f, 0.f);
+    if constexpr (!F3)
+        for (int e = threadIdx.x; e < px; e += nthr) stw[e] = __ldg(Bf.tw + e * tws);
+    // rows nx/2.. of the packed line are zero padding (rows below are all
+    // written).  FX (nx = L): they are not stored, the transform takes its
+    // points n2 >= NPT / 2 as zeros.
+    if constexpr (!FX)
+        for (int i = (nx >> 1) * ld + threadIdx.x; i < L * ld; i += nthr) zs[i] = make_float2(0.f, 0.f);
     __syncthreads();
 
 
@@ -83,9 +89,10 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xfwd(Pla
         const int j = F3 ? threadIdx.x % N1 : threadIdx.x / nl;
         float2 v[NPT];
 #pragma unroll
-        for (int n2 = 0; n2 < NPT; n2++) v[n2] = zs[(j + N1 * n2) * ld + line];
+        for (int n2 = 0; n2 < NPT; n2++)
+            v[n2] = (!FX || n2 < NPT / 2) ? zs[(j + N1 * n2) * ld + line] : make_float2(0.f, 0.f);
         if constexpr (F3) {
-            col_fft3<L, false, true, XPASS_F3_PADS, 1>(v, zs, ld, line, j, stw, px);
+            col_fft3<L, false, false, XPASS_F3_PADS, 1>(v, zs, ld, line, j, Bf.tw, P.twn);
 #pragma unroll
             for (int i = 0; i < NPT; i++) zs[col3_out_row<L>(j, i) * ld + line] = v[i];
         } else {
@@ -107,7 +114,7 @@ __global__ void __launch_bounds__(XPASS_THREADS, xpass_min_blocks(L)) k_xfwd(Pla
             float2 Zc = conjf2(zs[(k == 0 ? 0 : L - k) * ld + line]);
             float2 E = make_float2(0.5f * (Zk.x + Zc.x), 0.5f * (Zk.y + Zc.y));
             float2 D = make_float2(0.5f * (Zk.x - Zc.x), 0.5f * (Zk.y - Zc.y));
-            float2 wD = cmul(stw[k], D);
+            float2 wD = cmul(F3 ? __ldg(Bf.tw + k * tws) : stw[k], D);
             X = make_float2(E.x + wD.y, E.y - wD.x);
         }
         return X;
@@ -291,8 +298,12 @@ int rows_per_block(int L, int nrows) {
 }
 
 
-// shared memory of the x forward: the packed lines and the px-entry twiddle table
-size_t xfwd_smem(const Plan& P) { return ((size_t)xpass_fft_rows(P.L) * xpass_ld(P.R) + P.px) * sizeof(float2); }
+// shared memory of the x forward: the packed lines and (four-step lengths) the
+// px-entry twiddle table
+size_t xfwd_smem(const Plan& P) {
+    const size_t table = xpass_f3(P.L) ? 0 : (size_t)P.px;   // the three-factor transform reads the global table
+    return ((size_t)xpass_fft_rows(P.L) * xpass_ld(P.R) + table) * sizeof(float2);
+}
 
 
 bool x_fits(const Plan& P) { return P.L <= 1024 && xthreads(P) <= 512 && xinv_smem(P) <= 200 * 1024; }
