@@ -531,24 +531,15 @@ __global__ void __launch_bounds__(512, (FIXED && PH == 1024) ? 2 : 1) k_col_spli
                         if (k < C.n_out) out[k * out_r] = v[i];
                     }
                 } else {
-                    // the even half's rows come back in groups of 4 loads in
-                    // flight at once (a store between two loads of the same
-                    // array would otherwise order every load after the
-                    // previous store)
+                    // the odd half's terms are added onto the even half's rows
+                    // where they are (a reduction in L2, no load back): each
+                    // row holds one store and then one add, both from this
+                    // thread, so the sum is the one rounding of a + y
 #pragma unroll
-                    for (int i0 = 0; i0 < NPT; i0 += 4) {
-                        float2 a[4];
-#pragma unroll
-                        for (int u = 0; u < 4; u++) {
-                            const int k = out_row(i0 + u);
-                            a[u] = k < C.n_out ? out[k * out_r] : make_float2(0.f, 0.f);
-                        }
-#pragma unroll
-                        for (int u = 0; u < 4; u++) {
-                            const int k = out_row(i0 + u);
-                            const float2 y = cmul(v[i0 + u], conjf2(stw[k]));
-                            if (k < C.n_out) out[k * out_r] = make_float2(a[u].x + y.x, a[u].y + y.y);
-                        }
+                    for (int i = 0; i < NPT; i++) {
+                        const int k = out_row(i);
+                        const float2 y = cmul(v[i], conjf2(stw[k]));
+                        if (k < C.n_out) red_add_f2(out + k * out_r, y);
                     }
                 }
             }

@@ -110,6 +110,13 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
     }
 }
 
+// *p += v for a float2 in global memory: a device-scope atomic add whose
+// result is not used, so the add is done where the line lives (L2) and no
+// value comes back to the thread.
+__device__ __forceinline__ void red_add_f2(float2* p, float2 v) {
+    atomicAdd(p, v);
+}
+
 // ---- thread-block clusters ----------------------------------------------------
 // Barrier over every thread of every block of the cluster (hardware barrier;
 // release / acquire order the shared-memory writes before it against the
