@@ -534,7 +534,8 @@ __global__ void __launch_bounds__(512, (FIXED && PH == 1024) ? 2 : 1) k_col_spli
                     // the odd half's terms are added onto the even half's rows
                     // where they are (a reduction in L2, no load back): each
                     // row holds one store and then one add, both from this
-                    // thread, so the sum is the one rounding of a + y
+                    // thread, so the sum is the one rounding of a + y (the
+                    // atomic add flushes subnormal values to zero)
 #pragma unroll
                     for (int i = 0; i < NPT; i++) {
                         const int k = out_row(i);
