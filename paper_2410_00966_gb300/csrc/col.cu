@@ -393,8 +393,8 @@ __global__ void __launch_bounds__(192, 6) k_zconv2(Plan Pl, Buffers Bf, StageArg
 //   forward:  X[2k] = DFT_PH(x)[k],  X[2k+1] = DFT_PH(x_r W_P^r)[k],
 //   inverse:  y[n] = IDFT_PH(h_even)[n] + W_P^{-n} IDFT_PH(h_odd)[n],  n < PH.
 // The same threads do both halves one after the other; in the inverse the odd
-// half is added onto the rows the even half stored (each row stays with one
-// thread, so the read-back is the thread's own store).
+// half is added onto the rows the even half stored, by atomic adds done in L2
+// (each row stays with one thread: one store, then one add).
 // FIXED: one component of one 8-column tile per block (G = 1), rows 24 apart
 // in both spectra, at compile time.
 // F3 (FIXED with PH = 1024): the three-factor transform, 16 points per
