@@ -316,6 +316,25 @@ __global__ void __launch_bounds__(192, 6) k_zconv2(Plan Pl, Buffers Bf, StageArg
     const int t = blockIdx.y, o0 = blockIdx.x * Gb;
     const long long off_in = b * C.in_b + (o0 + g) * C.in_o + t * C.in_t + c * TX + tx;
     const long long off_out = b * C.out_b + (o0 + g) * C.out_o + t * C.out_t + c * TX + tx;
+    if constexpr (P <= 16) {
+        // the rows of the stored kernel this thread's product reads (see
+        // below), asked of L1 now so that they arrive during the forward
+        // transform instead of after its barrier (P = 32 has no registers
+        // to spare for the addresses)
+        const int GT = Gb * TX, lgt = __ffs(GT) - 1;
+        const int p = threadIdx.x & (GT - 1);
+        const int ky = o0 + (p >> lt), kx = t * TX + (p & (TX - 1));
+        const int kyr = ky > Pl.py / 2 ? Pl.py - ky : ky;
+        if (kx < Pl.hx) {
+            const float* Kb = Bf.kern + ((long long)kyr * Pl.NT * TX + kx) * 6;
+            const long long zs = (long long)Pl.hyk * Pl.NT * TX * 6;
+#pragma unroll
+            for (int it = 0; it < (P / 2 + 6) / 6; it++) {
+                const int kzr = (int)(threadIdx.x >> lgt) + 6 * it;
+                if (kzr <= P / 2) asm volatile("prefetch.global.L1 [%0];\n" ::"l"(Kb + kzr * zs));
+            }
+        }
+    }
     if (FIXED) {
         if (half == 0) zsplit_forward<P, 0, true>(C, sm, W, col, C.in + off_in, (int)C.in_r);
         else zsplit_forward<P, 1, true>(C, sm, W, col, C.in + off_in, (int)C.in_r);
