@@ -66,3 +66,35 @@ def test_missing_library_fails_loudly(tmp_path):
     import paper_2410_00966_gb300 as pkg
     with pytest.raises(ImportError):
         pkg.load_library(str(tmp_path / "nope.so"))
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets
+    of the C struct of the same name, as a C compiler lays it out from
+    include/mmcq.h (a field added on one side only fails here)."""
+    import shutil
+    import paper_2410_00966_gb300 as pkg
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [getattr(pkg, n) for n in ("mmcq_grid", "mmcq_opts", "mmcq_cavity", "mmcq_info",
+                                         "mmcq_objective", "mmcq_tuning", "mmcq_kernel_stat")]
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "mmcq.h"', 'int main(void) {']
+    for S in structs:
+        n = S.__name__
+        lines.append(f'    printf("{n} size %zu\\n", sizeof({n}));')
+        for f, _ in S._fields_:
+            lines.append(f'    printf("{n} {f} %zu\\n", offsetof({n}, {f}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(line.split()[:2]): int(line.split()[2]) for line in out if line.strip()}
+    for S in structs:
+        n = S.__name__
+        assert got[(n, "size")] == ctypes.sizeof(S), n
+        for f, _ in S._fields_:
+            assert got[(n, f)] == getattr(S, f).offset, (n, f)
